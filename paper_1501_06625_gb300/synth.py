@@ -1,0 +1,275 @@
+"""Seeded synthetic workloads for the path tracker.
+
+This module holds the input generators that both the CUDA library's tests and
+benchmarks and the CPU oracle consume.  It contains no arithmetic of the method
+itself: only pseudo-random draws, the combinatorial structure of the systems
+(supports and exponents) and unit-modulus coefficients rounded to double.
+
+Random numbers come from xoshiro256** seeded through splitmix64, both written
+here from their published definitions (Blackman & Vigna, "Scrambled linear
+pseudorandom number generators", 2018), so every run on every machine draws the
+same systems from the same seed.
+
+The paper's benchmark inputs (Pieri systems, cyclic n-roots start points,
+Section 4) came from scripts that are not available; the workloads below stand
+in for them by shape: dense general polynomials below dimension 100 (where
+evaluation and differentiation dominate, Introduction) and very sparse
+low-degree systems of several hundred equations (where the linear algebra
+dominates, Introduction).  The cyclic n-roots system (Section 4.2) has a closed
+form and is generated exactly.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_MASK = (1 << 64) - 1
+
+
+def _rotl(x: int, k: int) -> int:
+    return ((x << k) | (x >> (64 - k))) & _MASK
+
+
+class Rng:
+    """xoshiro256** with splitmix64 seeding."""
+
+    def __init__(self, seed: int):
+        z = seed & _MASK
+        self.s = []
+        for _ in range(4):
+            z = (z + 0x9E3779B97F4A7C15) & _MASK
+            w = z
+            w = ((w ^ (w >> 30)) * 0xBF58476D1CE4E5B9) & _MASK
+            w = ((w ^ (w >> 27)) * 0x94D049BB133111EB) & _MASK
+            self.s.append(w ^ (w >> 31))
+
+    def next_u64(self) -> int:
+        s = self.s
+        result = (_rotl((s[1] * 5) & _MASK, 7) * 9) & _MASK
+        t = (s[1] << 17) & _MASK
+        s[2] ^= s[0]
+        s[3] ^= s[1]
+        s[1] ^= s[2]
+        s[0] ^= s[3]
+        s[2] ^= t
+        s[3] = _rotl(s[3], 45)
+        return result
+
+    def uniform(self) -> float:
+        """53-bit uniform in [0, 1)."""
+        return (self.next_u64() >> 11) * (1.0 / (1 << 53))
+
+    def below(self, m: int) -> int:
+        """Integer in [0, m) by multiply-shift of a 64-bit draw."""
+        return (self.next_u64() * m) >> 64
+
+    def choice(self, seq):
+        return seq[self.below(len(seq))]
+
+    def sample(self, n: int, k: int) -> list[int]:
+        """k distinct integers of range(n), partial Fisher-Yates, sorted."""
+        if k > n:
+            raise ValueError("sample larger than population")
+        pool = list(range(n))
+        for i in range(k):
+            j = i + self.below(n - i)
+            pool[i], pool[j] = pool[j], pool[i]
+        return sorted(pool[:k])
+
+    def unit_complex(self) -> complex:
+        """e^{i theta}, theta = 2 pi u, rounded to double."""
+        th = 2.0 * math.pi * self.uniform()
+        return complex(math.cos(th), math.sin(th))
+
+
+@dataclass
+class SystemSpec:
+    """A fully expanded polynomial system: N polynomials in n variables.
+
+    Polynomial i owns terms term_ptr[i]..term_ptr[i+1]-1; term k owns the
+    (variable, exponent) pairs var_ptr[k]..var_ptr[k+1]-1 (exponent >= 1, the
+    variables of a term distinct); a term with no pair is a constant.
+    coeff[k] is the complex coefficient of term k, a double.
+    """
+
+    N: int
+    n: int
+    term_ptr: np.ndarray
+    var_ptr: np.ndarray
+    var_idx: np.ndarray
+    var_exp: np.ndarray
+    coeff: np.ndarray
+
+    @property
+    def M(self) -> int:
+        return int(self.term_ptr[-1])
+
+    def coeff_soa(self, L: int) -> np.ndarray:
+        """Coefficients as [L][2][M] doubles, zero-extended to L limbs."""
+        out = np.zeros((L, 2, self.M))
+        out[0, 0] = self.coeff.real
+        out[0, 1] = self.coeff.imag
+        return out
+
+    def degrees(self) -> np.ndarray:
+        d = np.zeros(self.N, dtype=np.int64)
+        for i in range(self.N):
+            for k in range(self.term_ptr[i], self.term_ptr[i + 1]):
+                d[i] = max(d[i], int(self.var_exp[self.var_ptr[k]:self.var_ptr[k + 1]].sum()))
+        return d
+
+    def max_vars(self) -> int:
+        return int(np.diff(self.var_ptr).max()) if self.M else 0
+
+
+def build_system(N: int, n: int, polys: list[list[tuple[complex, list[tuple[int, int]]]]]) -> SystemSpec:
+    """polys[i] = list of (coefficient, [(var, exp), ...]) terms."""
+    term_ptr, var_ptr, var_idx, var_exp, coeff = [0], [0], [], [], []
+    for terms in polys:
+        for c, mono in terms:
+            coeff.append(complex(c))
+            for v, e in mono:
+                var_idx.append(v)
+                var_exp.append(e)
+            var_ptr.append(len(var_idx))
+        term_ptr.append(len(coeff))
+    return SystemSpec(N, n,
+                      np.asarray(term_ptr, dtype=np.int32), np.asarray(var_ptr, dtype=np.int32),
+                      np.asarray(var_idx, dtype=np.int32), np.asarray(var_exp, dtype=np.int32),
+                      np.asarray(coeff, dtype=np.complex128))
+
+
+def dense_system(rng: Rng, n: int, terms_per_poly: int, vars_per_term: int,
+                 exps: tuple[int, ...], log10_mag: float = 0.0) -> SystemSpec:
+    """Each polynomial: terms over `vars_per_term` distinct variables drawn
+    uniformly without replacement, exponents uniform in `exps`, coefficients of
+    unit modulus (or modulus 10^{U[0, log10_mag]}) and uniform angle."""
+    polys = []
+    for _ in range(n):
+        terms = []
+        for _ in range(terms_per_poly):
+            vs = rng.sample(n, vars_per_term)
+            mono = [(v, rng.choice(exps)) for v in vs]
+            c = rng.unit_complex()
+            if log10_mag > 0.0:
+                c = c * 10.0 ** (log10_mag * rng.uniform())
+            terms.append((c, mono))
+        polys.append(terms)
+    return build_system(n, n, polys)
+
+
+def sparse_system(rng: Rng, n: int, extra_terms: int = 3, vars_per_term: int = 2,
+                  exps: tuple[int, ...] = (1, 2)) -> SystemSpec:
+    """Polynomial i: a linear term c x_i plus `extra_terms` monomials over
+    `vars_per_term` distinct variables other than x_i, exponents in `exps`."""
+    polys = []
+    for i in range(n):
+        terms = [(rng.unit_complex(), [(i, 1)])]
+        for _ in range(extra_terms):
+            vs = rng.sample(n - 1, vars_per_term)
+            vs = [v if v < i else v + 1 for v in vs]
+            terms.append((rng.unit_complex(), [(v, rng.choice(exps)) for v in vs]))
+        polys.append(terms)
+    return build_system(n, n, polys)
+
+
+def cyclic_system(n: int) -> SystemSpec:
+    """Cyclic n-roots (Section 4.2, Eq. (8)): f_i = sum_j prod_{k=j}^{j+i-1}
+    x_{k mod n} for i = 1..n-1, and f_n = x_0 x_1 ... x_{n-1} - 1."""
+    polys = []
+    for i in range(1, n):
+        terms = []
+        for j in range(n):
+            vs = sorted((j + k) % n for k in range(i))
+            terms.append((1.0, [(v, 1) for v in vs]))
+        polys.append(terms)
+    polys.append([(1.0, [(v, 1) for v in range(n)]), (-1.0, [])])
+    return build_system(n, n, polys)
+
+
+def default_params(L: int, **over) -> dict:
+    """Path-tracking parameters (the paper leaves them open)."""
+    p = dict(max_dt=0.1, min_dt=1e-12 if L == 2 else 1e-20,
+             tol_res=1e-24 if L == 2 else 1e-52, tol_dx=1e-24 if L == 2 else 1e-52,
+             max_res=1e8, max_x=1e8, max_steps=10000, max_newton=3, pred_order=4,
+             relax_k=1, fixed_steps=0)
+    p.update(over)
+    return p
+
+
+@dataclass
+class Workload:
+    """One path-tracking job: target system f (start system g, None = total
+    degree), gamma, start point x0 and tracking parameters, in L limbs."""
+
+    name: str
+    seed: int
+    L: int
+    f: SystemSpec
+    gamma: complex
+    x0: np.ndarray                  # complex, length n (doubles)
+    params: dict = field(default_factory=dict)
+    g: SystemSpec | None = None
+
+    @property
+    def n(self) -> int:
+        return self.f.n
+
+    def gamma_soa(self) -> np.ndarray:
+        out = np.zeros((self.L, 2))
+        out[0, 0], out[0, 1] = self.gamma.real, self.gamma.imag
+        return out
+
+    def x0_soa(self) -> np.ndarray:
+        out = np.zeros((self.L, 2, self.n))
+        out[0, 0], out[0, 1] = self.x0.real, self.x0.imag
+        return out
+
+
+def _limbs(prec) -> int:
+    if prec in (2, "dd", "DD"):
+        return 2
+    if prec in (4, "qd", "QD"):
+        return 4
+    raise ValueError(f"precision {prec!r}: expected dd or qd")
+
+
+def dense8(seed: int = 1, prec="dd") -> Workload:
+    """n=8; 8 terms per polynomial over 4 distinct variables, exponents in
+    {1,2}; total-degree start system from the all-ones root; a fixed schedule
+    of 100 steps with 3 Newton updates each."""
+    L = _limbs(prec)
+    rng = Rng(seed)
+    f = dense_system(rng, 8, 8, 4, (1, 2))
+    gamma = rng.unit_complex()
+    return Workload("dense8_fixed100", seed, L, f, gamma, np.ones(8, dtype=np.complex128),
+                    default_params(L, fixed_steps=100, max_newton=3))
+
+
+def dense64(seed: int = 1, prec="dd") -> Workload:
+    """n=64; 64 terms per polynomial over 16 distinct variables, exponents in
+    {1,2,3}; total-degree homotopy from the all-ones root, adaptive steps."""
+    L = _limbs(prec)
+    rng = Rng(seed)
+    f = dense_system(rng, 64, 64, 16, (1, 2, 3))
+    gamma = rng.unit_complex()
+    return Workload(f"dense64_{'dd' if L == 2 else 'qd'}", seed, L, f, gamma,
+                    np.ones(64, dtype=np.complex128), default_params(L))
+
+
+def sparse512(seed: int = 1, prec="qd") -> Workload:
+    """n=512; each polynomial one linear term in x_i plus 3 monomials over 2
+    other variables with exponents in {1,2}; total-degree homotopy, adaptive."""
+    L = _limbs(prec)
+    rng = Rng(seed)
+    f = sparse_system(rng, 512)
+    gamma = rng.unit_complex()
+    return Workload(f"sparse512_{'dd' if L == 2 else 'qd'}", seed, L, f, gamma,
+                    np.ones(512, dtype=np.complex128), default_params(L))
+
+
+def random_x(rng: Rng, n: int, radius: float = 1.0) -> np.ndarray:
+    """Points with coordinates of modulus radius*U[0.5, 1.5] and uniform angle."""
+    return np.array([rng.unit_complex() * radius * (0.5 + rng.uniform()) for _ in range(n)])
