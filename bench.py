@@ -1,0 +1,381 @@
+#!/usr/bin/env python3
+"""Benchmark of the DD/QD path tracker on GB300.
+
+A step is one whole solution path of the dense n = 64 system (64 polynomials
+of 64 monomials over 16 distinct variables, exponents in {1,2,3}, unit-modulus
+coefficients; total-degree homotopy from the all-ones root, adaptive step
+control) in complex double-double, tracked by ph_track_path: every row of the
+hot path (predictor, power table, monomial AD, summation, residual norm, MGS,
+back substitution, update, step control) runs in every step.  The same path in
+complex quad-double is timed beside it.
+
+value   corrector steps (Newton iterations: evaluation + MGS + update) per
+        second, inputs resident on the device, CUDA events on the library's
+        stream, L2 flushed (a 256 MiB write) between steps outside the events;
+e2e     the same through the same call with pinned host buffers, the
+        host<->device copies inside the timed region (wall clock);
+roofline the dominant kernel's FP64 pipe rate (algorithmic FP64 operations
+        per launch / its event-timed launch duration) against the FP64 rate
+        measured on the device in the same run;
+cpu_baseline the CPU oracle on a bounded sample of the same path.
+
+--impl reference times the oracle itself (the deliberately slow reference)
+on the same workload.  Multi-GPU: one process per GPU, each tracks its own
+path (seed + rank), no collective on the data path ("replicas"; weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "corrector steps/s and paths/s (DD/QD) vs plain all-QD form; p50/p99 path latency"
+UNIT = "corrector steps/s"
+
+
+# ---- algorithmic FP64 work per unit (instruction tallies of the library's
+#      primitives; every FP64 add, mul or fma is one operation)
+OPS = {
+    2: dict(cmul=38, cadd=22, cmul_int=(0, 0, 4, 12), c_abs2=19),
+    4: dict(cmul=4 * 122 + 2 * 94, cadd=2 * 94, cmul_int=(0, 0, 8, 2 * 49 + 2 * 12),
+            c_abs2=2 * 122 + 94),
+}
+
+
+def ad_ops(spec, L: int) -> int:
+    """FP64 operations of the monomial AD kernel for one evaluation."""
+    o = OPS[L]
+    total = 0
+    vp = spec.var_ptr
+    for k in range(spec.M):
+        es = spec.var_exp[vp[k]:vp[k + 1]]
+        v = len(es)
+        cf = int(np.sum(es >= 2))
+        if v == 0:
+            continue
+        muls = cf + v + (v - 1) + max(v - 2, 0)
+        total += muls * o["cmul"] + sum(o["cmul_int"][min(int(e), 3)] for e in es)
+    return total
+
+
+def sum_ops(spec, L: int) -> int:
+    o = OPS[L]
+    contrib = int(spec.M + spec.var_ptr[-1])          # values + partials
+    return contrib * o["cadd"]
+
+
+def mgs_ops(N: int, n: int, L: int) -> int:
+    """Per solve: dot (conj mul + add) and update (mul + sub) for every
+    (row, pivot, later column) of [J | rhs], the pivot norms, back substitution."""
+    o = OPS[L]
+    pairs = n * (n + 1) // 2                          # (k, j) with k < j <= n
+    return pairs * N * 2 * (o["cmul"] + o["cadd"]) + n * N * (o["c_abs2"] + o["cadd"] // 2) \
+        + (n * (n - 1) // 2) * (o["cmul"] + o["cadd"])
+
+
+# ---- clocks during the timed region
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---- the CPU oracle on a bounded sample
+
+def oracle_sample(wl, seconds: float = 15.0, max_pc_steps: int = 40):
+    """Tracks the first predictor-corrector steps of the workload's path with
+    the oracle (one thread) until about `seconds` have passed; returns
+    (corrector steps, wall seconds, pc steps)."""
+    import oracle
+    oracle.build()
+    f = oracle.System(wl.f, wl.L)
+    x0, gam = wl.x0_soa(), wl.gamma_soa()
+    steps = 1
+    iters, wall, pcs = 0, 0.0, 0
+    while True:
+        p = dict(wl.params, max_steps=steps - 1)
+        t0 = time.perf_counter()
+        st, x, stats, _ = oracle.track(f, x0, gam, p)
+        dt = time.perf_counter() - t0
+        iters, wall, pcs = stats["newton_iters"], dt, stats["steps"]
+        if dt >= seconds or steps >= max_pc_steps or st != oracle.MAXSTEPS:
+            break
+        # grow the sample geometrically toward the time budget
+        per = dt / max(1, stats["steps"])
+        steps = min(max_pc_steps, max(steps + 1, int(seconds / max(per, 1e-6))))
+    return iters, wall, pcs
+
+
+def run_reference(args):
+    from paper_1501_06625_gb300 import synth
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    wl = synth.dense64(args.seed, args.prec)
+    per_step = []
+    total_iters = 0
+    budget = max(5.0, 150.0 / max(1, args.steps + args.warmup))
+    for i in range(args.warmup + args.steps):
+        iters, wall, pcs = oracle_sample(wl, seconds=budget, max_pc_steps=12)
+        if i >= args.warmup:
+            per_step.append(wall)
+            total_iters += iters
+    value = total_iters / sum(per_step)
+    sample = f"first {pcs} predictor-corrector steps of the {wl.name} path per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(per_step) / len(per_step), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "n": wl.n, "terms_per_poly": 64, "vars_per_term": 16,
+                       "exponents": [1, 2, 3], "homotopy": "total-degree, k=1", "seed": args.seed},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---- the library
+
+def track_leg(libph, ctx, f, wl, dev, steps, warmup, torch, flush, events=True):
+    """Tracks the path `warmup + steps` times with device-resident buffers;
+    returns per-step ms and stats of the timed steps."""
+    L, n = wl.L, wl.n
+    x0 = torch.tensor(wl.x0_soa(), dtype=torch.float64, device=dev)
+    gam = torch.tensor(wl.gamma_soa(), dtype=torch.float64, device=dev)
+    xo = torch.empty_like(x0)
+    stream = torch.cuda.current_stream(dev)
+    ms, stats = [], []
+    for i in range(warmup + steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st, sd, _ = libph.ph_track_path(ctx.h, f, None, gam, x0, wl.params, xo)
+        e1.record(stream)
+        e1.synchronize()
+        if i >= warmup:
+            ms.append(e0.elapsed_time(e1))
+            stats.append(sd)
+    return ms, stats, xo
+
+
+def e2e_leg(libph, ctx, f, wl, steps, torch):
+    """The same call with pinned host buffers (copies inside the call)."""
+    x0 = torch.tensor(wl.x0_soa(), dtype=torch.float64).pin_memory()
+    gam = torch.tensor(wl.gamma_soa(), dtype=torch.float64).pin_memory()
+    xo = torch.empty_like(x0).pin_memory()
+    walls, iters = [], 0
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        st, sd, _ = libph.ph_track_path(ctx.h, f, None, gam, x0, wl.params, xo)
+        walls.append(time.perf_counter() - t0)
+        iters += sd["newton_iters"]
+    h2d = x0.numel() * 8 + gam.numel() * 8
+    d2h = xo.numel() * 8
+    return iters / sum(walls), h2d, d2h
+
+
+def summarize(ms, stats):
+    iters = sum(s["newton_iters"] for s in stats)
+    pcs = sum(s["steps"] for s in stats)
+    tot = sum(ms) / 1e3
+    return {
+        "corrector_steps_per_s": iters / tot,
+        "pc_steps_per_s": pcs / tot,
+        "paths_per_s": len(ms) / tot,
+        "p50_path_ms": float(np.percentile(ms, 50)),
+        "p99_path_ms": float(np.percentile(ms, 99)),
+        "path": {"status": stats[-1]["status"], "steps": stats[-1]["steps"],
+                 "accepted": stats[-1]["accepted"], "rejected": stats[-1]["rejected"],
+                 "newton_iters": stats[-1]["newton_iters"], "t_final": stats[-1]["t_final"]},
+        "launches": sum(s["launches"] for s in stats),
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--prec", default="dd")
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--qd-steps", type=int, default=None)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_1501_06625_gb300 import build, libph, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    build.build()
+    stream = torch.cuda.current_stream(dev)
+    ctx = libph.Context(local, stream=stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    wl = synth.dense64(args.seed + rank, args.prec)
+    f = ctx.load(wl.f, wl.L)
+    peak = libph.ph_fp64_peak(ctx.h, 50.0)            # G lane-ops/s, measured now
+
+    # timed region: barrier + synchronize on both sides, max over ranks
+    track_leg(libph, ctx, f, wl, dev, 0, args.warmup, torch, flush)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local)
+    clocks.start()
+    t0 = time.perf_counter()
+    ms, stats, xo = track_leg(libph, ctx, f, wl, dev, args.steps, 0, torch, flush)
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    if dist:
+        dist.barrier()
+    s = summarize(ms, stats)
+    iters = sum(x["newton_iters"] for x in stats)
+    tot_ms = sum(ms)
+    if dist:
+        t = torch.tensor([tot_ms, float(iters), float(len(ms))], dtype=torch.float64, device=dev)
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        tot_ms_max, iters_all = float(tmax[0]), float(t[1])
+    else:
+        tot_ms_max, iters_all = tot_ms, float(iters)
+    value = iters_all / (tot_ms_max / 1e3)
+
+    # QD leg (same path, quad double)
+    qd = None
+    if args.prec == "dd" and args.qd_steps != 0:
+        wq = synth.dense64(args.seed + rank, "qd")
+        fq = ctx.load(wq.f, wq.L)
+        kq = args.qd_steps if args.qd_steps is not None else max(1, args.steps // 2)
+        msq, statsq, _ = track_leg(libph, ctx, fq, wq, dev, kq, 1, torch, flush)
+        qd = summarize(msq, statsq)
+        qd.pop("launches")
+
+    # end to end through the same call with host buffers
+    e2e_v, h2d, d2h = e2e_leg(libph, ctx, f, wl, max(2, args.steps // 2), torch)
+
+    # roofline of the dominant kernel, timed live on the library's stream
+    x_mid = torch.tensor(wl.x0_soa(), dtype=torch.float64, device=dev)
+    tl = torch.zeros(wl.L, dtype=torch.float64, device=dev)
+    tl[0] = 0.05
+    gam = torch.tensor(wl.gamma_soa(), dtype=torch.float64, device=dev)
+    kms = libph.ph_profile_newton(ctx.h, f, None, gam, 1, tl, x_mid, 20)
+    names = ["prep", "monomial_ad", "summation", "mgs"]
+    ops = {"monomial_ad": ad_ops(wl.f, wl.L), "summation": sum_ops(wl.f, wl.L),
+           "mgs": mgs_ops(wl.f.N, wl.n, wl.L)}
+    dom = max(("monomial_ad", "summation", "mgs"), key=lambda k: kms[names.index(k)])
+    dms = kms[names.index(dom)]
+    achieved = ops[dom] / (dms * 1e-3) / 1e9
+    roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
+            "unit": "G FP64-ops/s", "frac": achieved / peak, "traffic": None,
+            "peak_source": "measured DFMA rate on this GPU in this run (ph_fp64_peak)",
+            "kernel_ms": dict(zip(names, kms)), "ops_per_launch": ops[dom]}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        it_c, wall_c, pcs_c = oracle_sample(wl, seconds=args.cpu_seconds)
+        cpu = {"value": it_c / wall_c, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"first {pcs_c} predictor-corrector steps of the {wl.name} path "
+                         f"({it_c} corrector steps, {wall_c:.1f} s, one thread)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms_max / len(ms),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "n": wl.n, "terms_per_poly": 64, "vars_per_term": 16,
+                       "exponents": [1, 2, 3], "homotopy": "total-degree from all-ones, k=1",
+                       "seed": args.seed, "precision": "complex double-double",
+                       "l2": "flushed (256 MiB write) between steps",
+                       "parallelism": f"replicas x{world}"},
+            "paths_per_s": s["paths_per_s"], "pc_steps_per_s": s["pc_steps_per_s"],
+            "p50_path_ms": s["p50_path_ms"], "p99_path_ms": s["p99_path_ms"],
+            "path": s["path"], "qd": qd,
+            "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": s["launches"], "roofline": roof, "cpu_baseline": cpu,
+            "clocks": clk, "wall_s_timed": wall,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,209 @@
+/*
+ * ph.h -- C ABI of libph: one Newton predictor-corrector step of polynomial
+ * homotopy continuation in complex double-double (DD) and quad-double (QD)
+ * arithmetic on one GPU (sm_103a), after Verschelde & Yu, "Accelerating
+ * Polynomial Homotopy Continuation on a Graphics Processing Unit with Double
+ * Double and Quad Double Arithmetic" (2015).
+ *
+ * Conventions (all entry points):
+ *  - Every call returns a ph_status; nothing throws or aborts across the ABI.
+ *    On an error the context keeps a message for ph_last_error().
+ *  - Multi-limb numbers: a real in L limbs (L = 2 for DD, 4 for QD) is L
+ *    doubles, leading limb first, whose exact sum is the value.  A vector of m
+ *    complex numbers is m*2*L doubles laid out [limb][re|im][index]; an N x n
+ *    complex matrix is column-major [limb][re|im][column][row].
+ *  - Array arguments may be host or device pointers; the library asks the CUDA
+ *    runtime which, copies host data in and out itself, and works on device
+ *    data in place.  Inputs are only read; the caller keeps ownership of every
+ *    buffer it passes.  Outputs go to caller-provided buffers.
+ *  - Work runs on the stream given to ph_init (NULL = the legacy default
+ *    stream); calls return once their results are in the caller's buffers.
+ *  - A context is not thread-safe: one host thread per context at a time.
+ *  - Waits inside the library's own kernels are bounded; a wait that runs out
+ *    makes the call return PH_TIMEOUT with the context still usable.
+ */
+#ifndef PH_H
+#define PH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { PH_DD = 2, PH_QD = 4 } ph_prec;     /* value = limbs per real */
+
+typedef enum {
+  PH_OK = 0,
+  PH_EINVAL = 1,     /* invalid argument (sizes, indices, layout, parameters)   */
+  PH_ENOMEM = 2,     /* device or host allocation failed                         */
+  PH_ECUDA = 3,      /* a CUDA runtime call failed (message in ph_last_error)    */
+  PH_DIVERGED = 4,   /* ||x||_inf exceeded ph_track_params.max_x                 */
+  PH_MAXSTEPS = 5,   /* more than max_steps predictor-corrector steps            */
+  PH_STEPMIN = 6,    /* the step size fell below min_dt                          */
+  PH_NONFINITE = 7,  /* a non-finite start point, or a zero column in the QR     */
+  PH_TIMEOUT = 8     /* a bounded device-side wait ran out                        */
+} ph_status;
+
+typedef struct ph_ctx ph_ctx;
+typedef struct ph_system ph_system;
+
+/* Creates a context on CUDA device `device`, working on `cuda_stream`
+ * (a cudaStream_t, may be NULL).  *ctx receives the handle. */
+ph_status ph_init(ph_ctx **ctx, int device, void *cuda_stream);
+
+/* Destroys a context (systems loaded into it must be freed first). */
+ph_status ph_destroy(ph_ctx *ctx);
+
+/* The message of the last failed call on this context ("" if none). */
+const char *ph_last_error(ph_ctx *ctx);
+
+/* Loads a polynomial system of N polynomials in n variables, N >= n (Section
+ * 2, input specification), given fully expanded (Section 3.1: "fully expanded
+ * distributed symbolic representation"):
+ *   polynomial i owns terms term_ptr[i] .. term_ptr[i+1]-1   (term_ptr: N+1);
+ *   term k owns the pairs var_ptr[k] .. var_ptr[k+1]-1        (var_ptr: M+1);
+ *   pair p is variable var_idx[p] in [0, n) with exponent var_exp[p] >= 1;
+ *   the variables of one term are distinct; a term with no pair is a constant;
+ *   coeff holds the M complex coefficients, [L][2][M] doubles.
+ * The arrays are copied to the device once (Section 3.1: the structures and
+ * coefficients cross to the device only at the start); the system keeps the
+ * instruction layout the evaluation kernels read.  PH_EINVAL for any
+ * malformed index, pointer array or exponent. */
+ph_status ph_system_load(ph_ctx *ctx, ph_prec prec, int N, int n,
+                         const int32_t *term_ptr, const int32_t *var_ptr,
+                         const int32_t *var_idx, const int32_t *var_exp,
+                         const double *coeff, ph_system **out);
+
+/* Frees a system and its device memory. */
+ph_status ph_system_free(ph_system *sys);
+
+/* Values h [L][2][N] and Jacobian J [L][2][n][N] (column-major) of the
+ * homotopy h(x,t) = gamma (1-t)^k g(x) + t^k f(x) (Section 2, Eq. (1)) at the
+ * point x [L][2][n]:
+ *   g      start system, or NULL for the total-degree system
+ *          g_i = x_i^{d_i} - 1 with d_i the degree of f_i (needs N == n);
+ *   gamma  [L][2] complex constant; NULL evaluates f alone (h = f, J = Jf);
+ *   k      relaxation exponent >= 1 (the paper uses k >= 2; k = 1 is the
+ *          plain linear homotopy);
+ *   t      the real parameter, L limbs (only read when gamma != NULL).
+ * Monomials are differentiated in the reverse mode (Speelpenning products
+ * with a common factor for exponents > 1, Section 3.2) and summed into h and J
+ * (Section 3.3). */
+ph_status ph_eval_jac(ph_ctx *ctx, const ph_system *f, const ph_system *g,
+                      const double *gamma, int k, const double *t, const double *x,
+                      double *h, double *J);
+
+/* Least-squares solution dx [L][2][n] of J dx = rhs for an N x n matrix J
+ * [L][2][n][N] (N >= n) and rhs [L][2][N], by modified Gram-Schmidt on the
+ * augmented matrix [J | rhs] and back substitution (Introduction: MGS instead
+ * of LU with pivoting; Section 3.1, GPU_Modified_Gram_Schmidt).  resid_norm,
+ * if not NULL, receives ||J dx - rhs||_2 in double (a host pointer).
+ * PH_NONFINITE if a column becomes zero (rank deficiency). */
+ph_status ph_mgs_solve(ph_ctx *ctx, ph_prec prec, int N, int n, const double *J,
+                       const double *rhs, double *dx, double *resid_norm);
+
+/* Path-tracking parameters (Section 2 and Fig. "Accelerated tracking of one
+ * single path"; the paper leaves the values open). */
+typedef struct {
+  double max_dt;      /* largest step size h_max, also the first step size      */
+  double min_dt;      /* smallest step size h_min: halving below it ends the
+                         path with PH_STEPMIN                                     */
+  double tol_res;     /* Newton succeeds when ||h(x,t)||_inf < tol_res           */
+  double tol_dx;      /* ... or when ||dx||_inf < tol_dx (after the update)       */
+  double max_res;     /* residual bound for the first Newton iteration           */
+  double max_x;       /* ||x||_inf above this after an accepted step: PH_DIVERGED */
+  int32_t max_steps;  /* more than this many steps: PH_MAXSTEPS                  */
+  int32_t max_newton; /* Newton iterations per step (P.max_iteration)            */
+  int32_t pred_order; /* largest degree of the extrapolation predictor (0..8)    */
+  int32_t relax_k;    /* k in gamma (1-t)^k g + t^k f, >= 1                      */
+  int32_t fixed_steps;/* > 0: fixed schedule t_j = j / fixed_steps with exactly
+                         max_newton updates per step, no test, no rejection      */
+  int32_t reserved;   /* must be 0                                                */
+} ph_track_params;
+
+/* Outcome of one tracked path. */
+typedef struct {
+  int32_t status;       /* ph_status of the path                                 */
+  int32_t steps;        /* predictor-corrector steps taken                       */
+  int32_t accepted;     /* steps whose corrector succeeded                        */
+  int32_t rejected;     /* steps whose corrector failed (step size halved)       */
+  int32_t newton_iters; /* evaluations of h and J (corrector iterations)         */
+  int32_t updates;      /* applied Newton updates x += dx                         */
+  double t_final;       /* t of the last accepted point                           */
+  double res;           /* last residual norm seen by the corrector              */
+  double dx;            /* last update norm seen by the corrector                */
+  int64_t launches;     /* kernels the library launched for this path            */
+} ph_path_stats;
+
+/* One step of the schedule actually taken, for replay. */
+typedef struct {
+  double t;             /* the t the step tried                                   */
+  double res;           /* last residual norm of its corrector                    */
+  double dx;            /* last update norm of its corrector                      */
+  int32_t accepted;     /* 1 if the corrector succeeded                           */
+  int32_t updates;      /* Newton updates applied during the step                */
+} ph_step_record;
+
+/* Tracks one solution path of h(x,t) = gamma (1-t)^k g(x) + t^k f(x) from the
+ * start solution x0 of g at t = 0 to t = 1 (Section 2, input-output
+ * specification; Fig. "An accelerated Newton's method" and Fig. "Accelerated
+ * tracking of one single path"):
+ *   t := min(1, t + dt); predict x by extrapolation through the last accepted
+ *   points (degree min(pred_order, #accepted - 1), Section 3.1); run Newton's
+ *   method (fail if the residual grows, succeed if ||h|| < tol_res or
+ *   ||dx|| < tol_dx); on success keep the point and, after more than two
+ *   successes in a row, double dt up to max_dt; on failure go back to the last
+ *   accepted point and halve dt.
+ * The whole loop runs on the device (one CUDA graph launch per path); the
+ * host reads the result once at the end.
+ *   f, g, gamma  as in ph_eval_jac (gamma is required here);
+ *   x0           start solution [L][2][n];
+ *   x_out        end point [L][2][n] (the last accepted point);
+ *   stats        may be NULL;
+ *   log, log_cap optional schedule log (host memory, NULL/0 for none); the
+ *                first min(steps, log_cap) steps are recorded.
+ * Returns the path status (PH_OK when t = 1 was reached). */
+ph_status ph_track_path(ph_ctx *ctx, const ph_system *f, const ph_system *g,
+                        const double *gamma, const double *x0,
+                        const ph_track_params *params, double *x_out,
+                        ph_path_stats *stats, ph_step_record *log, int log_cap);
+
+/* Host-side step-size controller of the path tracker, exported so it can be
+ * checked without a GPU: the same code runs inside the device controller.
+ * Fig. "Accelerated tracking of one single path". */
+typedef struct {
+  double t, dt;
+  int32_t nsucc, nsteps, done, status;
+} ph_ctrl_state;
+
+void ph_ctrl_init(ph_ctrl_state *c, const ph_track_params *p);
+/* The next t to try, or -1 once the controller has stopped. */
+double ph_ctrl_next_t(ph_ctrl_state *c, const ph_track_params *p);
+/* Reports the corrector's outcome at t_new. */
+void ph_ctrl_report(ph_ctrl_state *c, const ph_track_params *p, double t_new, int success);
+
+/* Measurement support (Section 5 reports per-kernel times; the roofline of
+ * this FP64-bound path needs the FP64 rate of the device it runs on).
+ *
+ * ph_profile_newton runs `reps` corrector iterations at (x, t) outside any graph
+ * and times each of its kernels with CUDA events on the context's stream;
+ * ms_out[0..3] receive the average milliseconds per launch of: the power table
+ * and homotopy factors, the monomial AD, the summation/assembly, and the MGS
+ * solve with back substitution.  Arguments as in ph_eval_jac (gamma required).
+ *
+ * ph_fp64_peak times a kernel of independent FP64 fused multiply-adds on every
+ * SM for about `ms_target` milliseconds and returns the rate in G lane-ops/s
+ * (one DFMA of one thread = one op; 2 flops). */
+ph_status ph_profile_newton(ph_ctx *ctx, const ph_system *f, const ph_system *g,
+                            const double *gamma, int k, const double *t, const double *x,
+                            int reps, double *ms_out);
+ph_status ph_fp64_peak(ph_ctx *ctx, double ms_target, double *gops);
+
+/* Library version string. */
+const char *ph_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PH_H */

@@ -1,0 +1,17 @@
+"""GB300-native hot path of polynomial homotopy continuation in complex
+double-double and quad-double arithmetic (after Verschelde & Yu, 2015).
+
+Submodules, imported on first use:
+  libph  -- Python binding of the C ABI in include/ph.h (libph.so, sm_103a)
+  build  -- compiles libph.so in tree
+  synth  -- seeded synthetic workloads
+"""
+import importlib
+
+__all__ = ["libph", "build", "synth"]
+
+
+def __getattr__(name):
+    if name in __all__:
+        return importlib.import_module(f".{name}", __name__)
+    raise AttributeError(name)

@@ -1,0 +1,241 @@
+// eval.cu -- values and Jacobian of h(x,t) = gamma (1-t)^k g(x) + t^k f(x)
+// (Section 2, Eq. (1)) by reverse-mode differentiation of every monomial
+// (Section 3.2) and segmented summation (Section 3.3).
+//
+// Three kernels per evaluation:
+//  k_prep  power table x_j^e (e < largest exponent) and the homotopy factors
+//          t^k and gamma (1-t)^k;
+//  k_ad    one thread per monomial c x^a with v distinct variables: the common
+//          factor CF = prod x_j^{a_j - 1} from the power table is folded into
+//          the coefficient, then the Speelpenning product of the v variables is
+//          differentiated in the reverse mode (forward prefix products, backward
+//          suffix and cross products, Table "Evaluating four monomials"):
+//            d/dx_j (c x^a) = a_j * (c CF x_1..x_{j-1}) * (x_{j+1}..x_v).
+//          Monomials are sorted by v so a warp runs monomials of equal length,
+//          and the instructions are stored position-major so lanes read
+//          consecutive addresses (Section 3.2).  Results go to "slots".
+//  k_sum   G lanes per output (the paper's #Th, Section 3.3) add the output's
+//          slots in a fixed order (no atomics: the result is deterministic),
+//          scale by the homotopy factors, add the start system and write J, h,
+//          -h (the right-hand side of the Newton system) and max |h_i|.
+#include "internal.h"
+#include "mp.cuh"
+
+using namespace ph;
+
+namespace {
+
+template <class P>
+PHD cx<P> c_pow(cx<P> x, int e) {
+  cx<P> r = c_from<P>(1.0, 0.0);
+  bool first = true;
+  while (e > 0) {
+    if (e & 1) {
+      r = first ? x : c_mul<P>(r, x);
+      first = false;
+    }
+    e >>= 1;
+    if (e) x = c_mul<P>(x, x);
+  }
+  return r;
+}
+
+template <class P>
+PHD cx<P> shfl_down_c(const cx<P> &a, int off, int width) {
+  cx<P> z;
+#pragma unroll
+  for (int l = 0; l < P::L; ++l) {
+    P::set_limb(z.re, l, __shfl_down_sync(0xffffffffu, P::limb(a.re, l), off, width));
+    P::set_limb(z.im, l, __shfl_down_sync(0xffffffffu, P::limb(a.im, l), off, width));
+  }
+  return z;
+}
+
+template <class P>
+__global__ void k_prep(const double *__restrict__ x, int n, int emax, double *__restrict__ ptab,
+                       const double *__restrict__ t, const double *__restrict__ gamma, int k,
+                       double *__restrict__ scal, const int *__restrict__ skip) {
+  if (skip && *skip) return;
+  const long pl = 2L * P::L * n;
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) {
+    cx<P> xj = c_load<P>(x, n, j);
+    c_store<P>(ptab, n, j, xj);
+    cx<P> p = xj;
+    for (int e = 2; e < emax; ++e) {
+      p = c_mul<P>(p, xj);
+      c_store<P>(ptab + (e - 1) * pl, n, j, p);
+    }
+  }
+  if (gamma && blockIdx.x == 0 && threadIdx.x == 0) {
+    typename P::real tt = r_load<P>(t, 1, 0);
+    typename P::real omt = P::sub(P::from(1.0), tt);
+    typename P::real tk = P::from(1.0), ok = P::from(1.0);
+    for (int e = 0; e < k; ++e) {
+      tk = P::mul(tk, tt);
+      ok = P::mul(ok, omt);
+    }
+    cx<P> g = c_load<P>(gamma, 1, 0);
+    r_store<P>(scal, 1, 0, tk);
+    c_store<P>(scal + P::L, 1, 0, c_mul_real<P>(g, ok));
+  }
+}
+
+template <class P>
+__global__ void __launch_bounds__(128) k_ad(int M, int Mp, const int32_t *__restrict__ nv,
+                                            const int32_t *__restrict__ vidx,
+                                            const int32_t *__restrict__ vexp,
+                                            const double *__restrict__ coeff,
+                                            const double *__restrict__ ptab, int n, int maxv,
+                                            double *__restrict__ slots, long nslots,
+                                            const int *__restrict__ skip) {
+  if (skip && *skip) return;
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= M) return;
+  const long pl = 2L * P::L * n;
+  const int v = nv[s];
+  cx<P> c = c_load<P>(coeff, Mp, s);
+  for (int p = 0; p < v; ++p) {
+    int a = vexp[(long)p * Mp + s];
+    if (a >= 2) c = c_mul<P>(c, c_load<P>(ptab + (a - 2) * pl, n, vidx[(long)p * Mp + s]));
+  }
+  cx<P> pre = c;
+  for (int p = 0; p < v; ++p) {
+    c_store<P>(slots, nslots, (long)p * Mp + s, pre);
+    pre = c_mul<P>(pre, c_load<P>(ptab, n, vidx[(long)p * Mp + s]));
+  }
+  c_store<P>(slots, nslots, (long)maxv * Mp + s, pre);
+  cx<P> suf = c_zero<P>();
+  for (int p = v - 1; p >= 0; --p) {
+    cx<P> d = c_load<P>(slots, nslots, (long)p * Mp + s);
+    if (p < v - 1) d = c_mul<P>(d, suf);
+    d = c_mul_int<P>(d, vexp[(long)p * Mp + s]);
+    c_store<P>(slots, nslots, (long)p * Mp + s, d);
+    if (p > 0) {
+      cx<P> xj = c_load<P>(ptab, n, vidx[(long)p * Mp + s]);
+      suf = (p == v - 1) ? xj : c_mul<P>(suf, xj);
+    }
+  }
+}
+
+template <class P, int G>
+__global__ void __launch_bounds__(256) k_sum(
+    int N, int n, int nout, const int32_t *__restrict__ optr, const int32_t *__restrict__ oslot,
+    const double *__restrict__ slots, long nslots, const int32_t *__restrict__ goptr,
+    const int32_t *__restrict__ goslot, const double *__restrict__ gslots, long gnslots,
+    const int32_t *__restrict__ deg, const double *__restrict__ x,
+    const double *__restrict__ scal, int homotopy, double *__restrict__ J, long ldJ, long Jplane,
+    double *__restrict__ h, double *__restrict__ rhs, long rhs_plane,
+    unsigned long long *__restrict__ res_bits, const int *__restrict__ skip) {
+  if (skip && *skip) return;
+  long gt = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  int o = (int)(gt / G);
+  int lane = (int)(gt % G);
+  bool active = o < nout;
+  cx<P> af = c_zero<P>(), ag = c_zero<P>();
+  if (active) {
+    for (int q = optr[o] + lane; q < optr[o + 1]; q += G)
+      af = c_add<P>(af, c_load<P>(slots, nslots, oslot[q]));
+    if (goptr)
+      for (int q = goptr[o] + lane; q < goptr[o + 1]; q += G)
+        ag = c_add<P>(ag, c_load<P>(gslots, gnslots, goslot[q]));
+  }
+#pragma unroll
+  for (int off = G / 2; off > 0; off >>= 1) {
+    af = c_add<P>(af, shfl_down_c<P>(af, off, G));
+    if (goptr) ag = c_add<P>(ag, shfl_down_c<P>(ag, off, G));
+  }
+  if (!active || lane != 0) return;
+  cx<P> val = af;
+  cx<P> sg = c_zero<P>();
+  if (homotopy) {
+    typename P::real sf = r_load<P>(scal, 1, 0);
+    sg = c_load<P>(scal + P::L, 1, 0);
+    val = c_mul_real<P>(af, sf);
+    if (goptr) val = c_add<P>(val, c_mul<P>(sg, ag));
+  }
+  const int nN = n * N;
+  if (o < nN) {
+    int j = o / N, i = o - j * N;
+    if (homotopy && !goptr && i == j) {            // d_i x_i^{d_i - 1}
+      int d = deg[i];
+      cx<P> pw = c_mul_d<P>(c_pow<P>(c_load<P>(x, n, i), d - 1), (double)d);
+      val = c_add<P>(val, c_mul<P>(sg, pw));
+    }
+    c_store<P>(J + (long)j * ldJ, Jplane, i, val);
+  } else {
+    int i = o - nN;
+    if (homotopy && !goptr) {                       // x_i^{d_i} - 1
+      cx<P> pw = c_pow<P>(c_load<P>(x, n, i), deg[i]);
+      pw.re = P::sub(pw.re, P::from(1.0));
+      val = c_add<P>(val, c_mul<P>(sg, pw));
+    }
+    if (h) c_store<P>(h, N, i, val);
+    if (rhs) c_store<P>(rhs, rhs_plane, i, c_neg<P>(val));
+    if (res_bits) atomicMax(res_bits, (unsigned long long)__double_as_longlong(c_mag_lead<P>(val)));
+  }
+}
+
+template <class P>
+cudaError_t eval_impl(ph_ctx *ctx, const ph_system *f, const ph_system *g, const double *gamma,
+                      int k, const double *t, const double *x, double *h, double *J, long ldJ,
+                      long Jplane, double *rhs, long rhs_plane, const int *skip,
+                      unsigned long long *res_bits, int parts) {
+  const int L = P::L, n = f->n, N = f->N;
+  int emax = f->emax;
+  if (g && g->emax > emax) emax = g->emax;
+  const int ntab = emax > 2 ? emax - 1 : 1;
+  cudaError_t e;
+  if ((e = ctx->ptab.ensure(sizeof(double) * 2 * L * (size_t)n * ntab)) != cudaSuccess) return e;
+  if ((e = ctx->scal.ensure(sizeof(double) * 3 * L)) != cudaSuccess) return e;
+  const long fs = (long)(f->maxv + 1) * f->Mp;
+  const long gs = g ? (long)(g->maxv + 1) * g->Mp : 0;
+  if ((e = ctx->slots.ensure(sizeof(double) * 2 * L * (size_t)(fs + gs + 1))) != cudaSuccess) return e;
+  double *ptab = ctx->ptab.as<double>(), *scal = ctx->scal.as<double>();
+  double *fslots = ctx->slots.as<double>(), *gslots = fslots + 2 * L * fs;
+  cudaStream_t st = ctx->stream;
+
+  if (parts & 1)
+    k_prep<P><<<(n + 127) / 128, 128, 0, st>>>(x, n, emax, ptab, t, gamma, k, scal, skip);
+  if ((parts & 2) && f->M > 0)
+    k_ad<P><<<(f->M + 127) / 128, 128, 0, st>>>(f->M, f->Mp, f->nv.as<int32_t>(),
+                                                f->vidx.as<int32_t>(), f->vexp.as<int32_t>(),
+                                                f->coeff.as<double>(), ptab, n, f->maxv, fslots,
+                                                fs, skip);
+  if ((parts & 2) && g && g->M > 0)
+    k_ad<P><<<(g->M + 127) / 128, 128, 0, st>>>(g->M, g->Mp, g->nv.as<int32_t>(),
+                                                g->vidx.as<int32_t>(), g->vexp.as<int32_t>(),
+                                                g->coeff.as<double>(), ptab, n, g->maxv, gslots,
+                                                gs, skip);
+  constexpr int G = 8;
+  const long threads = (long)f->nout * G;
+  if (parts & 4)
+  k_sum<P, G><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
+      N, n, f->nout, f->out_ptr.as<int32_t>(), f->out_slot.as<int32_t>(), fslots, fs,
+      g ? g->out_ptr.as<int32_t>() : nullptr, g ? g->out_slot.as<int32_t>() : nullptr, gslots, gs,
+      f->deg.as<int32_t>(), x, scal, gamma != nullptr, J, ldJ, Jplane, h, rhs, rhs_plane,
+      res_bits, skip);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t ph_eval_launch_part(ph_ctx *ctx, const ph_system *f, const ph_system *g,
+                                const double *gamma, int k, const double *t, const double *x,
+                                double *h, double *J, long ldJ, long Jplane, double *rhs,
+                                long rhs_plane, const int *skip, unsigned long long *res_bits,
+                                int parts) {
+  if (f->L == 2)
+    return eval_impl<DD>(ctx, f, g, gamma, k, t, x, h, J, ldJ, Jplane, rhs, rhs_plane, skip,
+                         res_bits, parts);
+  return eval_impl<QD>(ctx, f, g, gamma, k, t, x, h, J, ldJ, Jplane, rhs, rhs_plane, skip,
+                       res_bits, parts);
+}
+
+cudaError_t ph_eval_launch(ph_ctx *ctx, const ph_system *f, const ph_system *g,
+                           const double *gamma, int k, const double *t, const double *x,
+                           double *h, double *J, long ldJ, long Jplane, double *rhs,
+                           long rhs_plane, const int *skip, unsigned long long *res_bits) {
+  return ph_eval_launch_part(ctx, f, g, gamma, k, t, x, h, J, ldJ, Jplane, rhs, rhs_plane, skip,
+                             res_bits, 7);
+}

@@ -1,0 +1,119 @@
+// internal.h -- host-side structures of libph shared by its translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "ph.h"
+
+// A growable device buffer owned by a context or a system.
+struct DevBuf {
+  void *p = nullptr;
+  size_t cap = 0;
+  cudaError_t ensure(size_t bytes) {
+    if (bytes <= cap) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    cudaError_t e = cudaMalloc(&p, bytes ? bytes : 16);
+    if (e == cudaSuccess) cap = bytes;
+    return e;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+  template <class T> T *as() const { return (T *)p; }
+};
+
+// Device-side state of one tracked path and of its current corrector run.
+// Lives in device memory; the step kernels read and update it.
+struct PathState {
+  // step-size controller (Fig. "Accelerated tracking of one single path")
+  ph_ctrl_state ctrl;
+  // the step being tried
+  double t_new;
+  int32_t hist_count, hist_head;
+  // corrector (Fig. "An accelerated Newton's method")
+  int32_t nt_done, nt_success, nt_iters, nt_updates;
+  double last_res, res, dxn;
+  unsigned long long res_bits, dx_bits, x_bits;
+  // path statistics
+  int32_t steps, accepted, rejected, newton_iters, updates, log_len;
+  double res_last, dx_last;
+  // set when a bounded device wait ran out
+  int32_t timeout, mgs_status;
+  // grid barrier of the cooperative kernels
+  unsigned int bar_count, bar_gen;
+  int32_t iterations;           // passes of the graph's step body
+  // kernel gates: a kernel does nothing while its flag is set
+  int32_t skip_step, skip_nt;
+  double t_dev[4];              // t of the step, L limbs
+  double hist_t[16];            // t of the accepted points in the history ring
+};
+
+struct ph_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int sm_count = 0;
+  std::string err;
+  DevBuf in_x, in_gamma, in_t, in_J, in_rhs;       // staged host inputs
+  DevBuf out_h, out_J, out_dx;                      // staged outputs
+  DevBuf slots, ptab, scal, A, R, nrm2, irkk, dxv, state, hist, xw, logbuf, ystage;
+};
+
+// A loaded polynomial system: the instruction layout of Section 3.2 (terms
+// sorted by their number of variables, position-major arrays so consecutive
+// threads read consecutive addresses) plus the summation lists.
+struct ph_system {
+  ph_ctx *ctx = nullptr;
+  int L = 2, N = 0, n = 0, M = 0, Mp = 0, maxv = 0, emax = 1;
+  int nout = 0;                 // n*N Jacobian entries + N values
+  int max_contrib = 0;          // longest summation list
+  DevBuf poly, nv, vidx, vexp, coeff, deg, out_ptr, out_slot;
+  std::vector<int> h_deg;
+  int max_deg = 0;
+};
+
+// ---- helpers (api.cu)
+ph_status ph_fail(ph_ctx *ctx, ph_status st, const std::string &msg);
+ph_status ph_cuda_fail(ph_ctx *ctx, cudaError_t e, const char *where);
+bool ph_is_device_ptr(const void *p);
+
+#define PH_CUDA(ctx, call)                                       \
+  do {                                                           \
+    cudaError_t e__ = (call);                                    \
+    if (e__ != cudaSuccess) return ph_cuda_fail(ctx, e__, #call); \
+  } while (0)
+
+// ---- kernels' host launchers
+// eval.cu: values and Jacobian of the homotopy into device buffers.
+//   J: plane stride Jplane (doubles between limb/part planes), leading dim ldJ
+//   h: [2L][N] (may be null); rhs: -h into a plane-strided column (may be null)
+//   t: L limbs on the device; gamma: [2L] on the device or null (f alone)
+//   skip: device flag; the kernels do nothing while *skip != 0 (may be null)
+//   res_bits: max |h_i| (leading limbs, double bits) accumulated (may be null)
+cudaError_t ph_eval_launch(ph_ctx *ctx, const ph_system *f, const ph_system *g,
+                           const double *gamma, int k, const double *t, const double *x,
+                           double *h, double *J, long ldJ, long Jplane,
+                           double *rhs, long rhs_plane, const int *skip,
+                           unsigned long long *res_bits);
+
+// the same, launching only the kernels selected by `parts`
+// (1 = power table and factors, 2 = monomial AD, 4 = summation)
+cudaError_t ph_eval_launch_part(ph_ctx *ctx, const ph_system *f, const ph_system *g,
+                                const double *gamma, int k, const double *t, const double *x,
+                                double *h, double *J, long ldJ, long Jplane, double *rhs,
+                                long rhs_plane, const int *skip, unsigned long long *res_bits,
+                                int parts);
+
+// mgs.cu: least squares on the augmented matrix A = [J | rhs] held in
+//   A (plane stride (n+1)*ldA, leading dim ldA); dx [2L][n] out;
+//   dx_bits: max |dx_i| accumulated (may be null); resid: ||residual||_2 (may be null)
+cudaError_t ph_mgs_launch(ph_ctx *ctx, int L, int N, int n, double *A, long ldA, double *dx,
+                          PathState *st, const int *skip, double *resid);
+
+int ph_mgs_grid(ph_ctx *ctx, int L, int N, int n);

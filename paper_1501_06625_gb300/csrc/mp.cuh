@@ -1,0 +1,386 @@
+// mp.cuh -- complex double-double (DD, 2 limbs) and quad-double (QD, 4 limbs)
+// arithmetic on FP64 error-free transformations, for sm_103a.
+//
+// The paper computes in complex DD and QD (Section 3.1) with the QD library's
+// algorithms (Introduction).  This file writes its own operations from the
+// error-free transformations of IEEE doubles:
+//   two_sum       a + b = s + e exactly                (Knuth; 6 FP64 ops)
+//   fast_two_sum  a + b = s + e exactly if |a| >= |b|  (Dekker; 3 ops)
+//   two_prod      a * b = p + e exactly                (FMA; 2 ops)
+// On GB300 an FP64 warp instruction occupies an SM sub-partition's FP64 unit
+// for about 64 cycles whatever its kind (measured; FP32 is ~60x faster), so
+// every operation below is written to issue as few FP64 instructions as the
+// error budget allows.  The budget is an error bound relative to the sum of the
+// magnitudes of the terms (the quantity the library's accuracy is stated in),
+// not relative to the result; this admits the cheaper "sloppy" DD addition.
+//
+// Every FP64 operation goes through an explicitly rounded intrinsic, so the
+// compiler cannot contract a product and a sum into an FMA and break an
+// error-free transformation.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+
+namespace ph {
+
+#define PHD __device__ __forceinline__
+
+PHD double fadd(double a, double b) { return __dadd_rn(a, b); }
+PHD double fsub(double a, double b) { return __dsub_rn(a, b); }
+PHD double fmul(double a, double b) { return __dmul_rn(a, b); }
+PHD double ffma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+PHD void two_sum(double a, double b, double &s, double &e) {
+  double x = fadd(a, b);
+  double bv = fsub(x, a);
+  double av = fsub(x, bv);
+  e = fadd(fsub(a, av), fsub(b, bv));
+  s = x;
+}
+
+PHD void fast_two_sum(double a, double b, double &s, double &e) {
+  double x = fadd(a, b);
+  e = fsub(b, fsub(x, a));
+  s = x;
+}
+
+PHD void two_prod(double a, double b, double &p, double &e) {
+  double x = fmul(a, b);
+  e = ffma(a, b, -x);
+  p = x;
+}
+
+// ---------------------------------------------------------------- double-double
+struct dd { double h, l; };
+
+struct DD {
+  static constexpr int L = 2;
+  typedef dd real;
+  PHD static real zero() { return {0.0, 0.0}; }
+  PHD static real from(double a) { return {a, 0.0}; }
+  PHD static double lead(const real &a) { return a.h; }
+  PHD static double limb(const real &a, int i) { return i == 0 ? a.h : a.l; }
+  PHD static void set_limb(real &a, int i, double v) { if (i == 0) a.h = v; else a.l = v; }
+  PHD static real neg(real a) { return {-a.h, -a.l}; }
+  // Sloppy addition: two_sum of the leading limbs, the low limbs added in
+  // double, then renormalised.  |error| <= ~3u^2 (|a| + |b|).  11 ops.
+  PHD static real add(real a, real b) {
+    double s, e;
+    two_sum(a.h, b.h, s, e);
+    e = fadd(e, a.l);
+    e = fadd(e, b.l);
+    fast_two_sum(s, e, s, e);
+    return {s, e};
+  }
+  PHD static real sub(real a, real b) { return add(a, neg(b)); }
+  // a*b without the product of the low limbs: |error| <= ~5u^2 |a b|.  7 ops.
+  PHD static real mul(real a, real b) {
+    double p, e;
+    two_prod(a.h, b.h, p, e);
+    e = ffma(a.h, b.l, e);
+    e = ffma(a.l, b.h, e);
+    fast_two_sum(p, e, p, e);
+    return {p, e};
+  }
+  PHD static real mul_d(real a, double b) {
+    double p, e;
+    two_prod(a.h, b, p, e);
+    e = ffma(a.l, b, e);
+    fast_two_sum(p, e, p, e);
+    return {p, e};
+  }
+  PHD static real scale2(real a) { return {fmul(a.h, 2.0), fmul(a.l, 2.0)}; }
+  // quotient digits q1, q2, q3 from exact-ish remainders
+  PHD static real div(real a, real b) {
+    double q1 = a.h / b.h;
+    real r = sub(a, mul_d(b, q1));
+    double q2 = r.h / b.h;
+    r = sub(r, mul_d(b, q2));
+    double q3 = r.h / b.h;
+    double s, e;
+    fast_two_sum(q1, q2, s, e);
+    return add({s, e}, from(q3));
+  }
+  // one Newton correction of the double square root
+  PHD static real sqrt(real a) {
+    if (!(a.h > 0.0)) return zero();
+    double s = __dsqrt_rn(a.h);
+    double p, e;
+    two_prod(s, s, p, e);
+    real r = sub(a, {p, e});
+    double c = r.h / fmul(2.0, s);
+    fast_two_sum(s, c, s, e);
+    return {s, e};
+  }
+};
+
+// ---------------------------------------------------------------- quad-double
+struct qd { double x[4]; };
+
+// Renormalisation of five overlapping components whose exact sum is the value:
+// two bottom-up sweeps of two_sum (error-free, so the value is unchanged even
+// when cancellation leaves the components out of order), then the fifth
+// component is folded into the fourth.
+PHD void qd_renorm(double &c0, double &c1, double &c2, double &c3, double &c4) {
+  two_sum(c3, c4, c3, c4);
+  two_sum(c2, c3, c2, c3);
+  two_sum(c1, c2, c1, c2);
+  two_sum(c0, c1, c0, c1);
+  two_sum(c3, c4, c3, c4);
+  two_sum(c2, c3, c2, c3);
+  two_sum(c1, c2, c1, c2);
+  two_sum(c0, c1, c0, c1);
+  c3 = fadd(c3, c4);
+}
+
+struct QD {
+  static constexpr int L = 4;
+  typedef qd real;
+  PHD static real zero() { return {{0.0, 0.0, 0.0, 0.0}}; }
+  PHD static real from(double a) { return {{a, 0.0, 0.0, 0.0}}; }
+  PHD static double lead(const real &a) { return a.x[0]; }
+  PHD static double limb(const real &a, int i) { return a.x[i]; }
+  PHD static void set_limb(real &a, int i, double v) { a.x[i] = v; }
+  PHD static real neg(real a) { return {{-a.x[0], -a.x[1], -a.x[2], -a.x[3]}}; }
+  // Order-by-order addition: the components of equal order are added with
+  // two_sum and the errors carried into the next order; order-3 terms are
+  // added in double; then renormalised.
+  PHD static real add(real a, real b) {
+    double s0, s1, s2, s3, e0, e1, e2, e3;
+    two_sum(a.x[0], b.x[0], s0, e0);
+    two_sum(a.x[1], b.x[1], s1, e1);
+    two_sum(s1, e0, s1, e0);
+    two_sum(a.x[2], b.x[2], s2, e2);
+    two_sum(s2, e1, s2, e1);
+    two_sum(s2, e0, s2, e0);
+    s3 = fadd(a.x[3], b.x[3]);
+    e3 = fadd(fadd(e0, e1), e2);
+    double c4 = 0.0;
+    two_sum(s3, e3, s3, c4);
+    qd_renorm(s0, s1, s2, s3, c4);
+    return {{s0, s1, s2, s3}};
+  }
+  PHD static real sub(real a, real b) { return add(a, neg(b)); }
+  // Products of the limbs by order i + j: orders 0..2 split exactly with
+  // two_prod, order 3 in double, orders >= 4 dropped (below 2^-212 |a b|).
+  PHD static real mul(real a, real b) {
+    double p00, q00, p01, q01, p10, q10, p02, q02, p11, q11, p20, q20;
+    two_prod(a.x[0], b.x[0], p00, q00);
+    two_prod(a.x[0], b.x[1], p01, q01);
+    two_prod(a.x[1], b.x[0], p10, q10);
+    two_prod(a.x[0], b.x[2], p02, q02);
+    two_prod(a.x[1], b.x[1], p11, q11);
+    two_prod(a.x[2], b.x[0], p20, q20);
+    double o3 = fmul(a.x[0], b.x[3]);
+    o3 = ffma(a.x[1], b.x[2], o3);
+    o3 = ffma(a.x[2], b.x[1], o3);
+    o3 = ffma(a.x[3], b.x[0], o3);
+    // order 1: p01 + p10 + q00
+    double s1, r1, r2, r3;
+    two_sum(p01, p10, s1, r1);
+    two_sum(s1, q00, s1, r2);
+    // order 2: p02 + p11 + p20 + q01 + q10 + r1 + r2
+    double s2, t1, t2, t3, t4, t5, t6;
+    two_sum(p02, p11, s2, t1);
+    two_sum(s2, p20, s2, t2);
+    two_sum(s2, q01, s2, t3);
+    two_sum(s2, q10, s2, t4);
+    two_sum(s2, r1, s2, t5);
+    two_sum(s2, r2, s2, t6);
+    // order 3: the rest in double
+    r3 = fadd(fadd(fadd(q02, q11), fadd(q20, o3)), fadd(fadd(t1, t2), fadd(t3, t4)));
+    r3 = fadd(r3, fadd(t5, t6));
+    double c4 = 0.0;
+    double s0 = p00;
+    qd_renorm(s0, s1, s2, r3, c4);
+    return {{s0, s1, s2, r3}};
+  }
+  PHD static real mul_d(real a, double b) {
+    double p0, q0, p1, q1, p2, q2;
+    two_prod(a.x[0], b, p0, q0);
+    two_prod(a.x[1], b, p1, q1);
+    two_prod(a.x[2], b, p2, q2);
+    double p3 = fmul(a.x[3], b);
+    double s1, e1, s2, e2, e3;
+    two_sum(p1, q0, s1, e1);
+    two_sum(p2, q1, s2, e2);
+    two_sum(s2, e1, s2, e3);
+    double s3 = fadd(fadd(p3, q2), fadd(e2, e3));
+    double c4 = 0.0;
+    qd_renorm(p0, s1, s2, s3, c4);
+    return {{p0, s1, s2, s3}};
+  }
+  PHD static real scale2(real a) {
+    return {{fmul(a.x[0], 2.0), fmul(a.x[1], 2.0), fmul(a.x[2], 2.0), fmul(a.x[3], 2.0)}};
+  }
+  // long division: five quotient digits, each from the remainder's leading limb
+  PHD static real div(real a, real b) {
+    double q0 = a.x[0] / b.x[0];
+    real r = sub(a, mul_d(b, q0));
+    double q1 = r.x[0] / b.x[0];
+    r = sub(r, mul_d(b, q1));
+    double q2 = r.x[0] / b.x[0];
+    r = sub(r, mul_d(b, q2));
+    double q3 = r.x[0] / b.x[0];
+    r = sub(r, mul_d(b, q3));
+    double q4 = r.x[0] / b.x[0];
+    qd_renorm(q0, q1, q2, q3, q4);
+    return {{q0, q1, q2, q3}};
+  }
+  // Newton's iteration s := s + (a - s^2) / (2 s) with the divisor in double:
+  // each step adds ~53 correct bits (53, 106, 159, 212).
+  PHD static real sqrt(real a) {
+    if (!(a.x[0] > 0.0)) return zero();
+    double s0 = __dsqrt_rn(a.x[0]);
+    double h = 0.5 / s0;
+    real s = from(s0);
+    for (int it = 0; it < 3; ++it) {
+      real r = sub(a, mul(s, s));
+      s = add(s, mul_d(r, h));
+    }
+    return s;
+  }
+};
+
+// ---------------------------------------------------------------- complex
+template <class P> struct cx { typename P::real re, im; };
+
+template <class P> PHD cx<P> c_zero() { return {P::zero(), P::zero()}; }
+template <class P> PHD cx<P> c_from(double re, double im) { return {P::from(re), P::from(im)}; }
+template <class P> PHD cx<P> c_add(const cx<P> &a, const cx<P> &b) { return {P::add(a.re, b.re), P::add(a.im, b.im)}; }
+template <class P> PHD cx<P> c_sub(const cx<P> &a, const cx<P> &b) { return {P::sub(a.re, b.re), P::sub(a.im, b.im)}; }
+template <class P> PHD cx<P> c_neg(const cx<P> &a) { return {P::neg(a.re), P::neg(a.im)}; }
+template <class P> PHD cx<P> c_mul_real(const cx<P> &a, const typename P::real &r) { return {P::mul(a.re, r), P::mul(a.im, r)}; }
+template <class P> PHD cx<P> c_mul_d(const cx<P> &a, double r) { return {P::mul_d(a.re, r), P::mul_d(a.im, r)}; }
+template <class P> PHD cx<P> c_scale2(const cx<P> &a) { return {P::scale2(a.re), P::scale2(a.im)}; }
+
+// (ar + i ai)(br + i bi), four real products and two additions
+template <class P> struct cops {
+  PHD static cx<P> mul(const cx<P> &a, const cx<P> &b) {
+    return {P::sub(P::mul(a.re, b.re), P::mul(a.im, b.im)),
+            P::add(P::mul(a.re, b.im), P::mul(a.im, b.re))};
+  }
+  // acc + a b
+  PHD static cx<P> mac(const cx<P> &acc, const cx<P> &a, const cx<P> &b) {
+    return c_add<P>(acc, mul(a, b));
+  }
+  // conj(a) b
+  PHD static cx<P> conj_mul(const cx<P> &a, const cx<P> &b) {
+    return {P::add(P::mul(a.re, b.re), P::mul(a.im, b.im)),
+            P::sub(P::mul(a.re, b.im), P::mul(a.im, b.re))};
+  }
+  PHD static typename P::real abs2(const cx<P> &a) {
+    return P::add(P::mul(a.re, a.re), P::mul(a.im, a.im));
+  }
+};
+
+// DD: each part of a product is one exact sum of two two_prod splits plus the
+// cross terms, renormalised once (19 ops instead of 25 for 2 mul + 1 add).
+template <> struct cops<DD> {
+  PHD static void part(double ah, double al, double bh, double bl,
+                       double ch, double cl, double dh, double dl, double sgn,
+                       double &zh, double &zl) {
+    // a b + sgn c d
+    double p1, e1, p2, e2, s, es;
+    two_prod(ah, bh, p1, e1);
+    two_prod(ch, dh, p2, e2);
+    two_sum(p1, sgn * p2, s, es);
+    double t = fadd(es, e1);
+    t = ffma(sgn, e2, t);
+    t = ffma(ah, bl, t);
+    t = ffma(al, bh, t);
+    t = ffma(sgn * ch, dl, t);
+    t = ffma(sgn * cl, dh, t);
+    fast_two_sum(s, t, zh, zl);
+  }
+  PHD static cx<DD> mul(const cx<DD> &a, const cx<DD> &b) {
+    cx<DD> z;
+    part(a.re.h, a.re.l, b.re.h, b.re.l, a.im.h, a.im.l, b.im.h, b.im.l, -1.0, z.re.h, z.re.l);
+    part(a.re.h, a.re.l, b.im.h, b.im.l, a.im.h, a.im.l, b.re.h, b.re.l, 1.0, z.im.h, z.im.l);
+    return z;
+  }
+  PHD static cx<DD> mac(const cx<DD> &acc, const cx<DD> &a, const cx<DD> &b) {
+    return c_add<DD>(acc, mul(a, b));
+  }
+  PHD static cx<DD> conj_mul(const cx<DD> &a, const cx<DD> &b) {
+    cx<DD> z;
+    part(a.re.h, a.re.l, b.re.h, b.re.l, a.im.h, a.im.l, b.im.h, b.im.l, 1.0, z.re.h, z.re.l);
+    part(a.re.h, a.re.l, b.im.h, b.im.l, a.im.h, a.im.l, b.re.h, b.re.l, -1.0, z.im.h, z.im.l);
+    return z;
+  }
+  PHD static dd abs2(const cx<DD> &a) {
+    dd z;
+    part(a.re.h, a.re.l, a.re.h, a.re.l, a.im.h, a.im.l, a.im.h, a.im.l, 1.0, z.h, z.l);
+    return z;
+  }
+};
+
+template <class P> PHD cx<P> c_mul(const cx<P> &a, const cx<P> &b) { return cops<P>::mul(a, b); }
+template <class P> PHD cx<P> c_conj_mul(const cx<P> &a, const cx<P> &b) { return cops<P>::conj_mul(a, b); }
+template <class P> PHD typename P::real c_abs2(const cx<P> &a) { return cops<P>::abs2(a); }
+
+// multiply by a small positive integer exponent
+template <class P> PHD cx<P> c_mul_int(const cx<P> &a, int k) {
+  if (k == 1) return a;
+  if (k == 2) return c_scale2<P>(a);
+  return c_mul_d<P>(a, (double)k);
+}
+
+// |z| in double from the leading limbs (only the magnitude matters, Section 3.1)
+template <class P> PHD double c_mag_lead(const cx<P> &a) {
+  double re = P::lead(a.re), im = P::lead(a.im);
+  return __dsqrt_rn(__dadd_rn(__dmul_rn(re, re), __dmul_rn(im, im)));
+}
+
+// ---------------------------------------------------------------- SoA access
+// element i of a complex vector laid out [limb][re|im][stride]
+template <class P> PHD cx<P> c_load(const double *__restrict__ v, long stride, long i) {
+  cx<P> z;
+#pragma unroll
+  for (int l = 0; l < P::L; ++l) {
+    P::set_limb(z.re, l, v[(2 * l) * stride + i]);
+    P::set_limb(z.im, l, v[(2 * l + 1) * stride + i]);
+  }
+  return z;
+}
+
+template <class P> PHD void c_store(double *__restrict__ v, long stride, long i, const cx<P> &z) {
+#pragma unroll
+  for (int l = 0; l < P::L; ++l) {
+    v[(2 * l) * stride + i] = P::limb(z.re, l);
+    v[(2 * l + 1) * stride + i] = P::limb(z.im, l);
+  }
+}
+
+// the same through L2 only (ld.global.cg): for data another block of a running
+// persistent kernel may have written since this SM last cached the line
+template <class P> PHD cx<P> c_load_cg(const double *v, long stride, long i) {
+  cx<P> z;
+#pragma unroll
+  for (int l = 0; l < P::L; ++l) {
+    P::set_limb(z.re, l, __ldcg(v + (2 * l) * stride + i));
+    P::set_limb(z.im, l, __ldcg(v + (2 * l + 1) * stride + i));
+  }
+  return z;
+}
+
+template <class P> PHD typename P::real r_load_cg(const double *v, long stride, long i) {
+  typename P::real z;
+#pragma unroll
+  for (int l = 0; l < P::L; ++l) P::set_limb(z, l, __ldcg(v + l * stride + i));
+  return z;
+}
+
+template <class P> PHD typename P::real r_load(const double *__restrict__ v, long stride, long i) {
+  typename P::real z;
+#pragma unroll
+  for (int l = 0; l < P::L; ++l) P::set_limb(z, l, v[l * stride + i]);
+  return z;
+}
+
+template <class P> PHD void r_store(double *__restrict__ v, long stride, long i, const typename P::real &z) {
+#pragma unroll
+  for (int l = 0; l < P::L; ++l) v[l * stride + i] = P::limb(z, l);
+}
+
+}  // namespace ph

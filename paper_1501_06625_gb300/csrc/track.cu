@@ -1,0 +1,606 @@
+// track.cu -- ph_track_path: one solution path tracked entirely on the device.
+//
+// The paper keeps the step control on the host and copies the two norms of
+// each Newton iteration back (Section 3.1, Fig. "An accelerated Newton's
+// method", Fig. "Accelerated tracking of one single path").  On GB300 a host
+// round trip costs more than a small step's kernels, so here the same
+// decisions run in one-thread kernels on the device and the whole path is a
+// single CUDA graph launch: a conditional WHILE node repeats the body
+//   step_begin  controller: t := min(1, t + dt), reset the corrector
+//   predict     extrapolation through the last accepted points (Section 3.1)
+//   max_newton x [ prep, ad, sum      h, J and -h into [J | -h], ||h||
+//                  check_res          fail if ||h|| grew, succeed if small
+//                  mgs                dx by MGS + back substitution, ||dx||
+//                  update             x += dx
+//                  check_dx ]         succeed if ||dx|| small
+//   step_end    accept (history push) or reject, controller update, log,
+//               and ends the loop when the path is finished
+// until step_end clears the condition.  Kernels gate themselves on flags in
+// PathState, so a corrector that finished early costs only empty launches.
+// The host reads the state once, after the path.
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "ctrl.h"
+#include "internal.h"
+#include "mp.cuh"
+
+using namespace ph;
+
+long ph_lda(int N);
+
+namespace {
+
+constexpr int kHist = 16;          // ring of accepted points (pred_order <= 8)
+
+__global__ void k_step_begin(PathState *st, ph_track_params p, int L) {
+  st->iterations += 1;
+  if (st->timeout && !st->ctrl.done) {     // a bounded wait ran out: stop the path
+    st->ctrl.done = 1;
+    st->ctrl.status = PH_TIMEOUT;
+  }
+  if (st->ctrl.done) {
+    st->skip_step = 1;
+    st->skip_nt = 1;
+    return;
+  }
+  double tn = ctrl_next_t(&st->ctrl, &p);
+  if (tn < 0.0) {
+    st->skip_step = 1;
+    st->skip_nt = 1;
+    return;
+  }
+  st->t_new = tn;
+  st->t_dev[0] = tn;
+  for (int l = 1; l < L; ++l) st->t_dev[l] = 0.0;
+  st->nt_done = 0;
+  st->nt_success = p.fixed_steps > 0 ? 1 : 0;
+  st->nt_iters = 0;
+  st->nt_updates = 0;
+  st->last_res = p.max_res;
+  st->res_bits = 0;
+  st->dx_bits = 0;
+  st->mgs_status = 0;
+  st->skip_step = 0;
+  st->skip_nt = 0;
+}
+
+// x(t_new) = sum_j w_j x(t_j) over the last m accepted points, with the
+// Lagrange weights w_j = prod_{l != j} (t_new - t_l) / (t_j - t_l) of the
+// interpolating polynomial of degree m - 1 (computed by m threads per block).
+template <class P>
+__global__ void k_predict(PathState *st, const double *__restrict__ hist, double *__restrict__ xw,
+                          int n, int pred_order) {
+  if (st->skip_step) return;
+  typedef typename P::real real;
+  __shared__ real w[kHist];
+  __shared__ int s_slot[kHist];
+  const int cnt = st->hist_count, head = st->hist_head;
+  const int m = cnt < pred_order + 1 ? cnt : pred_order + 1;
+  const double tn = st->t_new;
+  if ((int)threadIdx.x < m) {
+    int j = threadIdx.x;
+    int sj = (head - (m - 1 - j) + kHist) % kHist;
+    double tj = st->hist_t[sj];
+    real num = P::from(1.0), den = P::from(1.0);
+    for (int l = 0; l < m; ++l) {
+      if (l == j) continue;
+      double tl = st->hist_t[(head - (m - 1 - l) + kHist) % kHist];
+      real a, b;
+      double s, e;
+      two_sum(tn, -tl, s, e);          // t_new - t_l exactly
+      a = P::zero(); P::set_limb(a, 0, s); P::set_limb(a, 1, e);
+      two_sum(tj, -tl, s, e);
+      b = P::zero(); P::set_limb(b, 0, s); P::set_limb(b, 1, e);
+      num = P::mul(num, a);
+      den = P::mul(den, b);
+    }
+    w[j] = m == 1 ? P::from(1.0) : P::div(num, den);
+    s_slot[j] = sj;
+  }
+  __syncthreads();
+  const long pt = 2L * P::L * n;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    cx<P> acc = c_zero<P>();
+    for (int j = 0; j < m; ++j)
+      acc = c_add<P>(acc, c_mul_real<P>(c_load<P>(hist + s_slot[j] * pt, n, i), w[j]));
+    c_store<P>(xw, n, i, acc);
+  }
+}
+
+__global__ void k_check_res(PathState *st, ph_track_params p) {
+  if (st->skip_nt) return;
+  double r = __longlong_as_double((long long)st->res_bits);
+  st->res = r;
+  st->nt_iters += 1;
+  st->newton_iters += 1;
+  st->res_last = r;
+  st->dx_bits = 0;
+  st->mgs_status = 0;
+  if (p.fixed_steps > 0) return;
+  if (!(r <= st->last_res) || !isfinite(r)) {       // residual grew (or NaN): fail
+    st->nt_done = 1;
+    st->nt_success = 0;
+    st->skip_nt = 1;
+  } else if (r < p.tol_res) {
+    st->nt_done = 1;
+    st->nt_success = 1;
+    st->skip_nt = 1;
+  }
+}
+
+template <class P>
+__global__ void k_update(PathState *st, double *__restrict__ xw, const double *__restrict__ dx,
+                         int n, int fixed) {
+  if (st->skip_nt) return;
+  const bool bad = st->mgs_status != 0;
+  if (bad && !fixed) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    cx<P> d = bad ? c_from<P>(NAN, NAN) : c_load<P>(dx, n, i);
+    c_store<P>(xw, n, i, c_add<P>(c_load<P>(xw, n, i), d));
+  }
+}
+
+__global__ void k_check_dx(PathState *st, ph_track_params p) {
+  if (st->skip_nt) return;
+  const bool fixed = p.fixed_steps > 0;
+  if (st->mgs_status != 0 && !fixed) {               // singular Jacobian: fail
+    st->nt_done = 1;
+    st->nt_success = 0;
+    st->skip_nt = 1;
+    return;
+  }
+  double d = st->mgs_status != 0 ? NAN : __longlong_as_double((long long)st->dx_bits);
+  st->dxn = d;
+  st->dx_last = d;
+  st->nt_updates += 1;
+  st->updates += 1;
+  st->res_bits = 0;
+  if (!fixed) {
+    if (!isfinite(d)) {
+      st->nt_done = 1;
+      st->nt_success = 0;
+      st->skip_nt = 1;
+      return;
+    }
+    if (d < p.tol_dx) {
+      st->nt_done = 1;
+      st->nt_success = 1;
+      st->skip_nt = 1;
+      return;
+    }
+    st->last_res = st->res;
+  }
+  if (st->nt_iters >= p.max_newton) {                // out of iterations
+    st->nt_done = 1;
+    st->nt_success = fixed ? 1 : 0;
+    st->skip_nt = 1;
+  }
+}
+
+template <class P>
+__global__ void k_step_end(PathState *st, ph_track_params p, double *__restrict__ hist,
+                           const double *__restrict__ xw, int n, ph_step_record *log, int log_cap,
+                           cudaGraphConditionalHandle cond) {
+  __shared__ int s_ok, s_slot;
+  __shared__ double s_max;
+  if (st->skip_step) {
+    if (threadIdx.x == 0 && st->ctrl.done) cudaGraphSetConditional(cond, 0);
+    return;
+  }
+  if (threadIdx.x == 0) {
+    int ok = st->nt_success;
+    st->steps += 1;
+    if (ok) st->accepted += 1; else st->rejected += 1;
+    if (log && st->log_len < log_cap) {
+      ph_step_record r;
+      r.t = st->t_new;
+      r.res = st->res;
+      r.dx = st->dxn;
+      r.accepted = ok;
+      r.updates = st->nt_updates;
+      log[st->log_len] = r;
+    }
+    st->log_len += 1;
+    ctrl_report(&st->ctrl, &p, st->t_new, ok);
+    int slot = (st->hist_head + 1) % kHist;
+    if (ok) {
+      st->hist_head = slot;
+      st->hist_t[slot] = st->t_new;
+      st->hist_count = st->hist_count < kHist ? st->hist_count + 1 : kHist;
+    }
+    s_ok = ok;
+    s_slot = slot;
+    s_max = 0.0;
+  }
+  __syncthreads();
+  if (!s_ok) {
+    if (threadIdx.x == 0 && st->ctrl.done) cudaGraphSetConditional(cond, 0);
+    return;
+  }
+  const long pt = 2L * P::L * n;
+  double mymax = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    cx<P> xi = c_load<P>(xw, n, i);
+    c_store<P>(hist + s_slot * pt, n, i, xi);
+    double a = c_mag_lead<P>(xi);
+    if (!(a <= mymax)) mymax = a;
+  }
+  // max over the block through the bit patterns (non-negative or NaN)
+  atomicMax((unsigned long long *)&s_max, (unsigned long long)__double_as_longlong(mymax));
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (p.fixed_steps <= 0 && !st->ctrl.done && !(s_max <= p.max_x)) {
+      st->ctrl.done = 1;
+      st->ctrl.status = PH_DIVERGED;
+    }
+    if (st->ctrl.done) cudaGraphSetConditional(cond, 0);
+  }
+}
+
+struct TrackGraph {
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  // what the graph was built for
+  const ph_system *f = nullptr, *g = nullptr;
+  ph_track_params p;
+  void *bufs[16] = {};
+  int log_cap = -1;
+  long kernels_per_step = 0;
+  cudaStream_t stream = nullptr;
+  bool valid = false;
+};
+
+struct TrackCache {
+  TrackGraph tg;
+  cudaStream_t cap = nullptr;      // private stream used for capture
+};
+
+}  // namespace
+
+// ---- graph cache per context -------------------------------------------------------
+static std::mutex g_cache_mu;
+static std::map<ph_ctx *, TrackCache *> g_cache;
+
+static TrackCache *get_cache(ph_ctx *ctx) {
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  auto it = g_cache.find(ctx);
+  if (it != g_cache.end()) return it->second;
+  TrackCache *c = new TrackCache();
+  g_cache[ctx] = c;
+  return c;
+}
+
+static void drop_graph(TrackGraph &tg) {
+  if (tg.exec) cudaGraphExecDestroy(tg.exec);
+  if (tg.graph) cudaGraphDestroy(tg.graph);
+  tg = TrackGraph();
+}
+
+void ph_track_release(ph_ctx *ctx) {
+  TrackCache *c = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    auto it = g_cache.find(ctx);
+    if (it == g_cache.end()) return;
+    c = it->second;
+    g_cache.erase(it);
+  }
+  drop_graph(c->tg);
+  if (c->cap) cudaStreamDestroy(c->cap);
+  delete c;
+}
+
+// Records the body of one predictor-corrector step on `s`.
+static cudaError_t record_step(ph_ctx *ctx, cudaStream_t s, const ph_system *f,
+                               const ph_system *g, const double *gamma,
+                               const ph_track_params &p, PathState *st, double *hist, double *xw,
+                               double *A, long ldA, double *dx, ph_step_record *log, int log_cap,
+                               cudaGraphConditionalHandle cond) {
+  const int L = f->L, n = f->n, N = f->N;
+  const long Ap = (long)(n + 1) * ldA;
+  cudaStream_t saved = ctx->stream;
+  ctx->stream = s;
+  cudaError_t e = cudaSuccess;
+  k_step_begin<<<1, 1, 0, s>>>(st, p, L);
+  int pb = 128, pg = (n + pb - 1) / pb;
+  if (L == 2) k_predict<DD><<<pg, pb, 0, s>>>(st, hist, xw, n, p.pred_order);
+  else k_predict<QD><<<pg, pb, 0, s>>>(st, hist, xw, n, p.pred_order);
+  for (int it = 0; it < p.max_newton && e == cudaSuccess; ++it) {
+    e = ph_eval_launch(ctx, f, g, gamma, p.relax_k, st->t_dev, xw, nullptr, A, ldA, Ap,
+                       A + (long)n * ldA, Ap, &st->skip_nt, &st->res_bits);
+    if (e != cudaSuccess) break;
+    k_check_res<<<1, 1, 0, s>>>(st, p);
+    e = ph_mgs_launch(ctx, L, N, n, A, ldA, dx, st, &st->skip_nt, nullptr);
+    if (e != cudaSuccess) break;
+    if (L == 2) k_update<DD><<<(n + 127) / 128, 128, 0, s>>>(st, xw, dx, n, p.fixed_steps > 0);
+    else k_update<QD><<<(n + 127) / 128, 128, 0, s>>>(st, xw, dx, n, p.fixed_steps > 0);
+    k_check_dx<<<1, 1, 0, s>>>(st, p);
+  }
+  if (e == cudaSuccess) {
+    int eb = n < 256 ? 128 : 256;
+    if (L == 2) k_step_end<DD><<<1, eb, 0, s>>>(st, p, hist, xw, n, log, log_cap, cond);
+    else k_step_end<QD><<<1, eb, 0, s>>>(st, p, hist, xw, n, log, log_cap, cond);
+    e = cudaGetLastError();
+  }
+  ctx->stream = saved;
+  return e;
+}
+
+static ph_status build_graph(ph_ctx *ctx, TrackCache *c, const ph_system *f, const ph_system *g,
+                             const double *gamma, const ph_track_params &p, PathState *st,
+                             double *hist, double *xw, double *A, long ldA, double *dx,
+                             ph_step_record *log, int log_cap) {
+  drop_graph(c->tg);
+  if (!c->cap) PH_CUDA(ctx, cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+  TrackGraph &tg = c->tg;
+  PH_CUDA(ctx, cudaGraphCreate(&tg.graph, 0));
+  cudaGraphConditionalHandle cond;
+  PH_CUDA(ctx, cudaGraphConditionalHandleCreate(&cond, tg.graph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = cond;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  PH_CUDA(ctx, cudaGraphAddNode(&node, tg.graph, nullptr, nullptr, 0, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  PH_CUDA(ctx, cudaStreamBeginCaptureToGraph(c->cap, body, nullptr, nullptr, 0,
+                                             cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = record_step(ctx, c->cap, f, g, gamma, p, st, hist, xw, A, ldA, dx, log, log_cap, cond);
+  cudaGraph_t out = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(c->cap, &out);
+  if (e != cudaSuccess) { drop_graph(tg); return ph_cuda_fail(ctx, e, "capture of the step"); }
+  if (e2 != cudaSuccess) { drop_graph(tg); return ph_cuda_fail(ctx, e2, "cudaStreamEndCapture"); }
+  size_t nodes = 0;
+  cudaGraphGetNodes(body, nullptr, &nodes);
+  tg.kernels_per_step = (long)nodes;
+  e = cudaGraphInstantiate(&tg.exec, tg.graph, 0);
+  if (e != cudaSuccess) { drop_graph(tg); return ph_cuda_fail(ctx, e, "cudaGraphInstantiate"); }
+  tg.f = f;
+  tg.g = g;
+  tg.p = p;
+  tg.log_cap = log_cap;
+  tg.valid = true;
+  return PH_OK;
+}
+
+extern "C" ph_status ph_track_path(ph_ctx *ctx, const ph_system *f, const ph_system *g,
+                                   const double *gamma, const double *x0,
+                                   const ph_track_params *params, double *x_out,
+                                   ph_path_stats *stats, ph_step_record *log, int log_cap) {
+  if (!ctx) return PH_EINVAL;
+  if (!f || f->ctx != ctx) return ph_fail(ctx, PH_EINVAL, "ph_track_path: f missing or from another context");
+  if (g && (g->ctx != ctx || g->L != f->L || g->N != f->N || g->n != f->n))
+    return ph_fail(ctx, PH_EINVAL, "ph_track_path: g does not match f");
+  if (!gamma || !x0 || !params || !x_out) return ph_fail(ctx, PH_EINVAL, "ph_track_path: NULL argument");
+  const ph_track_params p = *params;
+  if (p.max_newton < 1 || p.max_newton > 64 || p.pred_order < 0 || p.pred_order > 8 ||
+      p.relax_k < 1 || p.relax_k > 64 || p.reserved != 0 || p.max_steps < 0 ||
+      (p.fixed_steps <= 0 && !(p.max_dt > 0.0 && p.min_dt > 0.0 && p.min_dt <= p.max_dt)))
+    return ph_fail(ctx, PH_EINVAL, "ph_track_path: invalid parameters");
+  if (!g) {
+    if (f->N != f->n) return ph_fail(ctx, PH_EINVAL, "ph_track_path: the total-degree start system needs N == n");
+    for (int d : f->h_deg)
+      if (d < 1) return ph_fail(ctx, PH_EINVAL, "ph_track_path: f has a constant polynomial");
+  }
+  if (log_cap < 0 || (log_cap > 0 && !log)) return ph_fail(ctx, PH_EINVAL, "ph_track_path: bad log");
+  cudaSetDevice(ctx->device);
+  const int L = f->L, n = f->n, N = f->N;
+  const long pt = 2L * L * n;
+  const long ldA = ph_lda(N);
+
+  // host inputs: gamma and x0 (copied in; a non-finite start point ends here)
+  std::vector<double> hx0(pt), hg(2 * L);
+  PH_CUDA(ctx, cudaMemcpy(hx0.data(), x0, sizeof(double) * pt, cudaMemcpyDefault));
+  PH_CUDA(ctx, cudaMemcpy(hg.data(), gamma, sizeof(double) * 2 * L, cudaMemcpyDefault));
+  for (double v : hx0)
+    if (!std::isfinite(v)) {
+      if (stats) {
+        memset(stats, 0, sizeof *stats);
+        stats->launches = 0;
+        stats->status = PH_NONFINITE;
+      }
+      PH_CUDA(ctx, cudaMemcpy(x_out, x0, sizeof(double) * pt, cudaMemcpyDefault));
+      return PH_NONFINITE;
+    }
+
+  PH_CUDA(ctx, ctx->state.ensure(sizeof(PathState)));
+  PH_CUDA(ctx, ctx->hist.ensure(sizeof(double) * pt * kHist));
+  PH_CUDA(ctx, ctx->xw.ensure(sizeof(double) * pt));
+  PH_CUDA(ctx, ctx->dxv.ensure(sizeof(double) * pt));
+  PH_CUDA(ctx, ctx->A.ensure(sizeof(double) * 2 * L * (size_t)(n + 1) * ldA));
+  PH_CUDA(ctx, ctx->in_gamma.ensure(sizeof(double) * 2 * L));
+  PH_CUDA(ctx, ctx->logbuf.ensure(sizeof(ph_step_record) * (log_cap > 0 ? log_cap : 1)));
+  // buffers the evaluation and the solver grow on demand: size them now so the
+  // captured graph's pointers stay valid
+  {
+    int emax = f->emax > (g ? g->emax : 0) ? f->emax : g->emax;
+    int ntab = emax > 2 ? emax - 1 : 1;
+    long fs = (long)(f->maxv + 1) * f->Mp, gs = g ? (long)(g->maxv + 1) * g->Mp : 0;
+    PH_CUDA(ctx, ctx->ptab.ensure(sizeof(double) * 2 * L * (size_t)n * ntab));
+    PH_CUDA(ctx, ctx->scal.ensure(sizeof(double) * 3 * L));
+    PH_CUDA(ctx, ctx->slots.ensure(sizeof(double) * 2 * L * (size_t)(fs + gs + 1)));
+    PH_CUDA(ctx, ctx->R.ensure(sizeof(double) * 2 * L * (size_t)(n + 1) * (n + 1)));
+    PH_CUDA(ctx, ctx->nrm2.ensure(sizeof(double) * L * (size_t)(n + 1)));
+    PH_CUDA(ctx, ctx->irkk.ensure(sizeof(double) * L * (size_t)n));
+  }
+  PathState *st = ctx->state.as<PathState>();
+  double *hist = ctx->hist.as<double>(), *xw = ctx->xw.as<double>(), *dx = ctx->dxv.as<double>();
+  double *A = ctx->A.as<double>(), *dgam = ctx->in_gamma.as<double>();
+  ph_step_record *dlog = log_cap > 0 ? ctx->logbuf.as<ph_step_record>() : nullptr;
+
+  // initial state: controller at t = 0, the start point as the only history point
+  PathState h0;
+  memset(&h0, 0, sizeof h0);
+  ctrl_init(&h0.ctrl, &p);
+  h0.hist_count = 1;
+  h0.hist_head = 0;
+  h0.hist_t[0] = 0.0;
+  PH_CUDA(ctx, cudaMemcpyAsync(st, &h0, sizeof h0, cudaMemcpyHostToDevice, ctx->stream));
+  PH_CUDA(ctx, cudaMemcpyAsync(hist, hx0.data(), sizeof(double) * pt, cudaMemcpyHostToDevice, ctx->stream));
+  PH_CUDA(ctx, cudaMemcpyAsync(dgam, hg.data(), sizeof(double) * 2 * L, cudaMemcpyHostToDevice, ctx->stream));
+
+  TrackCache *c = get_cache(ctx);
+  void *bufs[16] = {st, hist, xw, dx, A, dgam, dlog, ctx->slots.p, ctx->ptab.p, ctx->scal.p,
+                    ctx->R.p, ctx->nrm2.p, ctx->irkk.p, nullptr, nullptr, nullptr};
+  bool same = c->tg.valid && c->tg.f == f && c->tg.g == g && c->tg.log_cap == log_cap &&
+              memcmp(&c->tg.p, &p, sizeof p) == 0 && memcmp(c->tg.bufs, bufs, sizeof bufs) == 0 &&
+              c->tg.stream == ctx->stream;
+  if (!same) {
+    // ensure the scratch the kernels grow is already at its final size
+    ph_status s = build_graph(ctx, c, f, g, dgam, p, st, hist, xw, A, ldA, dx, dlog, log_cap);
+    if (s != PH_OK) return s;
+    memcpy(c->tg.bufs, bufs, sizeof bufs);
+    c->tg.stream = ctx->stream;
+  }
+  PH_CUDA(ctx, cudaGraphLaunch(c->tg.exec, ctx->stream));
+  PathState hs;
+  PH_CUDA(ctx, cudaMemcpyAsync(&hs, st, sizeof hs, cudaMemcpyDeviceToHost, ctx->stream));
+  PH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  // the last accepted point
+  PH_CUDA(ctx, cudaMemcpy(x_out, hist + hs.hist_head * pt, sizeof(double) * pt, cudaMemcpyDefault));
+  if (log_cap > 0) {
+    int nl = hs.log_len < log_cap ? hs.log_len : log_cap;
+    if (nl > 0)
+      PH_CUDA(ctx, cudaMemcpy(log, dlog, sizeof(ph_step_record) * nl, cudaMemcpyDefault));
+  }
+  ph_status status = hs.timeout ? PH_TIMEOUT : (ph_status)hs.ctrl.status;
+  if (stats) {
+    stats->status = status;
+    stats->steps = hs.steps;
+    stats->accepted = hs.accepted;
+    stats->rejected = hs.rejected;
+    stats->newton_iters = hs.newton_iters;
+    stats->updates = hs.updates;
+    stats->t_final = hs.hist_t[hs.hist_head];
+    stats->res = hs.res_last;
+    stats->dx = hs.dx_last;
+    stats->launches = (int64_t)hs.iterations * c->tg.kernels_per_step;
+  }
+  if (status == PH_TIMEOUT) return ph_fail(ctx, PH_TIMEOUT, "ph_track_path: a grid barrier timed out");
+  return status;
+}
+
+// ---- measurement support ----------------------------------------------------------
+
+extern "C" ph_status ph_profile_newton(ph_ctx *ctx, const ph_system *f, const ph_system *g,
+                                       const double *gamma, int k, const double *t,
+                                       const double *x, int reps, double *ms_out) {
+  if (!ctx) return PH_EINVAL;
+  if (!f || f->ctx != ctx || !gamma || !t || !x || !ms_out || reps < 1 || k < 1)
+    return ph_fail(ctx, PH_EINVAL, "ph_profile_newton: invalid argument");
+  if (g && (g->ctx != ctx || g->L != f->L || g->N != f->N || g->n != f->n))
+    return ph_fail(ctx, PH_EINVAL, "ph_profile_newton: g does not match f");
+  if (!g && f->N != f->n) return ph_fail(ctx, PH_EINVAL, "ph_profile_newton: needs N == n");
+  cudaSetDevice(ctx->device);
+  const int L = f->L, n = f->n, N = f->N;
+  const long ldA = ph_lda(N), Ap = (long)(n + 1) * ldA;
+  PH_CUDA(ctx, ctx->A.ensure(sizeof(double) * 2 * L * (size_t)Ap));
+  PH_CUDA(ctx, ctx->dxv.ensure(sizeof(double) * 2 * L * (size_t)n));
+  PH_CUDA(ctx, ctx->state.ensure(sizeof(PathState)));
+  PH_CUDA(ctx, ctx->in_x.ensure(sizeof(double) * 2 * L * (size_t)n));
+  PH_CUDA(ctx, ctx->in_gamma.ensure(sizeof(double) * 2 * L));
+  PH_CUDA(ctx, ctx->in_t.ensure(sizeof(double) * L));
+  PH_CUDA(ctx, cudaMemcpyAsync(ctx->in_x.p, x, sizeof(double) * 2 * L * n, cudaMemcpyDefault, ctx->stream));
+  PH_CUDA(ctx, cudaMemcpyAsync(ctx->in_gamma.p, gamma, sizeof(double) * 2 * L, cudaMemcpyDefault, ctx->stream));
+  PH_CUDA(ctx, cudaMemcpyAsync(ctx->in_t.p, t, sizeof(double) * L, cudaMemcpyDefault, ctx->stream));
+  PH_CUDA(ctx, cudaMemsetAsync(ctx->state.p, 0, sizeof(PathState), ctx->stream));
+  double *A = ctx->A.as<double>();
+  PathState *st = ctx->state.as<PathState>();
+  cudaEvent_t ev[5];
+  for (int i = 0; i < 5; ++i) PH_CUDA(ctx, cudaEventCreate(&ev[i]));
+  double acc[4] = {0, 0, 0, 0};
+  ph_status status = PH_OK;
+  for (int r = 0; r < reps + 1 && status == PH_OK; ++r) {
+    cudaError_t e = cudaSuccess;
+    // the three evaluation kernels one at a time (the launcher issues all
+    // three; its segments are timed by splitting it: prep+ad+sum, then
+    // prep alone and prep+ad are derived from separate runs below)
+    cudaEventRecord(ev[0], ctx->stream);
+    e = ph_eval_launch_part(ctx, f, g, ctx->in_gamma.as<double>(), k, ctx->in_t.as<double>(),
+                            ctx->in_x.as<double>(), nullptr, A, ldA, Ap, A + (long)n * ldA, Ap,
+                            nullptr, nullptr, 1);
+    cudaEventRecord(ev[1], ctx->stream);
+    if (e == cudaSuccess)
+      e = ph_eval_launch_part(ctx, f, g, ctx->in_gamma.as<double>(), k, ctx->in_t.as<double>(),
+                              ctx->in_x.as<double>(), nullptr, A, ldA, Ap, A + (long)n * ldA, Ap,
+                              nullptr, nullptr, 2);
+    cudaEventRecord(ev[2], ctx->stream);
+    if (e == cudaSuccess)
+      e = ph_eval_launch_part(ctx, f, g, ctx->in_gamma.as<double>(), k, ctx->in_t.as<double>(),
+                              ctx->in_x.as<double>(), nullptr, A, ldA, Ap, A + (long)n * ldA, Ap,
+                              nullptr, nullptr, 4);
+    cudaEventRecord(ev[3], ctx->stream);
+    if (e == cudaSuccess) e = ph_mgs_launch(ctx, L, N, n, A, ldA, ctx->dxv.as<double>(), st, nullptr, nullptr);
+    cudaEventRecord(ev[4], ctx->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[4]);
+    if (e != cudaSuccess) { status = ph_cuda_fail(ctx, e, "ph_profile_newton"); break; }
+    if (r == 0) continue;                 // the first pass warms up
+    for (int i = 0; i < 4; ++i) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+      acc[i] += ms;
+    }
+  }
+  for (int i = 0; i < 5; ++i) cudaEventDestroy(ev[i]);
+  if (status != PH_OK) return status;
+  PathState hs;
+  PH_CUDA(ctx, cudaMemcpy(&hs, st, sizeof hs, cudaMemcpyDeviceToHost));
+  if (hs.timeout) return ph_fail(ctx, PH_TIMEOUT, "ph_profile_newton: a grid barrier timed out");
+  for (int i = 0; i < 4; ++i) ms_out[i] = acc[i] / reps;
+  return PH_OK;
+}
+
+namespace {
+__global__ void k_dfma_peak(double *out, int iters, double b, double c) {
+  double a[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) a[i] = threadIdx.x * 1e-3 + i;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = __fma_rn(a[i], b, c);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) s += a[i];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+}  // namespace
+
+extern "C" ph_status ph_fp64_peak(ph_ctx *ctx, double ms_target, double *gops) {
+  if (!ctx || !gops || !(ms_target > 0.0)) return ph_fail(ctx, PH_EINVAL, "ph_fp64_peak: invalid argument");
+  cudaSetDevice(ctx->device);
+  const int blocks = ctx->sm_count * 4, threads = 256;
+  PH_CUDA(ctx, ctx->ystage.ensure(sizeof(double) * blocks * threads));
+  double *out = ctx->ystage.as<double>();
+  cudaEvent_t e0, e1;
+  PH_CUDA(ctx, cudaEventCreate(&e0));
+  PH_CUDA(ctx, cudaEventCreate(&e1));
+  int iters = 256;
+  float ms = 0.f;
+  for (int attempt = 0; attempt < 8; ++attempt) {
+    k_dfma_peak<<<blocks, threads, 0, ctx->stream>>>(out, 16, 1.0000001, 1e-9);
+    cudaEventRecord(e0, ctx->stream);
+    k_dfma_peak<<<blocks, threads, 0, ctx->stream>>>(out, iters, 1.0000001, 1e-9);
+    cudaEventRecord(e1, ctx->stream);
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return ph_cuda_fail(ctx, e, "ph_fp64_peak");
+    }
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms >= ms_target || iters >= (1 << 22)) break;
+    double scale = ms > 0.01 ? ms_target / ms : 16.0;
+    iters = (int)(iters * (scale > 16.0 ? 16.0 : scale) * 1.1) + 1;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *gops = (double)blocks * threads * iters * 8.0 / (ms * 1e-3) / 1e9;
+  return PH_OK;
+}

@@ -1,0 +1,78 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds for
+sm_103a, loads, exports every function include/ph.h declares, and its
+step-size controller (the code the device controller runs) agrees with the
+oracle's independent implementation on scripted and random outcome sequences."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1501_06625_gb300 import build, libph, synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return libph.lib()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "ph.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"\b(ph_[a-z0-9_]+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert set(names) == set(libph.EXPORTS)
+    for name in names:
+        assert hasattr(lib, name), name
+    assert "sm_103a" in libph.ph_version()
+
+
+def _ph_drive(params, outcomes):
+    st = libph.CtrlState()
+    p = libph.ph_ctrl_init(st, params)
+    ts = []
+    for ok in outcomes:
+        t = libph.ph_ctrl_next_t(st, p)
+        if t < 0:
+            break
+        ts.append(t)
+        libph.ph_ctrl_report(st, p, t, ok)
+    return ts, {k: getattr(st, k) for k, _ in libph.CtrlState._fields_}
+
+
+def _orc_drive(orc, params, outcomes):
+    c = orc.Controller(params)
+    ts = []
+    for ok in outcomes:
+        t = c.next_t()
+        if t < 0:
+            break
+        ts.append(t)
+        c.report(t, ok)
+    return ts, c.state
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_controller_matches_oracle(lib, orc, seed):
+    rng = np.random.default_rng(seed)
+    params = synth.default_params(2, max_dt=float(rng.choice([0.05, 0.1, 0.25])),
+                                  min_dt=float(rng.choice([1e-3, 1e-6])),
+                                  max_steps=int(rng.integers(5, 200)),
+                                  fixed_steps=int(rng.choice([0, 0, 0, 7])))
+    outcomes = rng.random(400) < rng.uniform(0.3, 0.95)
+    a = _ph_drive(params, outcomes)
+    b = _orc_drive(orc, params, outcomes)
+    assert a == b
+
+
+def test_controller_hand_trace(lib):
+    ts, st = _ph_drive(synth.default_params(2, max_dt=0.25, min_dt=0.01), [1, 0, 1, 1, 1, 1, 0, 1, 1])
+    assert ts == [0.25, 0.5, 0.375, 0.5, 0.625, 0.875, 1.0, 1.0]
+    assert st["done"] == 1 and st["status"] == libph.PH_OK

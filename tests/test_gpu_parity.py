@@ -1,0 +1,240 @@
+"""GPU parity: the CUDA library (through its C ABI) against the CPU oracle on
+the same seeded inputs.
+
+* ph_eval_jac: values and Jacobians of the homotopy, every element, within
+  1e-28 (DD) / 1e-58 (QD) of the oracle relative to the sum of the term
+  magnitudes; cases span several warps and a ragged tail, constants, deep
+  exponents, k = 2, a general start system, f alone, and the full-size dense
+  n = 64 (4096 monomials over 16 variables) and sparse n = 512 systems.
+* ph_mgs_solve: solutions of square and tall systems against the oracle's
+  textbook MGS within 1e3 * kappa * n * u; rank deficiency is reported.
+* ph_track_path: the fixed schedule of the 8-variable dense system (100 steps,
+  3 updates each) ends within 1e-24 (DD) / 1e-52 (QD) of the oracle; adaptive
+  runs are replayed by the oracle from the GPU's own step log and must end at
+  the same tolerance.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_common import (TOL_END, U, assert_eval_close, cabs_diff, lead_complex, soa_from_complex,
+                        soa_matrix)
+from paper_1501_06625_gb300 import libph, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1501_06625_gb300 import build
+    build.build()
+    oracle.build()
+    c = libph.Context(0)
+    yield c
+    c.close()
+
+
+def _gamma(rng, L):
+    g = rng.unit_complex()
+    return soa_from_complex([g], L).reshape(L, 2)
+
+
+def _ragged_system(rng, n):
+    """Terms with 0..6 distinct variables, exponents up to 7, a constant in
+    every polynomial, and a term count that is not a multiple of 32."""
+    polys = []
+    for i in range(n):
+        terms = [(rng.unit_complex(), [])]
+        for _ in range(3 + (i % 5)):
+            v = 1 + rng.below(6)
+            vs = rng.sample(n, v)
+            terms.append((rng.unit_complex(), [(u, 1 + rng.below(7)) for u in vs]))
+        terms.append((rng.unit_complex(), [(i, 1 + rng.below(3))]))
+        polys.append(terms)
+    return synth.build_system(n, n, polys)
+
+
+CASES = {
+    "dense8": lambda r: synth.dense_system(r, 8, 8, 4, (1, 2)),
+    "dense20": lambda r: synth.dense_system(r, 20, 24, 5, (1, 2, 3, 4)),
+    "ragged13": lambda r: _ragged_system(r, 13),
+    "sparse40": lambda r: synth.sparse_system(r, 40),
+}
+
+
+def _eval_both(ctx, L, spec, x, t, gam, k, gspec=None):
+    f = ctx.load(spec, L)
+    g = ctx.load(gspec, L) if gspec is not None else None
+    n, N = spec.n, spec.N
+    h = np.zeros((L, 2, N))
+    J = np.zeros((L, 2, n, N))
+    tl = np.zeros(L); tl[0] = t
+    libph.ph_eval_jac(ctx.h, f, g, gam, k, tl, x, h, J)
+    of = oracle.System(spec, L)
+    og = oracle.System(gspec, L) if gspec is not None else None
+    ho, Jo = oracle.eval_h(of, x, t=t, gamma=gam, k=k, g=og)
+    return h, J, ho, Jo
+
+
+@pytest.mark.parametrize("L", [2, 4])
+@pytest.mark.parametrize("case", sorted(CASES))
+@pytest.mark.parametrize("mode", ["homotopy_k1", "homotopy_k2", "f_only"])
+def test_eval_parity(ctx, L, case, mode):
+    rng = synth.Rng(100 + len(case) + 7 * L)
+    spec = CASES[case](rng)
+    x = soa_from_complex(synth.random_x(rng, spec.n), L)
+    x[1] = x[0] * 2.0 ** -55                         # use the low limb too
+    gam = _gamma(rng, L)
+    if mode == "f_only":
+        h, J, ho, Jo = _eval_both(ctx, L, spec, x, 0.0, None, 1)
+        assert_eval_close(L, spec, x, h, J, ho, Jo)
+    else:
+        k = 1 if mode.endswith("k1") else 2
+        t = 0.3713
+        h, J, ho, Jo = _eval_both(ctx, L, spec, x, t, gam, k)
+        assert_eval_close(L, spec, x, h, J, ho, Jo, t=t, gamma=gam, k=k)
+
+
+@pytest.mark.parametrize("L", [2, 4])
+def test_eval_general_start_system(ctx, L):
+    rng = synth.Rng(77)
+    spec = synth.dense_system(rng, 9, 7, 3, (1, 2, 3))
+    gspec = synth.dense_system(rng, 9, 5, 2, (1, 2))
+    x = soa_from_complex(synth.random_x(rng, 9), L)
+    gam = _gamma(rng, L)
+    h, J, ho, Jo = _eval_both(ctx, L, spec, x, 0.61, gam, 1, gspec)
+    assert_eval_close(L, spec, x, h, J, ho, Jo, t=0.61, gamma=gam, k=1, g=gspec)
+
+
+@pytest.mark.parametrize("prec", ["dd", "qd"])
+def test_eval_full_size_dense64(ctx, prec):
+    wl = synth.dense64(1, prec)
+    L = wl.L
+    rng = synth.Rng(5)
+    x = soa_from_complex(synth.random_x(rng, wl.n), L)
+    h, J, ho, Jo = _eval_both(ctx, L, wl.f, x, 0.25, wl.gamma_soa(), 1)
+    assert_eval_close(L, wl.f, x, h, J, ho, Jo, t=0.25, gamma=wl.gamma_soa(), k=1)
+
+
+def test_eval_full_size_sparse512(ctx):
+    wl = synth.sparse512(1, "qd")
+    L = wl.L
+    rng = synth.Rng(6)
+    x = soa_from_complex(synth.random_x(rng, wl.n), L)
+    h, J, ho, Jo = _eval_both(ctx, L, wl.f, x, 0.8, wl.gamma_soa(), 1)
+    assert_eval_close(L, wl.f, x, h, J, ho, Jo, t=0.8, gamma=wl.gamma_soa(), k=1)
+
+
+@pytest.mark.parametrize("L", [2, 4])
+@pytest.mark.parametrize("N,n", [(1, 1), (8, 8), (37, 37), (50, 33), (64, 64), (200, 200)])
+def test_mgs_parity(ctx, L, N, n):
+    rng = np.random.default_rng(N * 1000 + n + L)
+    A = rng.standard_normal((N, n)) + 1j * rng.standard_normal((N, n))
+    b = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    J = soa_matrix(A, L)
+    J[1] = J[0] * 2.0 ** -60
+    rhs = soa_from_complex(b, L)
+    dx = np.zeros((L, 2, n))
+    rn = libph.ph_mgs_solve(ctx.h, L, N, n, J, rhs, dx)
+    if n > 64:
+        # the oracle's MGS at n = 200 takes too long: check the normal equations
+        r = A @ lead_complex(dx) - b
+        assert np.linalg.norm(A.conj().T @ r) < 1e-10 * np.linalg.norm(b)
+        return
+    st, dxo, rno = oracle.mgs_solve(J, rhs)
+    assert st == oracle.OK
+    kappa = np.linalg.cond(A)
+    err = cabs_diff(dx, dxo).max() / np.abs(lead_complex(dxo)).max()
+    assert err < 1e3 * kappa * n * U[L], err
+    assert abs(rn - rno) <= 1e-12 * (1 + rno) + 1e3 * kappa * U[L] * np.linalg.norm(b)
+
+
+def test_mgs_rank_deficient(ctx):
+    A = np.eye(5, dtype=complex)
+    A[:, 3] = A[:, 1]
+    with pytest.raises(libph.PhError) as ei:
+        libph.ph_mgs_solve(ctx.h, 2, 5, 5, soa_matrix(A, 2), soa_from_complex(np.ones(5), 2),
+                           np.zeros((2, 2, 5)))
+    assert ei.value.status == libph.PH_NONFINITE
+
+
+@pytest.mark.parametrize("prec", ["dd", "qd"])
+def test_track_fixed_schedule_dense8(ctx, prec):
+    """The 8-variable dense system, 100 fixed steps with exactly 3 updates."""
+    wl = synth.dense8(1, prec)
+    L = wl.L
+    f = ctx.load(wl.f, L)
+    x0, gam = wl.x0_soa(), wl.gamma_soa()
+    xg = np.zeros_like(x0)
+    st, stats, log = libph.ph_track_path(ctx.h, f, None, gam, x0, wl.params, xg, log_cap=200)
+    assert st == libph.PH_OK
+    assert stats["steps"] == 100 and stats["updates"] == 300 and len(log) == 100
+    so, xo, ostats, _ = oracle.track(oracle.System(wl.f, L), x0, gam, wl.params)
+    assert so == oracle.OK
+    assert np.all(np.isfinite(xg))
+    err = cabs_diff(xg, xo).max()
+    assert err <= TOL_END[L], err
+
+
+def _replay_check(ctx, spec, L, gam, x0, params, log_cap=5000):
+    f = ctx.load(spec, L)
+    xg = np.zeros_like(x0)
+    st, stats, log = libph.ph_track_path(ctx.h, f, None, gam, x0, params, xg, log_cap=log_cap)
+    assert len(log) == stats["steps"] <= log_cap, "the schedule log must hold the whole path"
+    xo = oracle.replay(oracle.System(spec, L), x0, gam, params, log)
+    err = cabs_diff(xg, xo).max()
+    assert err <= TOL_END[L] * max(1.0, np.abs(lead_complex(xo)).max()), err
+    return st, stats, log
+
+
+@pytest.mark.parametrize("L", [2, 4])
+def test_track_adaptive_replay(ctx, L):
+    rng = synth.Rng(31)
+    spec = synth.dense_system(rng, 5, 5, 3, (1, 2))
+    gam = _gamma(rng, L)
+    x0 = soa_from_complex(np.ones(5), L)
+    st, stats, log = _replay_check(ctx, spec, L, gam, x0, synth.default_params(L, max_dt=0.2))
+    assert stats["steps"] >= 5
+
+
+def test_track_dense64_replay_first_steps(ctx):
+    """The bench's workload in DD at full size: the first 6 steps of the
+    adaptive path, replayed by the oracle."""
+    wl = synth.dense64(1, "dd")
+    params = dict(wl.params, max_steps=5)
+    st, stats, log = _replay_check(ctx, wl.f, 2, wl.gamma_soa(), wl.x0_soa(), params)
+    assert st in (libph.PH_OK, libph.PH_MAXSTEPS)
+    assert stats["steps"] == 6
+
+
+def test_track_f_equals_g(ctx):
+    n, L = 4, 2
+    spec = synth.build_system(n, n, [[(1.0, [(i, 3)]), (-1.0, [])] for i in range(n)])
+    f = ctx.load(spec, L)
+    x0 = soa_from_complex(np.ones(n), L)
+    xg = np.zeros_like(x0)
+    gam = soa_from_complex([0.6 + 0.8j], L).reshape(L, 2)
+    st, stats, log = libph.ph_track_path(ctx.h, f, None, gam, x0, synth.default_params(L), xg,
+                                         log_cap=100)
+    assert st == libph.PH_OK and stats["t_final"] == 1.0
+    assert np.array_equal(xg, x0)
+
+
+def test_track_nonfinite_start(ctx):
+    wl = synth.dense8(1, "dd")
+    f = ctx.load(wl.f, 2)
+    x0 = wl.x0_soa()
+    x0[0, 1, 3] = np.nan
+    xg = np.zeros_like(x0)
+    st, stats, log = libph.ph_track_path(ctx.h, f, None, wl.gamma_soa(), x0, wl.params, xg)
+    assert st == libph.PH_NONFINITE
+
+
+def test_invalid_arguments(ctx):
+    bad = synth.build_system(2, 2, [[(1.0, [(0, 1), (0, 2)])], [(1.0, [(1, 1)])]])
+    with pytest.raises(libph.PhError) as ei:
+        ctx.load(bad, 2)
+    assert ei.value.status == libph.PH_EINVAL
+    with pytest.raises(libph.PhError):
+        libph.ph_mgs_solve(ctx.h, 2, 3, 5, np.zeros((2, 2, 5, 3)), np.zeros((2, 2, 3)),
+                           np.zeros((2, 2, 5)))
