@@ -5,7 +5,7 @@
 // Three kernels per evaluation:
 //  k_prep  power table x_j^e (e < largest exponent) and the homotopy factors
 //          t^k and gamma (1-t)^k;
-//  k_ad    one thread per monomial c x^a with v distinct variables: the common
+//  k_ad    one thread (or T lanes, k_ad_split) per monomial c x^a with v distinct variables: the common
 //          factor CF = prod x_j^{a_j - 1} from the power table is folded into
 //          the coefficient, then the Speelpenning product of the v variables is
 //          differentiated in the reverse mode (forward prefix products, backward
@@ -88,9 +88,9 @@ __global__ void __launch_bounds__(128) k_ad(int M, int Mp, const int32_t *__rest
                                             const double *__restrict__ coeff,
                                             const double *__restrict__ ptab, int n, int maxv,
                                             double *__restrict__ slots, long nslots,
-                                            const int *__restrict__ skip) {
+                                            const int *__restrict__ skip, int s0) {
   if (skip && *skip) return;
-  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  int s = s0 + blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= M) return;
   const long pl = 2L * P::L * n;
   const int v = nv[s];
@@ -114,6 +114,104 @@ __global__ void __launch_bounds__(128) k_ad(int M, int Mp, const int32_t *__rest
     if (p > 0) {
       cx<P> xj = c_load<P>(ptab, n, vidx[(long)p * Mp + s]);
       suf = (p == v - 1) ? xj : c_mul<P>(suf, xj);
+    }
+  }
+}
+
+template <class P>
+PHD cx<P> shfl_up_c(const cx<P> &a, int d, int width) {
+  cx<P> z;
+#pragma unroll
+  for (int l = 0; l < P::L; ++l) {
+    P::set_limb(z.re, l, __shfl_up_sync(0xffffffffu, P::limb(a.re, l), d, width));
+    P::set_limb(z.im, l, __shfl_up_sync(0xffffffffu, P::limb(a.im, l), d, width));
+  }
+  return z;
+}
+
+// T lanes per monomial (T = 2, 4, 8): lane q owns a chunk of c = ceil(v/T)
+// consecutive variable positions.  Each lane forms its chunk's factor
+// B_q = (c if q = 0) * CF_q * prod_{own} x_j, where CF_q collects the common
+// factor x_j^{a_j - 1} of its own positions; shuffle scans give the products
+// of the other chunks' factors to the left and right, and the lane finishes
+// its positions with a local reverse sweep:
+//   d/dx_j = a_j * (left * right * CF_q) * prod_{own l != j} x_l.
+// The critical path drops from ~3v to ~3v/T + 2 log2(T) + 2 complex products.
+template <class P, int T>
+__global__ void __launch_bounds__(128) k_ad_split(int s0, int s1, int Mp,
+                                                  const int32_t *__restrict__ nv,
+                                                  const int32_t *__restrict__ vidx,
+                                                  const int32_t *__restrict__ vexp,
+                                                  const double *__restrict__ coeff,
+                                                  const double *__restrict__ ptab, int n, int maxv,
+                                                  double *__restrict__ slots, long nslots,
+                                                  const int *__restrict__ skip) {
+  if (skip && *skip) return;
+  const long gt = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = s0 + (int)(gt / T);
+  const int q = (int)(gt % T);
+  const bool active = s < s1;                    // every lane still joins the shuffles
+  const long pl = 2L * P::L * n;
+  const int v = active ? nv[s] : 0;
+  const int c = (v + T - 1) / T;
+  const int p0 = q * c < v ? q * c : v;
+  const int p1 = p0 + c < v ? p0 + c : v;
+  const cx<P> one = c_from<P>(1.0, 0.0);
+  // the chunk's common factor and full factor
+  cx<P> cf = one;
+  bool has_cf = false;
+  for (int p = p0; p < p1; ++p) {
+    int a = vexp[(long)p * Mp + s];
+    if (a >= 2) {
+      cx<P> w = c_load<P>(ptab + (a - 2) * pl, n, vidx[(long)p * Mp + s]);
+      cf = has_cf ? c_mul<P>(cf, w) : w;
+      has_cf = true;
+    }
+  }
+  cx<P> B = (active && q == 0) ? c_load<P>(coeff, Mp, s) : one;
+  bool b_one = !(active && q == 0);
+  if (has_cf) { B = b_one ? cf : c_mul<P>(B, cf); b_one = false; }
+  for (int p = p0; p < p1; ++p) {
+    cx<P> xj = c_load<P>(ptab, n, vidx[(long)p * Mp + s]);
+    B = b_one ? xj : c_mul<P>(B, xj);
+    b_one = false;
+  }
+  // inclusive prefix and suffix products over the T lanes of this monomial
+  cx<P> I = B, S = B;
+#pragma unroll
+  for (int d = 1; d < T; d <<= 1) {
+    cx<P> y = shfl_up_c<P>(I, d, T);
+    if (q >= d) I = c_mul<P>(y, I);
+    cx<P> z = shfl_down_c<P>(S, d, T);
+    if (q + d < T) S = c_mul<P>(S, z);
+  }
+  cx<P> left = shfl_up_c<P>(I, 1, T);
+  cx<P> right = shfl_down_c<P>(S, 1, T);
+  if (!active) return;
+  if (q == T - 1) c_store<P>(slots, nslots, (long)maxv * Mp + s, I);   // the value
+  if (p0 == p1) return;
+  // outer factor of this chunk
+  cx<P> outer;
+  bool o_one = true;
+  if (q > 0) { outer = left; o_one = false; }
+  if (q < T - 1) { outer = o_one ? right : c_mul<P>(outer, right); o_one = false; }
+  if (has_cf) { outer = o_one ? cf : c_mul<P>(outer, cf); o_one = false; }
+  if (o_one) outer = one;
+  // local reverse sweep over the chunk (prefixes parked in the slots)
+  cx<P> pre = outer;
+  for (int p = p0; p < p1; ++p) {
+    c_store<P>(slots, nslots, (long)p * Mp + s, pre);
+    if (p + 1 < p1) pre = c_mul<P>(pre, c_load<P>(ptab, n, vidx[(long)p * Mp + s]));
+  }
+  cx<P> suf = one;
+  for (int p = p1 - 1; p >= p0; --p) {
+    cx<P> d = c_load<P>(slots, nslots, (long)p * Mp + s);
+    if (p < p1 - 1) d = c_mul<P>(d, suf);
+    d = c_mul_int<P>(d, vexp[(long)p * Mp + s]);
+    c_store<P>(slots, nslots, (long)p * Mp + s, d);
+    if (p > p0) {
+      cx<P> xj = c_load<P>(ptab, n, vidx[(long)p * Mp + s]);
+      suf = (p == p1 - 1) ? xj : c_mul<P>(suf, xj);
     }
   }
 }
@@ -176,6 +274,33 @@ __global__ void __launch_bounds__(256) k_sum(
   }
 }
 
+// One launch per bucket of monomials sharing a lane count (the buckets are
+// contiguous because the terms are sorted by their number of variables).
+template <class P>
+void ad_launch(const ph_system *sy, const double *ptab, int n, double *slots, long ns,
+               const int *skip, cudaStream_t st) {
+  for (const ph_system::Bucket &b : sy->buckets) {
+    const long threads = (long)(b.s1 - b.s0) * b.lanes;
+    const unsigned grid = (unsigned)((threads + 127) / 128);
+    const int32_t *nv = sy->nv.as<int32_t>(), *vi = sy->vidx.as<int32_t>(), *ve = sy->vexp.as<int32_t>();
+    const double *co = sy->coeff.as<double>();
+    switch (b.lanes) {
+      case 1:
+        k_ad<P><<<grid, 128, 0, st>>>(b.s1, sy->Mp, nv, vi, ve, co, ptab, n, sy->maxv, slots, ns, skip, b.s0);
+        break;
+      case 2:
+        k_ad_split<P, 2><<<grid, 128, 0, st>>>(b.s0, b.s1, sy->Mp, nv, vi, ve, co, ptab, n, sy->maxv, slots, ns, skip);
+        break;
+      case 4:
+        k_ad_split<P, 4><<<grid, 128, 0, st>>>(b.s0, b.s1, sy->Mp, nv, vi, ve, co, ptab, n, sy->maxv, slots, ns, skip);
+        break;
+      default:
+        k_ad_split<P, 8><<<grid, 128, 0, st>>>(b.s0, b.s1, sy->Mp, nv, vi, ve, co, ptab, n, sy->maxv, slots, ns, skip);
+        break;
+    }
+  }
+}
+
 template <class P>
 cudaError_t eval_impl(ph_ctx *ctx, const ph_system *f, const ph_system *g, const double *gamma,
                       int k, const double *t, const double *x, double *h, double *J, long ldJ,
@@ -197,16 +322,10 @@ cudaError_t eval_impl(ph_ctx *ctx, const ph_system *f, const ph_system *g, const
 
   if (parts & 1)
     k_prep<P><<<(n + 127) / 128, 128, 0, st>>>(x, n, emax, ptab, t, gamma, k, scal, skip);
-  if ((parts & 2) && f->M > 0)
-    k_ad<P><<<(f->M + 127) / 128, 128, 0, st>>>(f->M, f->Mp, f->nv.as<int32_t>(),
-                                                f->vidx.as<int32_t>(), f->vexp.as<int32_t>(),
-                                                f->coeff.as<double>(), ptab, n, f->maxv, fslots,
-                                                fs, skip);
-  if ((parts & 2) && g && g->M > 0)
-    k_ad<P><<<(g->M + 127) / 128, 128, 0, st>>>(g->M, g->Mp, g->nv.as<int32_t>(),
-                                                g->vidx.as<int32_t>(), g->vexp.as<int32_t>(),
-                                                g->coeff.as<double>(), ptab, n, g->maxv, gslots,
-                                                gs, skip);
+  if (parts & 2) {
+    if (f->M > 0) ad_launch<P>(f, ptab, n, fslots, fs, skip, st);
+    if (g && g->M > 0) ad_launch<P>(g, ptab, n, gslots, gs, skip, st);
+  }
   constexpr int G = 8;
   const long threads = (long)f->nout * G;
   if (parts & 4)

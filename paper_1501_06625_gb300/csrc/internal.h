@@ -74,6 +74,9 @@ struct ph_system {
   int nout = 0;                 // n*N Jacobian entries + N values
   int max_contrib = 0;          // longest summation list
   DevBuf poly, nv, vidx, vexp, coeff, deg, out_ptr, out_slot;
+  // sorted terms [s0, s1) differentiated with `lanes` threads per monomial
+  struct Bucket { int s0, s1, lanes; };
+  std::vector<Bucket> buckets;
   std::vector<int> h_deg;
   int max_deg = 0;
 };

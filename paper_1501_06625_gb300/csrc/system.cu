@@ -17,6 +17,15 @@
 
 #include "internal.h"
 
+// threads per monomial of v variables: enough that each lane's chunk has
+// about four positions (the reverse sweep dominates), at most 8
+int ph_ad_lanes(int v) {
+  if (v <= 5) return 1;
+  if (v <= 10) return 2;
+  if (v <= 24) return 4;
+  return 8;
+}
+
 static ph_status upload(ph_system *s, DevBuf &b, const void *src, size_t bytes) {
   cudaError_t e = b.ensure(bytes);
   if (e != cudaSuccess) return ph_cuda_fail(s->ctx, e, "cudaMalloc (system)");
@@ -106,6 +115,16 @@ extern "C" ph_status ph_system_load(ph_ctx *ctx, ph_prec prec, int N, int n,
       vexp[(size_t)p * Mp + sidx] = var_exp[var_ptr[k] + p];
     }
     for (int c = 0; c < 2 * L; ++c) co[(size_t)c * Mp + sidx] = coeff[(size_t)c * M + k];
+  }
+
+  // lanes per monomial by its number of variables (terms are sorted, so each
+  // lane count covers a contiguous range)
+  for (int sidx = 0; sidx < M;) {
+    int lanes = ph_ad_lanes(nv[sidx]);
+    int e = sidx;
+    while (e < M && ph_ad_lanes(nv[e]) == lanes) ++e;
+    s->buckets.push_back({sidx, e, lanes});
+    sidx = e;
   }
 
   // summation lists
