@@ -168,7 +168,8 @@ __global__ void __launch_bounds__(128) k_ad_split(int s0, int s1, int Mp,
       has_cf = true;
     }
   }
-  cx<P> B = (active && q == 0) ? c_load<P>(coeff, Mp, s) : one;
+  const cx<P> c0 = (active && q == 0) ? c_load<P>(coeff, Mp, s) : one;
+  cx<P> B = c0;
   bool b_one = !(active && q == 0);
   if (has_cf) { B = b_one ? cf : c_mul<P>(B, cf); b_one = false; }
   for (int p = p0; p < p1; ++p) {
@@ -190,10 +191,11 @@ __global__ void __launch_bounds__(128) k_ad_split(int s0, int s1, int Mp,
   if (!active) return;
   if (q == T - 1) c_store<P>(slots, nslots, (long)maxv * Mp + s, I);   // the value
   if (p0 == p1) return;
-  // outer factor of this chunk
+  // outer factor of this chunk (lane 0 carries the coefficient itself)
   cx<P> outer;
   bool o_one = true;
   if (q > 0) { outer = left; o_one = false; }
+  else { outer = c0; o_one = false; }
   if (q < T - 1) { outer = o_one ? right : c_mul<P>(outer, right); o_one = false; }
   if (has_cf) { outer = o_one ? cf : c_mul<P>(outer, cf); o_one = false; }
   if (o_one) outer = one;

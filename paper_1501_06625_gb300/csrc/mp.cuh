@@ -101,6 +101,16 @@ struct DD {
     fast_two_sum(q1, q2, s, e);
     return add({s, e}, from(q3));
   }
+  // 1/b: the double reciprocal y0 and one Newton correction y0 + y0 (1 - b y0);
+  // 1 - b.h y0 is exact in one FMA for a correctly rounded y0.  ~16 ops.
+  PHD static real recip(real b) {
+    double y0 = 1.0 / b.h;
+    double e = ffma(-b.h, y0, 1.0);
+    e = ffma(-b.l, y0, e);
+    double s, t;
+    fast_two_sum(y0, fmul(y0, e), s, t);
+    return {s, t};
+  }
   // one Newton correction of the double square root
   PHD static real sqrt(real a) {
     if (!(a.h > 0.0)) return zero();
@@ -226,6 +236,18 @@ struct QD {
     double q4 = r.x[0] / b.x[0];
     qd_renorm(q0, q1, q2, q3, q4);
     return {{q0, q1, q2, q3}};
+  }
+  // 1/b: a double-double reciprocal, then one Newton step y + y (1 - b y) in
+  // quad-double (106 -> 212 bits).
+  PHD static real recip(real b) {
+    double y0 = 1.0 / b.x[0];
+    double e = ffma(-b.x[0], y0, 1.0);
+    e = ffma(-b.x[1], y0, e);
+    double s, t;
+    fast_two_sum(y0, fmul(y0, e), s, t);
+    real y = {{s, t, 0.0, 0.0}};
+    real r = sub(from(1.0), mul(b, y));
+    return add(y, mul(y, r));
   }
   // Newton's iteration s := s + (a - s^2) / (2 s) with the divisor in double:
   // each step adds ~53 correct bits (53, 106, 159, 212).
