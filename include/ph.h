@@ -200,6 +200,26 @@ ph_status ph_profile_newton(ph_ctx *ctx, const ph_system *f, const ph_system *g,
                             int reps, double *ms_out);
 ph_status ph_fp64_peak(ph_ctx *ctx, double ms_target, double *gops);
 
+/* The least-squares solve of ph_mgs_solve for callers that must not allocate
+ * device memory: code running while a CUDA graph is being captured, processes
+ * whose device memory belongs to another allocator, real-time loops that cannot
+ * afford an allocation's implicit synchronisation.  The paper has no
+ * counterpart; this is a convenience of this library.
+ *   No context is needed and nothing is allocated: the scratch is one static
+ *   4 MiB device array that each GPU loading the library keeps until exit.
+ *   Sizes whose scratch (augmented matrix, projections, norms, solution) does
+ *   not fit return PH_EINVAL (n = N up to about 250 in DD, 180 in QD).
+ *   device, cuda_stream  the GPU (made current for the call) and the stream
+ *                        (a cudaStream_t, may be NULL) the work runs on;
+ *   J, rhs, dx, resid_norm  as in ph_mgs_solve (host or device arrays).
+ *   The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) and may load the module: make it before any stream
+ *   capture.  Every call shares the array, so calls that overlap on the GPU
+ *   race: serialise them.  The call returns after synchronising its stream. */
+ph_status ph_mgs_solve_static(int device, void *cuda_stream, ph_prec prec, int N, int n,
+                              const double *J, const double *rhs, double *dx,
+                              double *resid_norm);
+
 /* Library version string. */
 const char *ph_version(void);
 

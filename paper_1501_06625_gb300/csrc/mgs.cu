@@ -257,3 +257,16 @@ cudaError_t ph_mgs_launch(ph_ctx *ctx, int L, int N, int n, double *A, long ldA,
   if (L == 2) return launch_p<DD>(ctx, N, n, A, ldA, W, nrm2, inv2, dx, st, skip, resid);
   return launch_p<QD>(ctx, N, n, A, ldA, W, nrm2, inv2, dx, st, skip, resid);
 }
+
+// The same solve with every buffer supplied by the caller and the launch
+// configuration given explicitly (no context, no allocation): used by the
+// allocation-free entry point in noalloc.cu.
+cudaError_t ph_mgs_launch_buffers(int sm_count, cudaStream_t stream, int L, int N, int n,
+                                  double *A, long ldA, double *W, double *nrm2, double *inv2,
+                                  double *dx, PathState *st, double *resid) {
+  ph_ctx tmp;                       // carries the SM count and the stream only
+  tmp.sm_count = sm_count;
+  tmp.stream = stream;
+  if (L == 2) return launch_p<DD>(&tmp, N, n, A, ldA, W, nrm2, inv2, dx, st, nullptr, resid);
+  return launch_p<QD>(&tmp, N, n, A, ldA, W, nrm2, inv2, dx, st, nullptr, resid);
+}

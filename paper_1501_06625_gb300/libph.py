@@ -52,7 +52,8 @@ class CtrlState(C.Structure):
 
 EXPORTS = ["ph_init", "ph_destroy", "ph_last_error", "ph_system_load", "ph_system_free",
            "ph_eval_jac", "ph_mgs_solve", "ph_track_path", "ph_ctrl_init", "ph_ctrl_next_t",
-           "ph_ctrl_report", "ph_version", "ph_profile_newton", "ph_fp64_peak"]
+           "ph_ctrl_report", "ph_version", "ph_profile_newton", "ph_fp64_peak",
+           "ph_mgs_solve_static"]
 
 
 class PhError(RuntimeError):
@@ -93,6 +94,8 @@ def lib():
             L.ph_version.restype = C.c_char_p
             L.ph_profile_newton.argtypes = [vp, vp, vp, vp, C.c_int, vp, vp, C.c_int, dp]
             L.ph_fp64_peak.argtypes = [vp, C.c_double, dp]
+            L.ph_mgs_solve_static.argtypes = [C.c_int, vp, C.c_int, C.c_int, C.c_int, vp, vp, vp,
+                                              dp]
             _LIB = L
     return _LIB
 
@@ -165,6 +168,19 @@ def ph_eval_jac(ctx, f, g, gamma, k, t, x, h, J):
 def ph_mgs_solve(ctx, prec, N, n, J, rhs, dx) -> float:
     r = C.c_double(0.0)
     _check(ctx, lib().ph_mgs_solve(ctx, prec, N, n, _ptr(J), _ptr(rhs), _ptr(dx), C.byref(r)))
+    return r.value
+
+
+def ph_mgs_solve_static(device: int, stream, prec, N, n, J, rhs, dx) -> float:
+    """ph_mgs_solve without a context and without allocating (static scratch)."""
+    r = C.c_double(0.0)
+    raw = None
+    if stream is not None:
+        raw = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    st = lib().ph_mgs_solve_static(device, raw, prec, N, n, _ptr(J), _ptr(rhs), _ptr(dx),
+                                   C.byref(r))
+    if st != PH_OK:
+        raise PhError(st, "ph_mgs_solve_static failed")
     return r.value
 
 
