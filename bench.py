@@ -197,10 +197,11 @@ def run_reference(args):
 # ---- the library
 
 SEGMENT = {2: 50, 4: 20}       # predictor-corrector steps per bench step
+CONTROL = {"control": 0}       # 1: host-side step control (for profiling runs)
 
 
 def seg_params(wl):
-    return dict(wl.params, max_steps=SEGMENT[wl.L] - 1)
+    return dict(wl.params, max_steps=SEGMENT[wl.L] - 1, control=CONTROL["control"])
 
 
 def track_leg(libph, ctx, f, wl, dev, steps, warmup, torch, flush, events=True):
@@ -270,6 +271,9 @@ def main():
     ap.add_argument("--qd-steps", type=int, default=None)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--control", choices=["device", "host"], default="device",
+                    help="step control on the device (one graph per path segment) or on the "
+                         "host (one graph per step, as in the paper)")
     ap.add_argument("--no-sparse", action="store_true",
                     help="skip the n=512 QD solver roofline measurement")
     args = ap.parse_args()
@@ -277,6 +281,7 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    CONTROL["control"] = 1 if args.control == "host" else 0
 
     import torch
     from paper_1501_06625_gb300 import build, libph, synth
@@ -391,7 +396,7 @@ def main():
                        "seed": args.seed, "precision": "complex double-double",
                        "segment": f"first {SEGMENT[2]} predictor-corrector steps of the path",
                        "l2": "flushed (256 MiB write) between steps",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"replicas x{world}", "control": args.control},
             "segments_per_s": s["paths_per_s"], "pc_steps_per_s": s["pc_steps_per_s"],
             "p50_segment_ms": s["p50_segment_ms"], "p99_segment_ms": s["p99_segment_ms"],
             "path": s["path"], "qd": qd,

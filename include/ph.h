@@ -119,7 +119,10 @@ typedef struct {
   int32_t relax_k;    /* k in gamma (1-t)^k g + t^k f, >= 1                      */
   int32_t fixed_steps;/* > 0: fixed schedule t_j = j / fixed_steps with exactly
                          max_newton updates per step, no test, no rejection      */
-  int32_t reserved;   /* must be 0                                                */
+  int32_t control;    /* 0: the whole path is one graph launch, steps decided on
+                         the device; 1: the host launches one step at a time and
+                         reads the controller state back after each (the paper's
+                         host-side step control, Section 3.1)                    */
 } ph_track_params;
 
 /* Outcome of one tracked path. */
@@ -155,8 +158,9 @@ typedef struct {
  *   ||dx|| < tol_dx); on success keep the point and, after more than two
  *   successes in a row, double dt up to max_dt; on failure go back to the last
  *   accepted point and halve dt.
- * The whole loop runs on the device (one CUDA graph launch per path); the
- * host reads the result once at the end.
+ * With params->control = 0 the whole loop runs on the device (one CUDA graph
+ * launch per path) and the host reads the result once at the end; with 1 the
+ * host launches one step (one graph) at a time, as in the paper.
  *   f, g, gamma  as in ph_eval_jac (gamma is required here);
  *   x0           start solution [L][2][n];
  *   x_out        end point [L][2][n] (the last accepted point);

@@ -211,22 +211,17 @@ __global__ void __launch_bounds__(TPC) k_mgs(int N, int n, double *__restrict__ 
 template <class P, int TPC>
 cudaError_t launch_tpc(ph_ctx *ctx, int N, int n, double *A, long ldA, double *W, double *nrm2,
                        double *inv2, double *dx, PathState *st, const int *skip, double *resid) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(ph_mgs_grid(ctx, P::L, N, n));
-  cfg.blockDim = dim3(TPC);
-  cfg.dynamicSmemBytes = sizeof(double) * 2 * P::L * (size_t)n;
-  cfg.stream = ctx->stream;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  if (cfg.dynamicSmemBytes > 48 * 1024) {
+  const size_t smem = sizeof(double) * 2 * P::L * (size_t)n;
+  if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_mgs<P, TPC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)cfg.dynamicSmemBytes);
+                                         (int)smem);
     if (e != cudaSuccess) return e;
   }
-  return cudaLaunchKernelEx(&cfg, k_mgs<P, TPC>, N, n, A, ldA, W, nrm2, inv2, dx, st, skip, resid);
+  // cooperative launch: the driver guarantees that all blocks are resident
+  void *args[] = {&N, &n, &A, &ldA, &W, &nrm2, &inv2, &dx, &st, (void *)&skip, &resid};
+  return cudaLaunchCooperativeKernel((const void *)k_mgs<P, TPC>,
+                                     dim3(ph_mgs_grid(ctx, P::L, N, n)), dim3(TPC), args, smem,
+                                     ctx->stream);
 }
 
 template <class P>

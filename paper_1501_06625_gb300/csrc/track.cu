@@ -185,11 +185,11 @@ __global__ void k_check_dx(PathState *st, ph_track_params p) {
 template <class P>
 __global__ void k_step_end(PathState *st, ph_track_params p, double *__restrict__ hist,
                            const double *__restrict__ xw, int n, ph_step_record *log, int log_cap,
-                           cudaGraphConditionalHandle cond) {
+                           cudaGraphConditionalHandle cond, int use_cond) {
   __shared__ int s_ok, s_slot;
   __shared__ double s_max;
   if (st->skip_step) {
-    if (threadIdx.x == 0 && st->ctrl.done) cudaGraphSetConditional(cond, 0);
+    if (use_cond && threadIdx.x == 0 && st->ctrl.done) cudaGraphSetConditional(cond, 0);
     return;
   }
   if (threadIdx.x == 0) {
@@ -219,7 +219,7 @@ __global__ void k_step_end(PathState *st, ph_track_params p, double *__restrict_
   }
   __syncthreads();
   if (!s_ok) {
-    if (threadIdx.x == 0 && st->ctrl.done) cudaGraphSetConditional(cond, 0);
+    if (use_cond && threadIdx.x == 0 && st->ctrl.done) cudaGraphSetConditional(cond, 0);
     return;
   }
   const long pt = 2L * P::L * n;
@@ -238,7 +238,7 @@ __global__ void k_step_end(PathState *st, ph_track_params p, double *__restrict_
       st->ctrl.done = 1;
       st->ctrl.status = PH_DIVERGED;
     }
-    if (st->ctrl.done) cudaGraphSetConditional(cond, 0);
+    if (use_cond && st->ctrl.done) cudaGraphSetConditional(cond, 0);
   }
 }
 
@@ -258,6 +258,7 @@ struct TrackGraph {
 struct TrackCache {
   TrackGraph tg;
   cudaStream_t cap = nullptr;      // private stream used for capture
+  int32_t *done_host = nullptr;    // pinned flag for host-side step control
 };
 
 }  // namespace
@@ -292,6 +293,7 @@ void ph_track_release(ph_ctx *ctx) {
   }
   drop_graph(c->tg);
   if (c->cap) cudaStreamDestroy(c->cap);
+  if (c->done_host) cudaFreeHost(c->done_host);
   delete c;
 }
 
@@ -300,7 +302,7 @@ static cudaError_t record_step(ph_ctx *ctx, cudaStream_t s, const ph_system *f,
                                const ph_system *g, const double *gamma,
                                const ph_track_params &p, PathState *st, double *hist, double *xw,
                                double *A, long ldA, double *dx, ph_step_record *log, int log_cap,
-                               cudaGraphConditionalHandle cond) {
+                               cudaGraphConditionalHandle cond, int use_cond) {
   const int L = f->L, n = f->n, N = f->N;
   const long Ap = (long)(n + 1) * ldA;
   cudaStream_t saved = ctx->stream;
@@ -323,8 +325,8 @@ static cudaError_t record_step(ph_ctx *ctx, cudaStream_t s, const ph_system *f,
   }
   if (e == cudaSuccess) {
     int eb = n < 256 ? 128 : 256;
-    if (L == 2) k_step_end<DD><<<1, eb, 0, s>>>(st, p, hist, xw, n, log, log_cap, cond);
-    else k_step_end<QD><<<1, eb, 0, s>>>(st, p, hist, xw, n, log, log_cap, cond);
+    if (L == 2) k_step_end<DD><<<1, eb, 0, s>>>(st, p, hist, xw, n, log, log_cap, cond, use_cond);
+    else k_step_end<QD><<<1, eb, 0, s>>>(st, p, hist, xw, n, log, log_cap, cond, use_cond);
     e = cudaGetLastError();
   }
   ctx->stream = saved;
@@ -339,19 +341,25 @@ static ph_status build_graph(ph_ctx *ctx, TrackCache *c, const ph_system *f, con
   if (!c->cap) PH_CUDA(ctx, cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
   TrackGraph &tg = c->tg;
   PH_CUDA(ctx, cudaGraphCreate(&tg.graph, 0));
-  cudaGraphConditionalHandle cond;
-  PH_CUDA(ctx, cudaGraphConditionalHandleCreate(&cond, tg.graph, 1, cudaGraphCondAssignDefault));
-  cudaGraphNodeParams cp = {};
-  cp.type = cudaGraphNodeTypeConditional;
-  cp.conditional.handle = cond;
-  cp.conditional.type = cudaGraphCondTypeWhile;
-  cp.conditional.size = 1;
-  cudaGraphNode_t node;
-  PH_CUDA(ctx, cudaGraphAddNode(&node, tg.graph, nullptr, nullptr, 0, &cp));
-  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  cudaGraph_t body = tg.graph;
+  cudaGraphConditionalHandle cond = 0;
+  const int use_cond = p.control == 0;
+  if (use_cond) {
+    // a WHILE node repeats the step body until k_step_end clears the condition
+    PH_CUDA(ctx, cudaGraphConditionalHandleCreate(&cond, tg.graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    PH_CUDA(ctx, cudaGraphAddNode(&node, tg.graph, nullptr, nullptr, 0, &cp));
+    body = cp.conditional.phGraph_out[0];
+  }
   PH_CUDA(ctx, cudaStreamBeginCaptureToGraph(c->cap, body, nullptr, nullptr, 0,
                                              cudaStreamCaptureModeThreadLocal));
-  cudaError_t e = record_step(ctx, c->cap, f, g, gamma, p, st, hist, xw, A, ldA, dx, log, log_cap, cond);
+  cudaError_t e = record_step(ctx, c->cap, f, g, gamma, p, st, hist, xw, A, ldA, dx, log, log_cap,
+                              cond, use_cond);
   cudaGraph_t out = nullptr;
   cudaError_t e2 = cudaStreamEndCapture(c->cap, &out);
   if (e != cudaSuccess) { drop_graph(tg); return ph_cuda_fail(ctx, e, "capture of the step"); }
@@ -380,7 +388,7 @@ extern "C" ph_status ph_track_path(ph_ctx *ctx, const ph_system *f, const ph_sys
   if (!gamma || !x0 || !params || !x_out) return ph_fail(ctx, PH_EINVAL, "ph_track_path: NULL argument");
   const ph_track_params p = *params;
   if (p.max_newton < 1 || p.max_newton > 64 || p.pred_order < 0 || p.pred_order > 8 ||
-      p.relax_k < 1 || p.relax_k > 64 || p.reserved != 0 || p.max_steps < 0 ||
+      p.relax_k < 1 || p.relax_k > 64 || p.control < 0 || p.control > 1 || p.max_steps < 0 ||
       (p.fixed_steps <= 0 && !(p.max_dt > 0.0 && p.min_dt > 0.0 && p.min_dt <= p.max_dt)))
     return ph_fail(ctx, PH_EINVAL, "ph_track_path: invalid parameters");
   if (!g) {
@@ -458,8 +466,21 @@ extern "C" ph_status ph_track_path(ph_ctx *ctx, const ph_system *f, const ph_sys
     memcpy(c->tg.bufs, bufs, sizeof bufs);
     c->tg.stream = ctx->stream;
   }
-  PH_CUDA(ctx, cudaGraphLaunch(c->tg.exec, ctx->stream));
   PathState hs;
+  if (p.control == 0) {
+    PH_CUDA(ctx, cudaGraphLaunch(c->tg.exec, ctx->stream));
+  } else {
+    // host-side step control: one step per launch, the controller's done
+    // flag read back after each (a few bytes per step, Section 3.1)
+    if (!c->done_host) PH_CUDA(ctx, cudaMallocHost(&c->done_host, sizeof(int32_t)));
+    for (;;) {
+      PH_CUDA(ctx, cudaGraphLaunch(c->tg.exec, ctx->stream));
+      PH_CUDA(ctx, cudaMemcpyAsync(c->done_host, &st->ctrl.done, sizeof(int32_t),
+                                   cudaMemcpyDeviceToHost, ctx->stream));
+      PH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+      if (*c->done_host) break;
+    }
+  }
   PH_CUDA(ctx, cudaMemcpyAsync(&hs, st, sizeof hs, cudaMemcpyDeviceToHost, ctx->stream));
   PH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   // the last accepted point

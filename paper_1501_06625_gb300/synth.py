@@ -198,7 +198,7 @@ def default_params(L: int, **over) -> dict:
     p = dict(max_dt=0.1, min_dt=1e-12 if L == 2 else 1e-20,
              tol_res=1e-24 if L == 2 else 1e-52, tol_dx=1e-24 if L == 2 else 1e-52,
              max_res=1e8, max_x=1e8, max_steps=10000, max_newton=3 if L == 2 else 4,
-             pred_order=4, relax_k=1, fixed_steps=0)
+             pred_order=4, relax_k=1, fixed_steps=0, control=0)
     p.update(over)
     return p
 

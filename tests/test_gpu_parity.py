@@ -225,6 +225,27 @@ def test_track_dense64_replay_first_steps(ctx):
     assert stats["steps"] == 6
 
 
+@pytest.mark.parametrize("L", [2, 4])
+def test_host_control_matches_device_loop(ctx, L):
+    """The paper's host-side step control (one launch per step, the state read
+    back after each) runs the same kernels: the same log and end point."""
+    rng = synth.Rng(31)
+    spec = synth.dense_system(rng, 5, 5, 3, (1, 2))
+    gam = _gamma(rng, L)
+    x0 = soa_from_complex(np.ones(5), L)
+    f = ctx.load(spec, L)
+    out = []
+    for control in (0, 1):
+        p = synth.default_params(L, max_dt=0.2, max_steps=60, control=control)
+        xg = np.zeros_like(x0)
+        st, stats, log = libph.ph_track_path(ctx.h, f, None, gam, x0, p, xg, log_cap=100)
+        out.append((st, stats, log, xg))
+    assert out[0][0] == out[1][0]
+    assert out[0][2] == out[1][2]
+    assert np.array_equal(out[0][3], out[1][3])
+    assert out[1][1]["launches"] == out[0][1]["launches"]
+
+
 def test_track_f_equals_g(ctx):
     n, L = 4, 2
     spec = synth.build_system(n, n, [[(1.0, [(i, 3)]), (-1.0, [])] for i in range(n)])
