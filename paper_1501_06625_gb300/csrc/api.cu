@@ -59,7 +59,7 @@ extern "C" ph_status ph_destroy(ph_ctx *c) {
   DevBuf *bufs[] = {&c->in_x, &c->in_gamma, &c->in_t, &c->in_J, &c->in_rhs, &c->out_h,
                     &c->out_J, &c->out_dx, &c->slots, &c->ptab, &c->scal, &c->A, &c->R,
                     &c->nrm2, &c->irkk, &c->dxv, &c->state, &c->hist, &c->xw, &c->logbuf,
-                    &c->ystage};
+                    &c->ystage, &c->flags};
   for (DevBuf *b : bufs) b->release();
   delete c;
   return PH_OK;
@@ -180,6 +180,8 @@ extern "C" ph_status ph_mgs_solve(ph_ctx *ctx, ph_prec prec, int N, int n, const
   if ((s = stage_out(ctx, ctx->out_dx, dx, dxbytes, &ddx, &hdx)) != PH_OK) return s;
   PH_CUDA(ctx, ctx->ystage.ensure(sizeof(double)));
   double *dres = ctx->ystage.as<double>();
+  PH_CUDA(ctx, ctx->flags.ensure(sizeof(int) * (size_t)(n + 1)));
+  PH_CUDA(ctx, cudaMemsetAsync(ctx->flags.p, 0, sizeof(int) * (size_t)(n + 1), ctx->stream));
   PH_CUDA(ctx, ph_mgs_launch(ctx, L, N, n, A, ldA, ddx, st, nullptr, dres));
   if (hdx) PH_CUDA(ctx, cudaMemcpyAsync(dx, ddx, dxbytes, cudaMemcpyDeviceToHost, ctx->stream));
   double rn = 0.0;

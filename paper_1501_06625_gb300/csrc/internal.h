@@ -48,6 +48,9 @@ struct PathState {
   int32_t timeout, mgs_status;
   // grid barrier of the cooperative kernels
   unsigned int bar_count, bar_gen;
+  // the MGS solve: epoch of its pivot flags, blocks finished
+  int32_t mgs_epoch;
+  unsigned int mgs_done;
   int32_t iterations;           // passes of the graph's step body
   // kernel gates: a kernel does nothing while its flag is set
   int32_t skip_step, skip_nt;
@@ -62,7 +65,7 @@ struct ph_ctx {
   std::string err;
   DevBuf in_x, in_gamma, in_t, in_J, in_rhs;       // staged host inputs
   DevBuf out_h, out_J, out_dx;                      // staged outputs
-  DevBuf slots, ptab, scal, A, R, nrm2, irkk, dxv, state, hist, xw, logbuf, ystage;
+  DevBuf slots, ptab, scal, A, R, nrm2, irkk, dxv, state, hist, xw, logbuf, ystage, flags;
 };
 
 // A loaded polynomial system: the instruction layout of Section 3.2 (terms
@@ -115,7 +118,9 @@ cudaError_t ph_eval_launch_part(ph_ctx *ctx, const ph_system *f, const ph_system
 
 // mgs.cu: least squares on the augmented matrix A = [J | rhs] held in
 //   A (plane stride (n+1)*ldA, leading dim ldA); dx [2L][n] out;
-//   dx_bits: max |dx_i| accumulated (may be null); resid: ||residual||_2 (may be null)
+//   st->dx_bits: max |dx_i| accumulated; resid: ||residual||_2 (may be null).
+//   The pivot flags (ctx->flags, n+1 ints) must be zero when the state's
+//   mgs_epoch is zero: zero both at the start of every call.
 cudaError_t ph_mgs_launch(ph_ctx *ctx, int L, int N, int n, double *A, long ldA, double *dx,
                           PathState *st, const int *skip, double *resid);
 

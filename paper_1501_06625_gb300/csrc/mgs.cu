@@ -2,33 +2,41 @@
 // matrix A = [J | rhs] and back substitution (Introduction: MGS rather than
 // LU with partial pivoting; Section 3.1: GPU_Modified_Gram_Schmidt).
 //
-// One persistent kernel per solve.  Its blocks are co-resident (cooperative
-// launch) and meet at a grid barrier after every column step.  Each block is
-// one "column group" of TPC = 32..128 threads (one warp per SM sub-partition,
-// so the group that owns the next pivot never shares an FP64 unit with another
-// group); columns are dealt to blocks round-robin and a group's threads split
-// the rows.  On GB300 every FP64 instruction of a warp costs ~64 cycles, so the
-// length of the chain of dependent FP64 instructions per column step is what
-// bounds a single solve; the formulation below keeps that chain short:
+// One persistent kernel per solve, its blocks co-resident (cooperative launch).
+// Columns are dealt to blocks round-robin; every block owns at least one.
+// On GB300 an FP64 warp instruction occupies its SM sub-partition for ~64
+// cycles whether or not the next one depends on it, so a single solve is
+// bounded by the chain of FP64 instructions between one pivot and the next.
+// The kernel is organised to keep that chain short:
 //
-//   step k:  every group with a column j > k forms the unnormalised projection
-//            alpha_kj = (a_k^H a_j) / ||a_k||^2   and updates a_j -= alpha_kj a_k,
-//            which equals a_j - r_kj q_k of textbook MGS without forming q_k;
-//            the owner of column k+1 then computes ||a_{k+1}||^2 for step k+1.
-//   ||a_k||^2 needs one reciprocal per pivot (no square root, no division).
-//   The rows of R are r_kj = alpha_kj ||a_k||, so R dx = Q^H rhs becomes the
-//   unit upper-triangular system  dx_k = alpha_kn - sum_{j>k} alpha_kj dx_j,
-//   solved by block 0 with one complex multiply-add per step on its chain.
-//   Column n (rhs) ends as the least-squares residual vector.
+//  * Unnormalised projections: for pivot k, each block forms
+//      alpha_kj = (a_k^H a_j) / ||a_k||^2   and   a_j -= alpha_kj a_k   (j > k),
+//    which equals a_j - r_kj q_k of textbook MGS without forming q_k.  The owner
+//    of column k+1 updates that column first, computes ||a_{k+1}||^2 and
+//    publishes the pivot (column + norm) through a per-column flag.  Blocks
+//    wait only for the pivot they need (no grid barrier per step), and a block
+//    whose columns are all done leaves.  One reciprocal per pivot; no square
+//    root, no division.
+//  * Each block has four warps, one per SM sub-partition: warps 0/1 carry the
+//    real parts of two halves of the rows, warps 2/3 the imaginary parts, so a
+//    complex dot product, update or norm costs each warp about half the FP64
+//    instructions of the complex operation.
+//  * Double-double reductions keep unnormalised (sum, compensation) pairs
+//    through the tree (8 instructions per level instead of 11).
+//  * R is never formed: with r_kj = alpha_kj ||a_k||, R dx = Q^H rhs becomes the
+//    unit upper-triangular system dx_k = alpha_kn - sum_{j>k} alpha_kj dx_j,
+//    solved by block 0 with one fused multiply-subtract per step on its chain.
+//    Column n (rhs) ends as the least-squares residual vector.
 //
-// Data written by another block of the running kernel (the pivot column, the
-// norms, the alphas) is read through L2 only (ld.global.cg), since L1 is not
-// coherent across SMs; the leading dimension of A is a multiple of 32 doubles
-// so no cache line holds two columns.
+// Data another block may have written (the pivot column, the norms, the
+// alphas) is read through L2 only (ld.global.cg): L1 is not coherent across
+// SMs.  The leading dimension of A is a multiple of 32 doubles so no cache line
+// holds two columns.  Flags carry the solve's epoch (PathState::mgs_epoch + 1),
+// so they need no clearing between the solves of one call.
 //
-// The grid barrier waits on a generation counter with a time limit (2 s of
-// %globaltimer); a wait that runs out sets PathState::timeout and every block
-// returns, so the host gets PH_TIMEOUT and the context stays usable.
+// Every wait is bounded (2 s of %globaltimer); a wait that runs out sets
+// PathState::timeout and the blocks return, so the host gets PH_TIMEOUT and the
+// context stays usable.
 #include "internal.h"
 #include "mp.cuh"
 
@@ -36,7 +44,8 @@ using namespace ph;
 
 namespace {
 
-constexpr unsigned long long kBarrierLimitNs = 2000000000ull;
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;
+constexpr int kThreads = 128;
 
 PHD unsigned long long global_timer_ns() {
   unsigned long long t;
@@ -44,29 +53,24 @@ PHD unsigned long long global_timer_ns() {
   return t;
 }
 
-__device__ bool grid_sync(PathState *st) {
+// Thread 0 waits until *flag == tag (or the timeout flag is set); the block
+// then proceeds.  Returns false when the wait gave up.
+__device__ bool wait_flag(const int *flag, int tag, PathState *st) {
   __shared__ int s_ok;
-  __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned int *gen = &st->bar_gen;
+    volatile const int *f = flag;
     volatile int *tmo = &st->timeout;
-    unsigned int g0 = *gen;
-    __threadfence();
     int ok = 1;
-    if (atomicAdd(&st->bar_count, 1u) == gridDim.x - 1) {
-      atomicExch(&st->bar_count, 0u);
-      __threadfence();
-      atomicAdd(&st->bar_gen, 1u);
-    } else {
+    if (*f != tag) {
       unsigned long long t0 = global_timer_ns();
-      while (*gen == g0) {
+      unsigned spins = 0;
+      while (*f != tag) {
         if (*tmo) { ok = 0; break; }
-        if (global_timer_ns() - t0 > kBarrierLimitNs) {
+        if ((++spins & 255u) == 0 && global_timer_ns() - t0 > kWaitLimitNs) {
           atomicExch(&st->timeout, 1);
           ok = 0;
           break;
         }
-        __nanosleep(64);
       }
     }
     __threadfence();
@@ -76,160 +80,319 @@ __device__ bool grid_sync(PathState *st) {
   return s_ok != 0;
 }
 
+__device__ void publish(int *flag, int tag) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    *(volatile int *)flag = tag;
+  }
+}
+
+// ---- per-part arithmetic (one real component of a complex quantity) -------------
+//
+// acc: an accumulator of real terms; dot2(x1,y1,x2,y2,sg) adds x1 y1 + sg x2 y2;
+// sq(x) adds x^2; upd(a, ar, b, ai, c, sg) = a - ar b + sg ai c.
+
+template <class P> struct Part {
+  typedef typename P::real real;
+  struct acc { real v; };
+  PHD static acc zero() { return {P::zero()}; }
+  PHD static void dot2(acc &a, const real &x1, const real &y1, const real &x2, const real &y2,
+                       double sg) {
+    real t = P::mul(x2, y2);
+    if (sg < 0) t = P::neg(t);
+    a.v = P::add(a.v, P::add(P::mul(x1, y1), t));
+  }
+  PHD static void sq(acc &a, const real &x) { a.v = P::add(a.v, P::mul(x, x)); }
+  PHD static acc combine(const acc &a, const acc &b) { return {P::add(a.v, b.v)}; }
+  PHD static acc shfl(const acc &a, int m) {
+    acc z;
+#pragma unroll
+    for (int l = 0; l < P::L; ++l)
+      P::set_limb(z.v, l, __shfl_xor_sync(0xffffffffu, P::limb(a.v, l), m));
+    return z;
+  }
+  PHD static real value(const acc &a) { return a.v; }
+  PHD static real upd(const real &a, const real &ar, const real &b, const real &ai,
+                      const real &c, double sg) {
+    real t = P::mul(ai, c);
+    if (sg < 0) t = P::neg(t);
+    return P::add(a, P::sub(t, P::mul(ar, b)));
+  }
+};
+
+// double-double: Dot2-style unnormalised (s, c) accumulation
+template <> struct Part<DD> {
+  typedef dd real;
+  struct acc { double s, c; };
+  PHD static acc zero() { return {0.0, 0.0}; }
+  PHD static void add_term(acc &a, double p) {
+    double s, e;
+    ph::two_sum(a.s, p, s, e);
+    a.s = s;
+    a.c = ph::fadd(a.c, e);
+  }
+  PHD static void dot2(acc &a, const dd &x1, const dd &y1, const dd &x2, const dd &y2, double sg) {
+    double p1, e1, p2, e2;
+    ph::two_prod(x1.h, y1.h, p1, e1);
+    ph::two_prod(sg * x2.h, y2.h, p2, e2);
+    double lo = ph::fadd(e1, e2);
+    lo = ph::ffma(x1.h, y1.l, lo);
+    lo = ph::ffma(x1.l, y1.h, lo);
+    lo = ph::ffma(sg * x2.h, y2.l, lo);
+    lo = ph::ffma(sg * x2.l, y2.h, lo);
+    add_term(a, p1);
+    add_term(a, p2);
+    a.c = ph::fadd(a.c, lo);
+  }
+  PHD static void sq(acc &a, const dd &x) {
+    double p, e;
+    ph::two_prod(x.h, x.h, p, e);
+    e = ph::ffma(2.0 * x.h, x.l, e);
+    add_term(a, p);
+    a.c = ph::fadd(a.c, e);
+  }
+  PHD static acc combine(const acc &a, const acc &b) {
+    acc z;
+    double e;
+    ph::two_sum(a.s, b.s, z.s, e);
+    z.c = ph::fadd(ph::fadd(a.c, b.c), e);
+    return z;
+  }
+  PHD static acc shfl(const acc &a, int m) {
+    return {__shfl_xor_sync(0xffffffffu, a.s, m), __shfl_xor_sync(0xffffffffu, a.c, m)};
+  }
+  PHD static dd value(const acc &a) {
+    double s, e;
+    ph::fast_two_sum(a.s, a.c, s, e);
+    return {s, e};
+  }
+  // a - ar b + sg ai c with one renormalisation
+  PHD static dd upd(const dd &a, const dd &ar, const dd &b, const dd &ai, const dd &c, double sg) {
+    double p1, e1, p2, e2, s, es1, es2;
+    ph::two_prod(ar.h, b.h, p1, e1);
+    ph::two_prod(sg * ai.h, c.h, p2, e2);
+    ph::two_sum(a.h, -p1, s, es1);
+    ph::two_sum(s, p2, s, es2);
+    double lo = ph::fadd(ph::fadd(a.l, es1), es2);
+    lo = ph::fsub(lo, e1);
+    lo = ph::fadd(lo, e2);
+    lo = ph::ffma(-ar.h, b.l, lo);
+    lo = ph::ffma(-ar.l, b.h, lo);
+    lo = ph::ffma(sg * ai.h, c.l, lo);
+    lo = ph::ffma(sg * ai.l, c.h, lo);
+    double z, zl;
+    ph::fast_two_sum(s, lo, z, zl);
+    return {z, zl};
+  }
+};
+
+// Sum of the block's four warps by part: warps {0,1} -> part 0, {2,3} -> part 1.
+// Returns this warp's part total (normalised) to every lane.
 template <class P>
-PHD typename P::real shfl_xor_r(const typename P::real &a, int m) {
+__device__ typename P::real part_total(typename Part<P>::acc a, typename Part<P>::acc *sh) {
+  typedef Part<P> PO;
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) a = PO::combine(a, PO::shfl(a, m));
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) sh[w] = a;
+  __syncthreads();
+  typename PO::acc t = PO::combine(sh[w & 2], sh[(w & 2) + 1]);
+  __syncthreads();
+  return PO::value(t);
+}
+
+// Exchange a part value between the two halves of the block: warps of part q
+// receive the value the warps of part 1-q computed.
+template <class P>
+__device__ typename P::real swap_parts(const typename P::real &mine, typename P::real *sh) {
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0 && (w & 1) == 0) sh[w >> 1] = mine;
+  __syncthreads();
+  typename P::real other = sh[1 - (w >> 1)];
+  __syncthreads();
+  return other;
+}
+
+template <class P>
+PHD typename P::real load_part(const double *col, long Ap, int part, long i) {
   typename P::real z;
 #pragma unroll
-  for (int l = 0; l < P::L; ++l) P::set_limb(z, l, __shfl_xor_sync(0xffffffffu, P::limb(a, l), m));
+  for (int l = 0; l < P::L; ++l) P::set_limb(z, l, col[(2 * l + part) * Ap + i]);
   return z;
 }
 
-// Sum over the block (one column group of TPC threads); every thread gets it.
-template <class P, int TPC>
-__device__ cx<P> group_sum_c(cx<P> v) {
-  __shared__ cx<P> sh[TPC / 32];
+template <class P>
+PHD typename P::real load_part_cg(const double *col, long Ap, int part, long i) {
+  typename P::real z;
 #pragma unroll
-  for (int m = 16; m > 0; m >>= 1) {
-    v.re = P::add(v.re, shfl_xor_r<P>(v.re, m));
-    v.im = P::add(v.im, shfl_xor_r<P>(v.im, m));
-  }
-  if (TPC == 32) return v;
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-  __syncthreads();
-  v = sh[0];
-#pragma unroll
-  for (int w = 1; w < TPC / 32; ++w) v = c_add<P>(v, sh[w]);
-  __syncthreads();
-  return v;
+  for (int l = 0; l < P::L; ++l) P::set_limb(z, l, __ldcg(col + (2 * l + part) * Ap + i));
+  return z;
 }
 
-template <class P, int TPC>
-__device__ typename P::real group_sum_r(typename P::real v) {
-  __shared__ typename P::real sh[TPC / 32];
+template <class P>
+PHD void store_part(double *col, long Ap, int part, long i, const typename P::real &z) {
 #pragma unroll
-  for (int m = 16; m > 0; m >>= 1) v = P::add(v, shfl_xor_r<P>(v, m));
-  if (TPC == 32) return v;
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-  __syncthreads();
-  v = sh[0];
-#pragma unroll
-  for (int w = 1; w < TPC / 32; ++w) v = P::add(v, sh[w]);
-  __syncthreads();
-  return v;
+  for (int l = 0; l < P::L; ++l) col[(2 * l + part) * Ap + i] = P::limb(z, l);
 }
 
-template <class P, int TPC>
-__device__ typename P::real col_norm2(const double *A, long Ap, long ldA, int N, int j) {
-  typename P::real acc = P::zero();
-  for (int i = threadIdx.x; i < N; i += TPC)
-    acc = P::add(acc, c_abs2<P>(c_load<P>(A + (long)j * ldA, Ap, i)));
-  return group_sum_r<P, TPC>(acc);
+// ||a_j||^2 of a column (after its last update by this block)
+template <class P>
+__device__ typename P::real col_norm2(const double *col, long Ap, int N, int part, int r0,
+                                      typename Part<P>::acc *sh, typename P::real *shr) {
+  typename Part<P>::acc a = Part<P>::zero();
+  for (int i = r0; i < N; i += 64) Part<P>::sq(a, load_part<P>(col, Ap, part, i));
+  typename P::real mine = part_total<P>(a, sh);
+  typename P::real other = swap_parts<P>(mine, shr);
+  return P::add(mine, other);
 }
 
-// W: the alphas, [2L][nc][nc] column-major (alpha_kj at j*nc + k);
-// inv2: 1/||a_k||^2, [L][n]; nrm2: ||a_k||^2, [L][n+1].
-template <class P, int TPC>
-__global__ void __launch_bounds__(TPC) k_mgs(int N, int n, double *__restrict__ A, long ldA,
-                                             double *__restrict__ W, double *__restrict__ nrm2,
-                                             double *__restrict__ inv2s, double *__restrict__ dx,
-                                             PathState *st, const int *__restrict__ skip,
-                                             double *__restrict__ resid) {
+// W: alpha_kj at W[(2l+c) Wp + j nc + k] (column j of the alphas);
+// nrm2: ||a_k||^2 [L][nc]; ready: [nc] pivot flags.
+template <class P>
+__global__ void __launch_bounds__(kThreads) k_mgs(int N, int n, double *__restrict__ A, long ldA,
+                                                  double *__restrict__ W, double *__restrict__ nrm2,
+                                                  double *__restrict__ dx, int *__restrict__ ready,
+                                                  PathState *st, const int *__restrict__ skip,
+                                                  double *__restrict__ resid) {
   if (skip && *skip) return;
   typedef typename P::real real;
-  extern __shared__ double s_y[];          // back substitution: [2L][n]
+  typedef Part<P> PO;
+  __shared__ typename PO::acc sh_acc[4];
+  __shared__ real sh_r[2];
+  extern __shared__ double s_y[];                // back substitution: [L][2][n]
   const int nc = n + 1;
   const long Ap = (long)nc * ldA, Wp = (long)nc * nc;
   const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
+  const int w = tid >> 5, lane = tid & 31;
+  const int part = w >> 1;                       // 0 = real, 1 = imaginary
+  const int r0 = (w & 1) * 32 + lane;            // rows r0, r0 + 64, ...
+  const int tag = st->mgs_epoch + 1;
+  const int last_own = b + ((n - b) / G) * G;    // largest column this block owns
 
   if (b == 0) {
-    real s = col_norm2<P, TPC>(A, Ap, ldA, N, 0);
+    real s = col_norm2<P>(A, Ap, N, part, r0, sh_acc, sh_r);
     if (tid == 0) r_store<P>(nrm2, nc, 0, s);
+    publish(&ready[0], tag);
   }
-  if (!grid_sync(st)) return;
-
-  int status = PH_OK;
-  for (int k = 0; k < n; ++k) {
-    real r2 = r_load_cg<P>(nrm2, nc, k);
-    double lead = P::lead(r2);
-    if (!(lead > 0.0) || !isfinite(lead)) {   // the same decision in every block
-      status = PH_NONFINITE;
+  for (int k = 0; k < last_own; ++k) {
+    if (!wait_flag(&ready[k], tag, st)) break;
+    const real r2 = r_load_cg<P>(nrm2, nc, k);
+    const double lead = P::lead(r2);
+    if (!(lead > 0.0) || !isfinite(lead)) {      // every block reads the same value
+      if (tid == 0) atomicExch(&st->mgs_status, PH_NONFINITE);
       break;
     }
-    int j = k + 1 + (((b - (k + 1)) % G) + G) % G;
-    if (j <= n || b == 0) {
-      real inv2 = P::recip(r2);
-      if (b == 0 && tid == 0) r_store<P>(inv2s, n, k, inv2);
-      for (; j <= n; j += G) {
-        cx<P> d = c_zero<P>();
-        for (int i = tid; i < N; i += TPC)
-          d = c_add<P>(d, c_conj_mul<P>(c_load_cg<P>(A + (long)k * ldA, Ap, i),
-                                        c_load<P>(A + (long)j * ldA, Ap, i)));
-        d = group_sum_c<P, TPC>(d);
-        cx<P> alpha = c_mul_real<P>(d, inv2);
-        if (tid == 0) c_store<P>(W + (long)j * nc, Wp, k, alpha);
-        for (int i = tid; i < N; i += TPC) {
-          cx<P> aj = c_load<P>(A + (long)j * ldA, Ap, i);
-          cx<P> ak = c_load_cg<P>(A + (long)k * ldA, Ap, i);
-          c_store<P>(A + (long)j * ldA, Ap, i, c_sub<P>(aj, c_mul<P>(alpha, ak)));
-        }
-        if (j == k + 1) {
-          real s = col_norm2<P, TPC>(A, Ap, ldA, N, j);
-          if (tid == 0) r_store<P>(nrm2, nc, j, s);
+    const real inv2 = P::recip(r2);
+    const double *ak = A + (long)k * ldA;
+    for (int j = k + 1 + (((b - (k + 1)) % G) + G) % G; j <= n; j += G) {
+      double *aj = A + (long)j * ldA;
+      // this warp's part of a_k^H a_j:  re = akr ajr + aki aji,  im = akr aji - aki ajr
+      typename PO::acc a = PO::zero();
+      for (int i = r0; i < N; i += 64) {
+        real akr = load_part_cg<P>(ak, Ap, 0, i), aki = load_part_cg<P>(ak, Ap, 1, i);
+        real ajr = load_part<P>(aj, Ap, 0, i), aji = load_part<P>(aj, Ap, 1, i);
+        if (part == 0) PO::dot2(a, akr, ajr, aki, aji, 1.0);
+        else PO::dot2(a, akr, aji, aki, ajr, -1.0);
+      }
+      real d = part_total<P>(a, sh_acc);
+      real al = P::mul(d, inv2);                  // this part of alpha_kj
+      real al_o = swap_parts<P>(al, sh_r);        // the other part
+      const real alr = part == 0 ? al : al_o, ali = part == 0 ? al_o : al;
+      if (tid == 0) {
+#pragma unroll
+        for (int l = 0; l < P::L; ++l) {
+          W[(2 * l) * Wp + (long)j * nc + k] = P::limb(alr, l);
+          W[(2 * l + 1) * Wp + (long)j * nc + k] = P::limb(ali, l);
         }
       }
+      // a_j -= alpha a_k:  re: ajr - alr akr + ali aki;  im: aji - alr aki - ali akr
+      for (int i = r0; i < N; i += 64) {
+        real akr = load_part_cg<P>(ak, Ap, 0, i), aki = load_part_cg<P>(ak, Ap, 1, i);
+        if (part == 0)
+          store_part<P>(aj, Ap, 0, i, PO::upd(load_part<P>(aj, Ap, 0, i), alr, akr, ali, aki, 1.0));
+        else
+          store_part<P>(aj, Ap, 1, i, PO::upd(load_part<P>(aj, Ap, 1, i), alr, aki, ali, akr, -1.0));
+      }
+      if (j == k + 1) {
+        __syncthreads();                           // both parts of the column written
+        real s = col_norm2<P>(aj, Ap, N, part, r0, sh_acc, sh_r);
+        if (tid == 0) r_store<P>(nrm2, nc, j, s);
+        publish(&ready[j], tag);
+      }
     }
-    if (!grid_sync(st)) return;
+  }
+  // completion: block 0 waits for every block, then solves R dx = Q^H rhs
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    atomicAdd(&st->mgs_done, 1u);
   }
   if (b != 0) return;
-  if (status != PH_OK) {
-    if (tid == 0) st->mgs_status = status;
-    return;
+  if (tid == 0) {
+    volatile unsigned int *done = &st->mgs_done;
+    volatile int *tmo = &st->timeout;
+    unsigned long long t0 = global_timer_ns();
+    unsigned spins = 0;
+    while (*done < (unsigned)G) {
+      if (*tmo) break;
+      if ((++spins & 255u) == 0 && global_timer_ns() - t0 > kWaitLimitNs) {
+        atomicExch(&st->timeout, 1);
+        break;
+      }
+    }
+    __threadfence();
   }
-  // least-squares residual ||a_n|| after the last projection
+  __syncthreads();
+  if (*(volatile int *)&st->timeout) return;
+  __syncthreads();
+  if (tid == 0) {
+    st->mgs_done = 0;
+    st->mgs_epoch = tag;                           // this solve's flags become stale
+  }
+  if (*(volatile int *)&st->mgs_status != PH_OK) return;
   if (tid == 0 && resid) *resid = __dsqrt_rn(P::lead(r_load_cg<P>(nrm2, nc, n)));
   // back substitution on y = alpha_{., n}:  dx_k = y_k;  y_i -= alpha_ik dx_k (i < k)
-  const double *y0 = W + (long)n * nc;
-  for (int i = tid; i < n; i += TPC) c_store<P>(s_y, n, i, c_load_cg<P>(y0, Wp, i));
+  const double *yc = W + (long)n * nc;
+  for (int i = tid; i < n; i += kThreads) c_store<P>(s_y, n, i, c_load_cg<P>(yc, Wp, i));
   __syncthreads();
-  for (int k = n - 1; k >= 0; --k) {
-    cx<P> xk = c_load<P>(s_y, n, k);
-    if (tid == 0) c_store<P>(dx, n, k, xk);
-    for (int i = tid; i < k; i += TPC) {
-      cx<P> yi = c_load<P>(s_y, n, i);
-      c_store<P>(s_y, n, i, c_sub<P>(yi, c_mul<P>(c_load_cg<P>(W + (long)k * nc, Wp, i), xk)));
+  for (int k = n - 1; k >= 1; --k) {
+    const real xr = load_part<P>(s_y, n, 0, k), xi = load_part<P>(s_y, n, 1, k);
+    const double *Wk = W + (long)k * nc;
+    // warps of part 0 update the real parts of rows i < k, part 1 the imaginary
+    for (int i = (w & 1) * 32 + lane; i < k; i += 64) {
+      real wr = load_part_cg<P>(Wk, Wp, 0, i), wi = load_part_cg<P>(Wk, Wp, 1, i);
+      if (part == 0) store_part<P>(s_y, n, 0, i, PO::upd(load_part<P>(s_y, n, 0, i), wr, xr, wi, xi, 1.0));
+      else store_part<P>(s_y, n, 1, i, PO::upd(load_part<P>(s_y, n, 1, i), wr, xi, wi, xr, -1.0));
     }
     __syncthreads();
   }
   double m = 0.0;
-  for (int i = tid; i < n; i += TPC) {
-    double a = c_mag_lead<P>(c_load<P>(s_y, n, i));
+  for (int i = tid; i < n; i += kThreads) {
+    cx<P> v = c_load<P>(s_y, n, i);
+    c_store<P>(dx, n, i, v);
+    double a = c_mag_lead<P>(v);
     if (!(a <= m)) m = a;
   }
   atomicMax(&st->dx_bits, (unsigned long long)__double_as_longlong(m));
 }
 
-template <class P, int TPC>
-cudaError_t launch_tpc(ph_ctx *ctx, int N, int n, double *A, long ldA, double *W, double *nrm2,
-                       double *inv2, double *dx, PathState *st, const int *skip, double *resid) {
+template <class P>
+cudaError_t launch_p(int sm_count, cudaStream_t stream, int N, int n, double *A, long ldA,
+                     double *W, double *nrm2, double *dx, int *ready, PathState *st,
+                     const int *skip, double *resid) {
   const size_t smem = sizeof(double) * 2 * P::L * (size_t)n;
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_mgs<P, TPC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_mgs<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
   }
+  int grid = n + 1 < sm_count ? n + 1 : sm_count;
+  if (grid < 1) grid = 1;
   // cooperative launch: the driver guarantees that all blocks are resident
-  void *args[] = {&N, &n, &A, &ldA, &W, &nrm2, &inv2, &dx, &st, (void *)&skip, &resid};
-  return cudaLaunchCooperativeKernel((const void *)k_mgs<P, TPC>,
-                                     dim3(ph_mgs_grid(ctx, P::L, N, n)), dim3(TPC), args, smem,
-                                     ctx->stream);
-}
-
-template <class P>
-cudaError_t launch_p(ph_ctx *ctx, int N, int n, double *A, long ldA, double *W, double *nrm2,
-                     double *inv2, double *dx, PathState *st, const int *skip, double *resid) {
-  if (N <= 32) return launch_tpc<P, 32>(ctx, N, n, A, ldA, W, nrm2, inv2, dx, st, skip, resid);
-  if (N <= 64) return launch_tpc<P, 64>(ctx, N, n, A, ldA, W, nrm2, inv2, dx, st, skip, resid);
-  return launch_tpc<P, 128>(ctx, N, n, A, ldA, W, nrm2, inv2, dx, st, skip, resid);
+  void *args[] = {&N, &n, &A, &ldA, &W, &nrm2, &dx, &ready, &st, (void *)&skip, &resid};
+  return cudaLaunchCooperativeKernel((const void *)k_mgs<P>, dim3(grid), dim3(kThreads), args,
+                                     smem, stream);
 }
 
 }  // namespace
@@ -247,21 +410,24 @@ cudaError_t ph_mgs_launch(ph_ctx *ctx, int L, int N, int n, double *A, long ldA,
   cudaError_t e;
   if ((e = ctx->R.ensure(sizeof(double) * 2 * L * (size_t)nc * nc)) != cudaSuccess) return e;
   if ((e = ctx->nrm2.ensure(sizeof(double) * L * (size_t)nc)) != cudaSuccess) return e;
-  if ((e = ctx->irkk.ensure(sizeof(double) * L * (size_t)n)) != cudaSuccess) return e;
-  double *W = ctx->R.as<double>(), *nrm2 = ctx->nrm2.as<double>(), *inv2 = ctx->irkk.as<double>();
-  if (L == 2) return launch_p<DD>(ctx, N, n, A, ldA, W, nrm2, inv2, dx, st, skip, resid);
-  return launch_p<QD>(ctx, N, n, A, ldA, W, nrm2, inv2, dx, st, skip, resid);
+  if ((e = ctx->flags.ensure(sizeof(int) * (size_t)nc)) != cudaSuccess) return e;
+  double *W = ctx->R.as<double>(), *nrm2 = ctx->nrm2.as<double>();
+  if (L == 2)
+    return launch_p<DD>(ctx->sm_count, ctx->stream, N, n, A, ldA, W, nrm2, dx,
+                        ctx->flags.as<int>(), st, skip, resid);
+  return launch_p<QD>(ctx->sm_count, ctx->stream, N, n, A, ldA, W, nrm2, dx, ctx->flags.as<int>(),
+                      st, skip, resid);
 }
 
 // The same solve with every buffer supplied by the caller and the launch
 // configuration given explicitly (no context, no allocation): used by the
-// allocation-free entry point in noalloc.cu.
+// allocation-free entry point in noalloc.cu.  `ready` holds n+1 ints that must
+// not hold the value PathState::mgs_epoch + 1 (zeroed flags with a zeroed state
+// qualify).
 cudaError_t ph_mgs_launch_buffers(int sm_count, cudaStream_t stream, int L, int N, int n,
-                                  double *A, long ldA, double *W, double *nrm2, double *inv2,
-                                  double *dx, PathState *st, double *resid) {
-  ph_ctx tmp;                       // carries the SM count and the stream only
-  tmp.sm_count = sm_count;
-  tmp.stream = stream;
-  if (L == 2) return launch_p<DD>(&tmp, N, n, A, ldA, W, nrm2, inv2, dx, st, nullptr, resid);
-  return launch_p<QD>(&tmp, N, n, A, ldA, W, nrm2, inv2, dx, st, nullptr, resid);
+                                  double *A, long ldA, double *W, double *nrm2, double *dx,
+                                  int *ready, PathState *st, double *resid) {
+  if (L == 2)
+    return launch_p<DD>(sm_count, stream, N, n, A, ldA, W, nrm2, dx, ready, st, nullptr, resid);
+  return launch_p<QD>(sm_count, stream, N, n, A, ldA, W, nrm2, dx, ready, st, nullptr, resid);
 }

@@ -7,7 +7,7 @@
 // allocator, a fixed arena), and real-time loops where an allocation's
 // implicit synchronisation is not acceptable.  This entry point allocates
 // nothing.  Its scratch memory (the augmented matrix, the projections, the
-// pivot norms, the solution, the barrier and status words) is one file-scope
+// pivot norms and flags, the solution, the status words) is one file-scope
 // device array of kScratchBytes, which every GPU that loads the library holds
 // until the process exits.
 //
@@ -17,8 +17,8 @@
 // it.  That first call may load the module; make it before any stream
 // capture.  All calls share the one array: calls that overlap on the GPU
 // (other streams, other host threads) race and must be serialised by the
-// caller.  What must start at zero (the barrier and status words) is cleared
-// on the caller's stream at the start of every call.
+// caller.  What must start at zero (the status words and the pivot flags) is
+// cleared on the caller's stream at the start of every call.
 #include <mutex>
 
 #include "internal.h"
@@ -38,8 +38,8 @@ size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 }  // namespace
 
 cudaError_t ph_mgs_launch_buffers(int sm_count, cudaStream_t stream, int L, int N, int n,
-                                  double *A, long ldA, double *W, double *nrm2, double *inv2,
-                                  double *dx, PathState *st, double *resid);
+                                  double *A, long ldA, double *W, double *nrm2, double *dx,
+                                  int *ready, PathState *st, double *resid);
 long ph_lda(int N);
 
 extern "C" ph_status ph_mgs_solve_static(int device, void *cuda_stream, ph_prec prec, int N,
@@ -50,13 +50,13 @@ extern "C" ph_status ph_mgs_solve_static(int device, void *cuda_stream, ph_prec 
   if (device < 0 || device >= kMaxDevices) return PH_EINVAL;
   const int L = (int)prec, nc = n + 1;
   const long ldA = ph_lda(N), Ap = (long)nc * ldA;
-  // layout of the scratch array: state | A | W | norms | 1/norms | dx | residual
+  // layout of the scratch array: state | A | W | norms | pivot flags | dx | residual
   const size_t o_st = 0;
   const size_t o_A = o_st + align256(sizeof(PathState));
   const size_t o_W = o_A + align256(sizeof(double) * 2 * L * (size_t)Ap);
   const size_t o_n = o_W + align256(sizeof(double) * 2 * L * (size_t)nc * nc);
   const size_t o_i = o_n + align256(sizeof(double) * L * (size_t)nc);
-  const size_t o_x = o_i + align256(sizeof(double) * L * (size_t)n);
+  const size_t o_x = o_i + align256(sizeof(int) * (size_t)nc);
   const size_t o_r = o_x + align256(sizeof(double) * 2 * L * (size_t)n);
   const size_t need = o_r + align256(sizeof(double));
   if (need > kScratchBytes) return PH_EINVAL;    // too large for the static scratch
@@ -88,19 +88,21 @@ extern "C" ph_status ph_mgs_solve_static(int device, void *cuda_stream, ph_prec 
   cudaStream_t s = (cudaStream_t)cuda_stream;
   PathState *st = (PathState *)(base + o_st);
   double *A = (double *)(base + o_A), *W = (double *)(base + o_W), *nrm2 = (double *)(base + o_n);
-  double *inv2 = (double *)(base + o_i), *xo = (double *)(base + o_x), *res = (double *)(base + o_r);
+  int *ready = (int *)(base + o_i);
+  double *xo = (double *)(base + o_x), *res = (double *)(base + o_r);
   PathState hs;
   double rn = 0.0;
   cudaError_t e = cudaSuccess;
   if (status == PH_OK) {
     e = cudaMemsetAsync(st, 0, sizeof(PathState), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ready, 0, sizeof(int) * (size_t)nc, s);
     for (int c = 0; c < 2 * L && e == cudaSuccess; ++c)
       e = cudaMemcpy2DAsync(A + c * Ap, ldA * sizeof(double), J + (long)c * n * N, N * sizeof(double),
                             N * sizeof(double), n, cudaMemcpyDefault, s);
     if (e == cudaSuccess)
       e = cudaMemcpy2DAsync(A + (long)n * ldA, Ap * sizeof(double), rhs, N * sizeof(double),
                             N * sizeof(double), 2 * L, cudaMemcpyDefault, s);
-    if (e == cudaSuccess) e = ph_mgs_launch_buffers(sms, s, L, N, n, A, ldA, W, nrm2, inv2, xo, st, res);
+    if (e == cudaSuccess) e = ph_mgs_launch_buffers(sms, s, L, N, n, A, ldA, W, nrm2, xo, ready, st, res);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(dx, xo, sizeof(double) * 2 * L * n, cudaMemcpyDefault, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&rn, res, sizeof(double), cudaMemcpyDeviceToHost, s);

@@ -436,6 +436,7 @@ extern "C" ph_status ph_track_path(ph_ctx *ctx, const ph_system *f, const ph_sys
     PH_CUDA(ctx, ctx->R.ensure(sizeof(double) * 2 * L * (size_t)(n + 1) * (n + 1)));
     PH_CUDA(ctx, ctx->nrm2.ensure(sizeof(double) * L * (size_t)(n + 1)));
     PH_CUDA(ctx, ctx->irkk.ensure(sizeof(double) * L * (size_t)n));
+    PH_CUDA(ctx, ctx->flags.ensure(sizeof(int) * (size_t)(n + 1)));
   }
   PathState *st = ctx->state.as<PathState>();
   double *hist = ctx->hist.as<double>(), *xw = ctx->xw.as<double>(), *dx = ctx->dxv.as<double>();
@@ -450,12 +451,13 @@ extern "C" ph_status ph_track_path(ph_ctx *ctx, const ph_system *f, const ph_sys
   h0.hist_head = 0;
   h0.hist_t[0] = 0.0;
   PH_CUDA(ctx, cudaMemcpyAsync(st, &h0, sizeof h0, cudaMemcpyHostToDevice, ctx->stream));
+  PH_CUDA(ctx, cudaMemsetAsync(ctx->flags.p, 0, sizeof(int) * (size_t)(n + 1), ctx->stream));
   PH_CUDA(ctx, cudaMemcpyAsync(hist, hx0.data(), sizeof(double) * pt, cudaMemcpyHostToDevice, ctx->stream));
   PH_CUDA(ctx, cudaMemcpyAsync(dgam, hg.data(), sizeof(double) * 2 * L, cudaMemcpyHostToDevice, ctx->stream));
 
   TrackCache *c = get_cache(ctx);
   void *bufs[16] = {st, hist, xw, dx, A, dgam, dlog, ctx->slots.p, ctx->ptab.p, ctx->scal.p,
-                    ctx->R.p, ctx->nrm2.p, ctx->irkk.p, nullptr, nullptr, nullptr};
+                    ctx->R.p, ctx->nrm2.p, ctx->irkk.p, ctx->flags.p, nullptr, nullptr};
   bool same = c->tg.valid && c->tg.f == f && c->tg.g == g && c->tg.log_cap == log_cap &&
               memcmp(&c->tg.p, &p, sizeof p) == 0 && memcmp(c->tg.bufs, bufs, sizeof bufs) == 0 &&
               c->tg.stream == ctx->stream;
@@ -531,6 +533,8 @@ extern "C" ph_status ph_profile_newton(ph_ctx *ctx, const ph_system *f, const ph
   PH_CUDA(ctx, cudaMemcpyAsync(ctx->in_gamma.p, gamma, sizeof(double) * 2 * L, cudaMemcpyDefault, ctx->stream));
   PH_CUDA(ctx, cudaMemcpyAsync(ctx->in_t.p, t, sizeof(double) * L, cudaMemcpyDefault, ctx->stream));
   PH_CUDA(ctx, cudaMemsetAsync(ctx->state.p, 0, sizeof(PathState), ctx->stream));
+  PH_CUDA(ctx, ctx->flags.ensure(sizeof(int) * (size_t)(n + 1)));
+  PH_CUDA(ctx, cudaMemsetAsync(ctx->flags.p, 0, sizeof(int) * (size_t)(n + 1), ctx->stream));
   double *A = ctx->A.as<double>();
   PathState *st = ctx->state.as<PathState>();
   cudaEvent_t ev[5];
