@@ -243,6 +243,19 @@ def e2e_leg(libph, ctx, f, wl, steps, torch):
     return iters / sum(walls), h2d, d2h
 
 
+def batch_starts(wl, count, seed=7):
+    """Total-degree start solutions exp(2 pi i m_i / d_i) (rounded to double):
+    the all-ones root first, then random choices of the m_i."""
+    d = wl.f.degrees()
+    rng = np.random.default_rng(seed)
+    out = np.zeros((count, wl.L, 2, wl.n))
+    for p in range(count):
+        ms = np.zeros(wl.n, dtype=int) if p == 0 else rng.integers(0, d)
+        z = np.exp(2j * np.pi * ms / d)
+        out[p, 0, 0], out[p, 0, 1] = z.real, z.imag
+    return out
+
+
 def summarize(ms, stats):
     iters = sum(s["newton_iters"] for s in stats)
     pcs = sum(s["steps"] for s in stats)
@@ -274,6 +287,8 @@ def main():
     ap.add_argument("--control", choices=["device", "host"], default="device",
                     help="step control on the device (one graph per path segment) or on the "
                          "host (one graph per step, as in the paper)")
+    ap.add_argument("--batch-paths", type=int, default=304,
+                    help="paths of the many-path leg (0 skips it)")
     ap.add_argument("--no-sparse", action="store_true",
                     help="skip the n=512 QD solver roofline measurement")
     args = ap.parse_args()
@@ -341,6 +356,35 @@ def main():
         qd = summarize(msq, statsq)
         qd.pop("launches")
 
+    # many-path form: the same system, distinct total-degree start roots, the
+    # same segment per path, one persistent kernel (ph_track_paths)
+    batch = None
+    if args.batch_paths > 0:
+        bx0 = torch.tensor(batch_starts(wl, args.batch_paths), dtype=torch.float64, device=dev)
+        bxo = torch.empty_like(bx0)
+        bgam = torch.tensor(wl.gamma_soa(), dtype=torch.float64, device=dev)
+        libph.ph_track_paths(ctx.h, f, None, bgam, bx0, seg_params(wl), bxo)   # warm-up
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bstats, _ = libph.ph_track_paths(ctx.h, f, None, bgam, bx0, seg_params(wl), bxo)
+        e1.record(stream)
+        e1.synchronize()
+        bms = e0.elapsed_time(e1)
+        bit = sum(x["newton_iters"] for x in bstats)
+        bops = bit * (ad_ops(wl.f, wl.L) + sum_ops(wl.f, wl.L) + mgs_ops(wl.f.N, wl.n, wl.L))
+        bach = bops / (bms * 1e-3) / 1e9
+        batch = {"paths": args.batch_paths, "ms": bms,
+                 "corrector_steps_per_s": bit / (bms * 1e-3),
+                 "pc_steps_per_s": sum(x["steps"] for x in bstats) / (bms * 1e-3),
+                 "segments_per_s": args.batch_paths / (bms * 1e-3),
+                 "vs_single_path": (bit / (bms * 1e-3)) / value,
+                 "gpu_launches": 1,
+                 "roofline": {"bound": "alu", "kernel": "k_paths (whole step, many paths)",
+                              "achieved": bach, "peak": peak, "unit": "G FP64-ops/s",
+                              "frac": bach / peak}}
+
     # end to end through the same call with host buffers
     e2e_v, h2d, d2h = e2e_leg(libph, ctx, f, wl, max(2, args.steps // 2), torch)
 
@@ -399,7 +443,7 @@ def main():
                        "parallelism": f"replicas x{world}", "control": args.control},
             "segments_per_s": s["paths_per_s"], "pc_steps_per_s": s["pc_steps_per_s"],
             "p50_segment_ms": s["p50_segment_ms"], "p99_segment_ms": s["p99_segment_ms"],
-            "path": s["path"], "qd": qd,
+            "path": s["path"], "qd": qd, "batched": batch,
             "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": s["launches"], "roofline": roof, "roofline_sparse512_mgs": roof512,

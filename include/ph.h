@@ -173,6 +173,22 @@ ph_status ph_track_path(ph_ctx *ctx, const ph_system *f, const ph_system *g,
                         const ph_track_params *params, double *x_out,
                         ph_path_stats *stats, ph_step_record *log, int log_cap);
 
+/* Tracks npaths solution paths of the same homotopy, each from its own start
+ * point, to t = 1: the many-path form.  The paper accelerates one path at a
+ * time (Section 3; many paths are its companion work); this entry point keeps
+ * the GPU busy with many.  One persistent kernel: each thread block takes the
+ * next unstarted path, tracks it to its end with the same predictor, corrector,
+ * MGS and step control as ph_track_path (params->control is ignored), stores
+ * the end point and takes the next path, so paths of uneven length balance.
+ *   x0     [npaths][L][2][n] start points; x_out [npaths][L][2][n] end points;
+ *   stats  [npaths] (may be NULL); log [npaths][log_cap] (may be NULL/0): the
+ *          first log_cap steps of each path.
+ * Returns PH_OK when the launch completed; each path's status is in stats. */
+ph_status ph_track_paths(ph_ctx *ctx, const ph_system *f, const ph_system *g,
+                         const double *gamma, int npaths, const double *x0,
+                         const ph_track_params *params, double *x_out, ph_path_stats *stats,
+                         ph_step_record *log, int log_cap);
+
 /* Host-side step-size controller of the path tracker, exported so it can be
  * checked without a GPU: the same code runs inside the device controller.
  * Fig. "Accelerated tracking of one single path". */

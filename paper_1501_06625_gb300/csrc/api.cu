@@ -59,7 +59,8 @@ extern "C" ph_status ph_destroy(ph_ctx *c) {
   DevBuf *bufs[] = {&c->in_x, &c->in_gamma, &c->in_t, &c->in_J, &c->in_rhs, &c->out_h,
                     &c->out_J, &c->out_dx, &c->slots, &c->ptab, &c->scal, &c->A, &c->R,
                     &c->nrm2, &c->irkk, &c->dxv, &c->state, &c->hist, &c->xw, &c->logbuf,
-                    &c->ystage, &c->flags};
+                    &c->ystage, &c->flags, &c->spow, &c->bws, &c->bq, &c->bx0, &c->bxo,
+                    &c->bstats, &c->blog};
   for (DevBuf *b : bufs) b->release();
   delete c;
   return PH_OK;

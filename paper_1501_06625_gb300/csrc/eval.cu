@@ -20,65 +20,21 @@
 //          -h (the right-hand side of the Newton system) and max |h_i|.
 #include "internal.h"
 #include "mp.cuh"
+#include "pathdev.cuh"
 
 using namespace ph;
 
 namespace {
 
 template <class P>
-PHD cx<P> c_pow(cx<P> x, int e) {
-  cx<P> r = c_from<P>(1.0, 0.0);
-  bool first = true;
-  while (e > 0) {
-    if (e & 1) {
-      r = first ? x : c_mul<P>(r, x);
-      first = false;
-    }
-    e >>= 1;
-    if (e) x = c_mul<P>(x, x);
-  }
-  return r;
-}
-
-template <class P>
-PHD cx<P> shfl_down_c(const cx<P> &a, int off, int width) {
-  cx<P> z;
-#pragma unroll
-  for (int l = 0; l < P::L; ++l) {
-    P::set_limb(z.re, l, __shfl_down_sync(0xffffffffu, P::limb(a.re, l), off, width));
-    P::set_limb(z.im, l, __shfl_down_sync(0xffffffffu, P::limb(a.im, l), off, width));
-  }
-  return z;
-}
-
-template <class P>
 __global__ void k_prep(const double *__restrict__ x, int n, int emax, double *__restrict__ ptab,
+                       const int32_t *__restrict__ deg, double *__restrict__ spow,
                        const double *__restrict__ t, const double *__restrict__ gamma, int k,
                        double *__restrict__ scal, const int *__restrict__ skip) {
   if (skip && *skip) return;
-  const long pl = 2L * P::L * n;
   int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < n) {
-    cx<P> xj = c_load<P>(x, n, j);
-    c_store<P>(ptab, n, j, xj);
-    cx<P> p = xj;
-    for (int e = 2; e < emax; ++e) {
-      p = c_mul<P>(p, xj);
-      c_store<P>(ptab + (e - 1) * pl, n, j, p);
-    }
-  }
-  if (gamma && blockIdx.x == 0 && threadIdx.x == 0) {
-    typename P::real tt = r_load<P>(t, 1, 0);
-    typename P::real omt = P::sub(P::from(1.0), tt);
-    typename P::real tk = P::from(1.0), ok = P::from(1.0);
-    for (int e = 0; e < k; ++e) {
-      tk = P::mul(tk, tt);
-      ok = P::mul(ok, omt);
-    }
-    cx<P> g = c_load<P>(gamma, 1, 0);
-    r_store<P>(scal, 1, 0, tk);
-    c_store<P>(scal + P::L, 1, 0, c_mul_real<P>(g, ok));
-  }
+  if (j < n) prep_variable<P>(j, x, n, emax, ptab, deg, spow);
+  if (gamma && blockIdx.x == 0 && threadIdx.x == 0) prep_factors<P>(t, gamma, k, scal);
 }
 
 template <class P>
@@ -92,30 +48,7 @@ __global__ void __launch_bounds__(128) k_ad(int M, int Mp, const int32_t *__rest
   if (skip && *skip) return;
   int s = s0 + blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= M) return;
-  const long pl = 2L * P::L * n;
-  const int v = nv[s];
-  cx<P> c = c_load<P>(coeff, Mp, s);
-  for (int p = 0; p < v; ++p) {
-    int a = vexp[(long)p * Mp + s];
-    if (a >= 2) c = c_mul<P>(c, c_load<P>(ptab + (a - 2) * pl, n, vidx[(long)p * Mp + s]));
-  }
-  cx<P> pre = c;
-  for (int p = 0; p < v; ++p) {
-    c_store<P>(slots, nslots, (long)p * Mp + s, pre);
-    pre = c_mul<P>(pre, c_load<P>(ptab, n, vidx[(long)p * Mp + s]));
-  }
-  c_store<P>(slots, nslots, (long)maxv * Mp + s, pre);
-  cx<P> suf = c_zero<P>();
-  for (int p = v - 1; p >= 0; --p) {
-    cx<P> d = c_load<P>(slots, nslots, (long)p * Mp + s);
-    if (p < v - 1) d = c_mul<P>(d, suf);
-    d = c_mul_int<P>(d, vexp[(long)p * Mp + s]);
-    c_store<P>(slots, nslots, (long)p * Mp + s, d);
-    if (p > 0) {
-      cx<P> xj = c_load<P>(ptab, n, vidx[(long)p * Mp + s]);
-      suf = (p == v - 1) ? xj : c_mul<P>(suf, xj);
-    }
-  }
+  ad_term<P>(s, Mp, nv, vidx, vexp, coeff, ptab, n, maxv, slots, nslots);
 }
 
 template <class P>
@@ -223,53 +156,24 @@ __global__ void __launch_bounds__(256) k_sum(
     int N, int n, int nout, const int32_t *__restrict__ optr, const int32_t *__restrict__ oslot,
     const double *__restrict__ slots, long nslots, const int32_t *__restrict__ goptr,
     const int32_t *__restrict__ goslot, const double *__restrict__ gslots, long gnslots,
-    const int32_t *__restrict__ deg, const double *__restrict__ x,
-    const double *__restrict__ scal, int homotopy, double *__restrict__ J, long ldJ, long Jplane,
-    double *__restrict__ h, double *__restrict__ rhs, long rhs_plane,
-    unsigned long long *__restrict__ res_bits, const int *__restrict__ skip) {
+    const double *__restrict__ spow, const double *__restrict__ scal, int homotopy,
+    double *__restrict__ J, long ldJ, long Jplane, double *__restrict__ h,
+    double *__restrict__ rhs, long rhs_plane, unsigned long long *__restrict__ res_bits,
+    const int *__restrict__ skip) {
   if (skip && *skip) return;
   long gt = (long)blockIdx.x * blockDim.x + threadIdx.x;
   int o = (int)(gt / G);
   int lane = (int)(gt % G);
   bool active = o < nout;
-  cx<P> af = c_zero<P>(), ag = c_zero<P>();
-  if (active) {
-    for (int q = optr[o] + lane; q < optr[o + 1]; q += G)
-      af = c_add<P>(af, c_load<P>(slots, nslots, oslot[q]));
-    if (goptr)
-      for (int q = goptr[o] + lane; q < goptr[o + 1]; q += G)
-        ag = c_add<P>(ag, c_load<P>(gslots, gnslots, goslot[q]));
-  }
-#pragma unroll
-  for (int off = G / 2; off > 0; off >>= 1) {
-    af = c_add<P>(af, shfl_down_c<P>(af, off, G));
-    if (goptr) ag = c_add<P>(ag, shfl_down_c<P>(ag, off, G));
-  }
+  cx<P> val = sum_output<P, G>(active, o, lane, N, n, optr, oslot, slots, nslots, goptr, goslot,
+                               gslots, gnslots, spow, scal, homotopy);
   if (!active || lane != 0) return;
-  cx<P> val = af;
-  cx<P> sg = c_zero<P>();
-  if (homotopy) {
-    typename P::real sf = r_load<P>(scal, 1, 0);
-    sg = c_load<P>(scal + P::L, 1, 0);
-    val = c_mul_real<P>(af, sf);
-    if (goptr) val = c_add<P>(val, c_mul<P>(sg, ag));
-  }
   const int nN = n * N;
   if (o < nN) {
     int j = o / N, i = o - j * N;
-    if (homotopy && !goptr && i == j) {            // d_i x_i^{d_i - 1}
-      int d = deg[i];
-      cx<P> pw = c_mul_d<P>(c_pow<P>(c_load<P>(x, n, i), d - 1), (double)d);
-      val = c_add<P>(val, c_mul<P>(sg, pw));
-    }
     c_store<P>(J + (long)j * ldJ, Jplane, i, val);
   } else {
     int i = o - nN;
-    if (homotopy && !goptr) {                       // x_i^{d_i} - 1
-      cx<P> pw = c_pow<P>(c_load<P>(x, n, i), deg[i]);
-      pw.re = P::sub(pw.re, P::from(1.0));
-      val = c_add<P>(val, c_mul<P>(sg, pw));
-    }
     if (h) c_store<P>(h, N, i, val);
     if (rhs) c_store<P>(rhs, rhs_plane, i, c_neg<P>(val));
     if (res_bits) atomicMax(res_bits, (unsigned long long)__double_as_longlong(c_mag_lead<P>(val)));
@@ -315,6 +219,9 @@ cudaError_t eval_impl(ph_ctx *ctx, const ph_system *f, const ph_system *g, const
   cudaError_t e;
   if ((e = ctx->ptab.ensure(sizeof(double) * 2 * L * (size_t)n * ntab)) != cudaSuccess) return e;
   if ((e = ctx->scal.ensure(sizeof(double) * 3 * L)) != cudaSuccess) return e;
+  if ((e = ctx->spow.ensure(sizeof(double) * 4 * L * (size_t)n)) != cudaSuccess) return e;
+  // the total-degree start system's powers are needed only with a homotopy and no g
+  double *spow = (gamma && !g) ? ctx->spow.as<double>() : nullptr;
   const long fs = (long)(f->maxv + 1) * f->Mp;
   const long gs = g ? (long)(g->maxv + 1) * g->Mp : 0;
   if ((e = ctx->slots.ensure(sizeof(double) * 2 * L * (size_t)(fs + gs + 1))) != cudaSuccess) return e;
@@ -323,7 +230,8 @@ cudaError_t eval_impl(ph_ctx *ctx, const ph_system *f, const ph_system *g, const
   cudaStream_t st = ctx->stream;
 
   if (parts & 1)
-    k_prep<P><<<(n + 127) / 128, 128, 0, st>>>(x, n, emax, ptab, t, gamma, k, scal, skip);
+    k_prep<P><<<(n + 127) / 128, 128, 0, st>>>(x, n, emax, ptab, f->deg.as<int32_t>(), spow, t,
+                                               gamma, k, scal, skip);
   if (parts & 2) {
     if (f->M > 0) ad_launch<P>(f, ptab, n, fslots, fs, skip, st);
     if (g && g->M > 0) ad_launch<P>(g, ptab, n, gslots, gs, skip, st);
@@ -334,8 +242,7 @@ cudaError_t eval_impl(ph_ctx *ctx, const ph_system *f, const ph_system *g, const
   k_sum<P, G><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
       N, n, f->nout, f->out_ptr.as<int32_t>(), f->out_slot.as<int32_t>(), fslots, fs,
       g ? g->out_ptr.as<int32_t>() : nullptr, g ? g->out_slot.as<int32_t>() : nullptr, gslots, gs,
-      f->deg.as<int32_t>(), x, scal, gamma != nullptr, J, ldJ, Jplane, h, rhs, rhs_plane,
-      res_bits, skip);
+      spow, scal, gamma != nullptr, J, ldJ, Jplane, h, rhs, rhs_plane, res_bits, skip);
   return cudaGetLastError();
 }
 

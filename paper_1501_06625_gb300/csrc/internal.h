@@ -65,7 +65,8 @@ struct ph_ctx {
   std::string err;
   DevBuf in_x, in_gamma, in_t, in_J, in_rhs;       // staged host inputs
   DevBuf out_h, out_J, out_dx;                      // staged outputs
-  DevBuf slots, ptab, scal, A, R, nrm2, irkk, dxv, state, hist, xw, logbuf, ystage, flags;
+  DevBuf slots, ptab, scal, A, R, nrm2, irkk, dxv, state, hist, xw, logbuf, ystage, flags, spow;
+  DevBuf bws, bq, bx0, bxo, bstats, blog;           // many-path tracking
 };
 
 // A loaded polynomial system: the instruction layout of Section 3.2 (terms

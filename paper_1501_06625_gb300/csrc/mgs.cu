@@ -39,6 +39,7 @@
 // context stays usable.
 #include "internal.h"
 #include "mp.cuh"
+#include "pathdev.cuh"
 
 using namespace ph;
 
@@ -87,105 +88,6 @@ __device__ void publish(int *flag, int tag) {
     *(volatile int *)flag = tag;
   }
 }
-
-// ---- per-part arithmetic (one real component of a complex quantity) -------------
-//
-// acc: an accumulator of real terms; dot2(x1,y1,x2,y2,sg) adds x1 y1 + sg x2 y2;
-// sq(x) adds x^2; upd(a, ar, b, ai, c, sg) = a - ar b + sg ai c.
-
-template <class P> struct Part {
-  typedef typename P::real real;
-  struct acc { real v; };
-  PHD static acc zero() { return {P::zero()}; }
-  PHD static void dot2(acc &a, const real &x1, const real &y1, const real &x2, const real &y2,
-                       double sg) {
-    real t = P::mul(x2, y2);
-    if (sg < 0) t = P::neg(t);
-    a.v = P::add(a.v, P::add(P::mul(x1, y1), t));
-  }
-  PHD static void sq(acc &a, const real &x) { a.v = P::add(a.v, P::mul(x, x)); }
-  PHD static acc combine(const acc &a, const acc &b) { return {P::add(a.v, b.v)}; }
-  PHD static acc shfl(const acc &a, int m) {
-    acc z;
-#pragma unroll
-    for (int l = 0; l < P::L; ++l)
-      P::set_limb(z.v, l, __shfl_xor_sync(0xffffffffu, P::limb(a.v, l), m));
-    return z;
-  }
-  PHD static real value(const acc &a) { return a.v; }
-  PHD static real upd(const real &a, const real &ar, const real &b, const real &ai,
-                      const real &c, double sg) {
-    real t = P::mul(ai, c);
-    if (sg < 0) t = P::neg(t);
-    return P::add(a, P::sub(t, P::mul(ar, b)));
-  }
-};
-
-// double-double: Dot2-style unnormalised (s, c) accumulation
-template <> struct Part<DD> {
-  typedef dd real;
-  struct acc { double s, c; };
-  PHD static acc zero() { return {0.0, 0.0}; }
-  PHD static void add_term(acc &a, double p) {
-    double s, e;
-    ph::two_sum(a.s, p, s, e);
-    a.s = s;
-    a.c = ph::fadd(a.c, e);
-  }
-  PHD static void dot2(acc &a, const dd &x1, const dd &y1, const dd &x2, const dd &y2, double sg) {
-    double p1, e1, p2, e2;
-    ph::two_prod(x1.h, y1.h, p1, e1);
-    ph::two_prod(sg * x2.h, y2.h, p2, e2);
-    double lo = ph::fadd(e1, e2);
-    lo = ph::ffma(x1.h, y1.l, lo);
-    lo = ph::ffma(x1.l, y1.h, lo);
-    lo = ph::ffma(sg * x2.h, y2.l, lo);
-    lo = ph::ffma(sg * x2.l, y2.h, lo);
-    add_term(a, p1);
-    add_term(a, p2);
-    a.c = ph::fadd(a.c, lo);
-  }
-  PHD static void sq(acc &a, const dd &x) {
-    double p, e;
-    ph::two_prod(x.h, x.h, p, e);
-    e = ph::ffma(2.0 * x.h, x.l, e);
-    add_term(a, p);
-    a.c = ph::fadd(a.c, e);
-  }
-  PHD static acc combine(const acc &a, const acc &b) {
-    acc z;
-    double e;
-    ph::two_sum(a.s, b.s, z.s, e);
-    z.c = ph::fadd(ph::fadd(a.c, b.c), e);
-    return z;
-  }
-  PHD static acc shfl(const acc &a, int m) {
-    return {__shfl_xor_sync(0xffffffffu, a.s, m), __shfl_xor_sync(0xffffffffu, a.c, m)};
-  }
-  PHD static dd value(const acc &a) {
-    double s, e;
-    ph::fast_two_sum(a.s, a.c, s, e);
-    return {s, e};
-  }
-  // a - ar b + sg ai c with one renormalisation
-  PHD static dd upd(const dd &a, const dd &ar, const dd &b, const dd &ai, const dd &c, double sg) {
-    double p1, e1, p2, e2, s, es1, es2;
-    ph::two_prod(ar.h, b.h, p1, e1);
-    ph::two_prod(sg * ai.h, c.h, p2, e2);
-    ph::two_sum(a.h, -p1, s, es1);
-    ph::two_sum(s, p2, s, es2);
-    double lo = ph::fadd(ph::fadd(a.l, es1), es2);
-    lo = ph::fsub(lo, e1);
-    lo = ph::fadd(lo, e2);
-    lo = ph::ffma(-ar.h, b.l, lo);
-    lo = ph::ffma(-ar.l, b.h, lo);
-    lo = ph::ffma(sg * ai.h, c.l, lo);
-    lo = ph::ffma(sg * ai.l, c.h, lo);
-    double z, zl;
-    ph::fast_two_sum(s, lo, z, zl);
-    return {z, zl};
-  }
-};
 
 // Sum of the block's four warps by part: warps {0,1} -> part 0, {2,3} -> part 1.
 // Returns this warp's part total (normalised) to every lane.

@@ -341,6 +341,21 @@ template <class P> PHD cx<P> c_mul(const cx<P> &a, const cx<P> &b) { return cops
 template <class P> PHD cx<P> c_conj_mul(const cx<P> &a, const cx<P> &b) { return cops<P>::conj_mul(a, b); }
 template <class P> PHD typename P::real c_abs2(const cx<P> &a) { return cops<P>::abs2(a); }
 
+// x^e by binary powering (e >= 0)
+template <class P> PHD cx<P> c_pow(cx<P> x, int e) {
+  cx<P> r = c_from<P>(1.0, 0.0);
+  bool first = true;
+  while (e > 0) {
+    if (e & 1) {
+      r = first ? x : cops<P>::mul(r, x);
+      first = false;
+    }
+    e >>= 1;
+    if (e) x = cops<P>::mul(x, x);
+  }
+  return r;
+}
+
 // multiply by a small positive integer exponent
 template <class P> PHD cx<P> c_mul_int(const cx<P> &a, int k) {
   if (k == 1) return a;

@@ -1,0 +1,242 @@
+// pathdev.cuh -- device functions of the evaluation shared by the single-path
+// kernels (eval.cu) and the many-path kernel (batch.cu).
+//
+// Layouts (see system.cu): sorted term s at position p reads vidx/vexp[p*Mp+s];
+// its partial derivative with respect to that variable goes to slot p*Mp+s and
+// its value to slot maxv*Mp+s of a slot buffer [2L][nslots]; ptab holds x^e at
+// [(e-1)][2L][n]; spow holds the start system's d_i x_i^{d_i-1} at [0][2L][n]
+// and x_i^{d_i} - 1 at [1][2L][n].
+#pragma once
+#include "mp.cuh"
+
+namespace ph {
+
+// Powers of one variable for the power table (x^1 .. x^{emax-1}) and, for the
+// total-degree start system, d x^{d-1} and x^d - 1.
+template <class P>
+__device__ void prep_variable(int j, const double *__restrict__ x, int n, int emax,
+                              double *__restrict__ ptab, const int32_t *__restrict__ deg,
+                              double *__restrict__ spow) {
+  const long pl = 2L * P::L * n;
+  cx<P> xj = c_load<P>(x, n, j);
+  c_store<P>(ptab, n, j, xj);
+  cx<P> p = xj;
+  for (int e = 2; e < emax; ++e) {
+    p = c_mul<P>(p, xj);
+    c_store<P>(ptab + (e - 1) * pl, n, j, p);
+  }
+  if (spow) {
+    const int d = deg[j];
+    cx<P> pw = c_pow<P>(xj, d - 1);                       // x^{d-1}
+    c_store<P>(spow, n, j, c_mul_d<P>(pw, (double)d));
+    cx<P> xd = c_mul<P>(pw, xj);
+    xd.re = P::sub(xd.re, P::from(1.0));
+    c_store<P>(spow + pl, n, j, xd);
+  }
+}
+
+// t^k (real) and gamma (1-t)^k (complex) into scal: [L] then [2L]
+template <class P>
+__device__ void prep_factors(const double *__restrict__ t, const double *__restrict__ gamma,
+                             int k, double *__restrict__ scal) {
+  typename P::real tt = r_load<P>(t, 1, 0);
+  typename P::real omt = P::sub(P::from(1.0), tt);
+  typename P::real tk = P::from(1.0), ok = P::from(1.0);
+  for (int e = 0; e < k; ++e) {
+    tk = P::mul(tk, tt);
+    ok = P::mul(ok, omt);
+  }
+  cx<P> g = c_load<P>(gamma, 1, 0);
+  r_store<P>(scal, 1, 0, tk);
+  c_store<P>(scal + P::L, 1, 0, c_mul_real<P>(g, ok));
+}
+
+// Reverse-mode differentiation of sorted term s by one thread: the common
+// factor prod x_j^{a_j-1} is folded into the coefficient, then forward prefix
+// products (parked in the slots), backward suffix and cross products:
+//   d/dx_j (c x^a) = a_j (c CF x_1..x_{j-1}) (x_{j+1}..x_v).
+template <class P>
+__device__ void ad_term(int s, int Mp, const int32_t *__restrict__ nv,
+                        const int32_t *__restrict__ vidx, const int32_t *__restrict__ vexp,
+                        const double *__restrict__ coeff, const double *__restrict__ ptab, int n,
+                        int maxv, double *__restrict__ slots, long nslots) {
+  const long pl = 2L * P::L * n;
+  const int v = nv[s];
+  cx<P> c = c_load<P>(coeff, Mp, s);
+  for (int p = 0; p < v; ++p) {
+    int a = vexp[(long)p * Mp + s];
+    if (a >= 2) c = c_mul<P>(c, c_load<P>(ptab + (a - 2) * pl, n, vidx[(long)p * Mp + s]));
+  }
+  cx<P> pre = c;
+  for (int p = 0; p < v; ++p) {
+    c_store<P>(slots, nslots, (long)p * Mp + s, pre);
+    pre = c_mul<P>(pre, c_load<P>(ptab, n, vidx[(long)p * Mp + s]));
+  }
+  c_store<P>(slots, nslots, (long)maxv * Mp + s, pre);
+  cx<P> suf = c_zero<P>();
+  for (int p = v - 1; p >= 0; --p) {
+    cx<P> d = c_load<P>(slots, nslots, (long)p * Mp + s);
+    if (p < v - 1) d = c_mul<P>(d, suf);
+    d = c_mul_int<P>(d, vexp[(long)p * Mp + s]);
+    c_store<P>(slots, nslots, (long)p * Mp + s, d);
+    if (p > 0) {
+      cx<P> xj = c_load<P>(ptab, n, vidx[(long)p * Mp + s]);
+      suf = (p == v - 1) ? xj : c_mul<P>(suf, xj);
+    }
+  }
+}
+
+template <class P>
+PHD cx<P> shfl_down_c(const cx<P> &a, int off, int width) {
+  cx<P> z;
+#pragma unroll
+  for (int l = 0; l < P::L; ++l) {
+    P::set_limb(z.re, l, __shfl_down_sync(0xffffffffu, P::limb(a.re, l), off, width));
+    P::set_limb(z.im, l, __shfl_down_sync(0xffffffffu, P::limb(a.im, l), off, width));
+  }
+  return z;
+}
+
+// Summation of output o by the G lanes of a group (every lane of the warp must
+// call this, active or not).  Returns the finished output on lane 0 of the
+// group: the sum of its slots (in the order of the terms), times t^k when a
+// homotopy is evaluated, plus gamma (1-t)^k times the start system's term
+// (from g's slots, or from spow for the total-degree system).
+template <class P, int G>
+__device__ cx<P> sum_output(bool active, int o, int lane, int N, int n,
+                            const int32_t *__restrict__ optr, const int32_t *__restrict__ oslot,
+                            const double *__restrict__ slots, long nslots,
+                            const int32_t *__restrict__ goptr, const int32_t *__restrict__ goslot,
+                            const double *__restrict__ gslots, long gnslots,
+                            const double *__restrict__ spow, const double *__restrict__ scal,
+                            int homotopy) {
+  cx<P> af = c_zero<P>(), ag = c_zero<P>();
+  if (active) {
+    for (int q = optr[o] + lane; q < optr[o + 1]; q += G)
+      af = c_add<P>(af, c_load<P>(slots, nslots, oslot[q]));
+    if (goptr)
+      for (int q = goptr[o] + lane; q < goptr[o + 1]; q += G)
+        ag = c_add<P>(ag, c_load<P>(gslots, gnslots, goslot[q]));
+  }
+#pragma unroll
+  for (int off = G / 2; off > 0; off >>= 1) {
+    af = c_add<P>(af, shfl_down_c<P>(af, off, G));
+    if (goptr) ag = c_add<P>(ag, shfl_down_c<P>(ag, off, G));
+  }
+  if (!active || lane != 0 || !homotopy) return af;
+  const typename P::real sf = r_load<P>(scal, 1, 0);
+  const cx<P> sg = c_load<P>(scal + P::L, 1, 0);
+  cx<P> val = c_mul_real<P>(af, sf);
+  if (goptr) return c_add<P>(val, c_mul<P>(sg, ag));
+  const int nN = n * N;
+  const long pl = 2L * P::L * n;
+  if (o < nN) {
+    int j = o / N, i = o - j * N;
+    if (i == j) val = c_add<P>(val, c_mul<P>(sg, c_load<P>(spow, n, i)));
+  } else {
+    val = c_add<P>(val, c_mul<P>(sg, c_load<P>(spow + pl, n, o - nN)));
+  }
+  return val;
+}
+
+// ---- per-part arithmetic (one real component of a complex quantity) -------------
+//
+// acc: an accumulator of real terms; dot2(x1,y1,x2,y2,sg) adds x1 y1 + sg x2 y2;
+// sq(x) adds x^2; upd(a, ar, b, ai, c, sg) = a - ar b + sg ai c.
+
+template <class P> struct Part {
+  typedef typename P::real real;
+  struct acc { real v; };
+  PHD static acc zero() { return {P::zero()}; }
+  PHD static void dot2(acc &a, const real &x1, const real &y1, const real &x2, const real &y2,
+                       double sg) {
+    real t = P::mul(x2, y2);
+    if (sg < 0) t = P::neg(t);
+    a.v = P::add(a.v, P::add(P::mul(x1, y1), t));
+  }
+  PHD static void sq(acc &a, const real &x) { a.v = P::add(a.v, P::mul(x, x)); }
+  PHD static acc combine(const acc &a, const acc &b) { return {P::add(a.v, b.v)}; }
+  PHD static acc shfl(const acc &a, int m) {
+    acc z;
+#pragma unroll
+    for (int l = 0; l < P::L; ++l)
+      P::set_limb(z.v, l, __shfl_xor_sync(0xffffffffu, P::limb(a.v, l), m));
+    return z;
+  }
+  PHD static real value(const acc &a) { return a.v; }
+  PHD static real upd(const real &a, const real &ar, const real &b, const real &ai,
+                      const real &c, double sg) {
+    real t = P::mul(ai, c);
+    if (sg < 0) t = P::neg(t);
+    return P::add(a, P::sub(t, P::mul(ar, b)));
+  }
+};
+
+// double-double: Dot2-style unnormalised (s, c) accumulation
+template <> struct Part<DD> {
+  typedef dd real;
+  struct acc { double s, c; };
+  PHD static acc zero() { return {0.0, 0.0}; }
+  PHD static void add_term(acc &a, double p) {
+    double s, e;
+    ph::two_sum(a.s, p, s, e);
+    a.s = s;
+    a.c = ph::fadd(a.c, e);
+  }
+  PHD static void dot2(acc &a, const dd &x1, const dd &y1, const dd &x2, const dd &y2, double sg) {
+    double p1, e1, p2, e2;
+    ph::two_prod(x1.h, y1.h, p1, e1);
+    ph::two_prod(sg * x2.h, y2.h, p2, e2);
+    double lo = ph::fadd(e1, e2);
+    lo = ph::ffma(x1.h, y1.l, lo);
+    lo = ph::ffma(x1.l, y1.h, lo);
+    lo = ph::ffma(sg * x2.h, y2.l, lo);
+    lo = ph::ffma(sg * x2.l, y2.h, lo);
+    add_term(a, p1);
+    add_term(a, p2);
+    a.c = ph::fadd(a.c, lo);
+  }
+  PHD static void sq(acc &a, const dd &x) {
+    double p, e;
+    ph::two_prod(x.h, x.h, p, e);
+    e = ph::ffma(2.0 * x.h, x.l, e);
+    add_term(a, p);
+    a.c = ph::fadd(a.c, e);
+  }
+  PHD static acc combine(const acc &a, const acc &b) {
+    acc z;
+    double e;
+    ph::two_sum(a.s, b.s, z.s, e);
+    z.c = ph::fadd(ph::fadd(a.c, b.c), e);
+    return z;
+  }
+  PHD static acc shfl(const acc &a, int m) {
+    return {__shfl_xor_sync(0xffffffffu, a.s, m), __shfl_xor_sync(0xffffffffu, a.c, m)};
+  }
+  PHD static dd value(const acc &a) {
+    double s, e;
+    ph::fast_two_sum(a.s, a.c, s, e);
+    return {s, e};
+  }
+  // a - ar b + sg ai c with one renormalisation
+  PHD static dd upd(const dd &a, const dd &ar, const dd &b, const dd &ai, const dd &c, double sg) {
+    double p1, e1, p2, e2, s, es1, es2;
+    ph::two_prod(ar.h, b.h, p1, e1);
+    ph::two_prod(sg * ai.h, c.h, p2, e2);
+    ph::two_sum(a.h, -p1, s, es1);
+    ph::two_sum(s, p2, s, es2);
+    double lo = ph::fadd(ph::fadd(a.l, es1), es2);
+    lo = ph::fsub(lo, e1);
+    lo = ph::fadd(lo, e2);
+    lo = ph::ffma(-ar.h, b.l, lo);
+    lo = ph::ffma(-ar.l, b.h, lo);
+    lo = ph::ffma(sg * ai.h, c.l, lo);
+    lo = ph::ffma(sg * ai.l, c.h, lo);
+    double z, zl;
+    ph::fast_two_sum(s, lo, z, zl);
+    return {z, zl};
+  }
+};
+
+
+}  // namespace ph

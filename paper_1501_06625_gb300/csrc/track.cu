@@ -432,6 +432,7 @@ extern "C" ph_status ph_track_path(ph_ctx *ctx, const ph_system *f, const ph_sys
     long fs = (long)(f->maxv + 1) * f->Mp, gs = g ? (long)(g->maxv + 1) * g->Mp : 0;
     PH_CUDA(ctx, ctx->ptab.ensure(sizeof(double) * 2 * L * (size_t)n * ntab));
     PH_CUDA(ctx, ctx->scal.ensure(sizeof(double) * 3 * L));
+    PH_CUDA(ctx, ctx->spow.ensure(sizeof(double) * 4 * L * (size_t)n));
     PH_CUDA(ctx, ctx->slots.ensure(sizeof(double) * 2 * L * (size_t)(fs + gs + 1)));
     PH_CUDA(ctx, ctx->R.ensure(sizeof(double) * 2 * L * (size_t)(n + 1) * (n + 1)));
     PH_CUDA(ctx, ctx->nrm2.ensure(sizeof(double) * L * (size_t)(n + 1)));
@@ -457,7 +458,7 @@ extern "C" ph_status ph_track_path(ph_ctx *ctx, const ph_system *f, const ph_sys
 
   TrackCache *c = get_cache(ctx);
   void *bufs[16] = {st, hist, xw, dx, A, dgam, dlog, ctx->slots.p, ctx->ptab.p, ctx->scal.p,
-                    ctx->R.p, ctx->nrm2.p, ctx->irkk.p, ctx->flags.p, nullptr, nullptr};
+                    ctx->R.p, ctx->nrm2.p, ctx->irkk.p, ctx->flags.p, ctx->spow.p, nullptr};
   bool same = c->tg.valid && c->tg.f == f && c->tg.g == g && c->tg.log_cap == log_cap &&
               memcmp(&c->tg.p, &p, sizeof p) == 0 && memcmp(c->tg.bufs, bufs, sizeof bufs) == 0 &&
               c->tg.stream == ctx->stream;

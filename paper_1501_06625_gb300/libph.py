@@ -53,7 +53,7 @@ class CtrlState(C.Structure):
 EXPORTS = ["ph_init", "ph_destroy", "ph_last_error", "ph_system_load", "ph_system_free",
            "ph_eval_jac", "ph_mgs_solve", "ph_track_path", "ph_ctrl_init", "ph_ctrl_next_t",
            "ph_ctrl_report", "ph_version", "ph_profile_newton", "ph_fp64_peak",
-           "ph_mgs_solve_static"]
+           "ph_mgs_solve_static", "ph_track_paths"]
 
 
 class PhError(RuntimeError):
@@ -94,6 +94,8 @@ def lib():
             L.ph_version.restype = C.c_char_p
             L.ph_profile_newton.argtypes = [vp, vp, vp, vp, C.c_int, vp, vp, C.c_int, dp]
             L.ph_fp64_peak.argtypes = [vp, C.c_double, dp]
+            L.ph_track_paths.argtypes = [vp, vp, vp, vp, C.c_int, vp, C.POINTER(TrackParams), vp,
+                                         C.POINTER(PathStats), C.POINTER(StepRecord), C.c_int]
             L.ph_mgs_solve_static.argtypes = [C.c_int, vp, C.c_int, C.c_int, C.c_int, vp, vp, vp,
                                               dp]
             _LIB = L
@@ -206,6 +208,24 @@ def ph_track_path(ctx, f, g, gamma, x0, params: dict, x_out, log_cap: int = 0):
     recs = [dict(t=log[i].t, res=log[i].res, dx=log[i].dx, accepted=log[i].accepted,
                  updates=log[i].updates) for i in range(n)]
     return st, sd, recs
+
+
+def ph_track_paths(ctx, f, g, gamma, x0, params: dict, x_out, log_cap: int = 0):
+    """x0, x_out: [npaths][L][2][n].  Returns (list of stats dicts, list of logs)."""
+    npaths = int(x0.shape[0])
+    p = make_params(params)
+    stats = (PathStats * max(1, npaths))()
+    log = (StepRecord * max(1, npaths * log_cap))()
+    _check(ctx, lib().ph_track_paths(ctx, f, g, _ptr(gamma), npaths, _ptr(x0), C.byref(p),
+                                     _ptr(x_out), stats, log if log_cap > 0 else None, log_cap))
+    sds = [{name: getattr(stats[i], name) for name, _ in PathStats._fields_} for i in range(npaths)]
+    logs = []
+    for i in range(npaths):
+        nrec = min(sds[i]["steps"], log_cap)
+        logs.append([dict(t=log[i * log_cap + r].t, res=log[i * log_cap + r].res,
+                          dx=log[i * log_cap + r].dx, accepted=log[i * log_cap + r].accepted,
+                          updates=log[i * log_cap + r].updates) for r in range(nrec)])
+    return sds, logs
 
 
 def ph_ctrl_init(state: CtrlState, params: dict):
