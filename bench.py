@@ -256,6 +256,86 @@ def batch_starts(wl, count, seed=7):
     return out
 
 
+def serve_leg(libph, synth, ctx, nreq, seed):
+    """A stream of path-tracking requests through the continuous-batching loop
+    (ph_server_*).  A pool of 16 systems per (recipe, precision): n =
+    round(exp(U[ln 16, ln 64])); the dense recipe (n terms per polynomial over
+    min(16, n) variables, exponents {1,2,3}) or the sparse one (a linear term
+    plus 3 two-variable terms, exponents {1,2}) with probability 1/2 each.  A
+    request: double-double with probability 0.7, else quad-double; a system of
+    the pool; a random total-degree start root; the first 20 predictor-corrector
+    steps (adaptive).  Closed loop first (all submitted at once: the capacity),
+    then Poisson arrivals at 0.8 x that capacity (latency under load).  The
+    sequential figure tracks a sample of the same requests one by one with
+    ph_track_path."""
+    rng = np.random.default_rng(seed + 1000)
+    systems = {}
+    reqs = []
+    for _ in range(nreq):
+        dense = bool(rng.random() < 0.5)
+        L = 2 if rng.random() < 0.7 else 4
+        idx = int(rng.integers(0, 16))
+        key = (dense, L, idx)
+        if key not in systems:
+            srng = synth.Rng(seed * 7919 + 131 * idx + 17 * L + int(dense))
+            n = int(round(np.exp(srng.uniform() * (np.log(64) - np.log(16)) + np.log(16))))
+            spec = (synth.dense_system(srng, n, n, min(16, n), (1, 2, 3)) if dense
+                    else synth.sparse_system(srng, n))
+            g = srng.unit_complex()
+            gam = np.zeros((L, 2))
+            gam[0] = [g.real, g.imag]
+            systems[key] = (ctx.load(spec, L), spec, gam, L)
+        f, spec, gam, L = systems[key]
+        d = np.array(spec.degrees())
+        z = np.exp(2j * np.pi * rng.integers(0, d) / d)
+        x0 = np.zeros((L, 2, spec.n))
+        x0[0, 0], x0[0, 1] = z.real, z.imag
+        reqs.append((f, gam, x0, synth.default_params(L, max_steps=19)))
+
+    srv = libph.ph_server_create(ctx.h, max_n=64, pool_bytes=8 << 30, queue_cap=1024)
+    try:
+        def run(arrivals):
+            ids = []
+            t0 = time.perf_counter()
+            for (f, gam, x0, params), ta in zip(reqs, arrivals):
+                while time.perf_counter() - t0 < ta:
+                    pass
+                ids.append(libph.ph_server_submit(ctx.h, srv, f, None, gam, x0, params))
+            lats, iters = [], 0
+            for jid in ids:
+                st, lat = libph.ph_server_wait(ctx.h, srv, jid, 120000)
+                lats.append(lat)
+                iters += st["newton_iters"]
+            return time.perf_counter() - t0, lats, iters
+
+        run([0.0] * min(64, nreq))                       # warm-up
+        wall, lats, iters = run([0.0] * nreq)
+        cap = nreq / wall
+        arrivals = np.cumsum(rng.exponential(1.0 / (0.8 * cap), nreq))
+        wall2, lats2, _ = run(list(arrivals))
+        info = libph.ph_server_info(srv)
+    finally:
+        libph.ph_server_destroy(srv)
+
+    k = min(16, nreq)
+    t0 = time.perf_counter()
+    for f, gam, x0, params in reqs[:k]:
+        libph.ph_track_path(ctx.h, f, None, gam, x0, params, np.zeros_like(x0))
+    seq_rate = k / (time.perf_counter() - t0)
+    return {"requests": nreq,
+            "mix": "n log-uniform in [16,64]; dense/sparse 50/50; DD/QD 70/30; "
+                   "20 adaptive steps per request; 16 systems per recipe and precision",
+            "closed_loop": {"paths_per_s": cap, "corrector_steps_per_s": iters / wall,
+                            "p50_ms": float(np.percentile(lats, 50)),
+                            "p99_ms": float(np.percentile(lats, 99))},
+            "poisson_0.8": {"offered_per_s": 0.8 * cap, "paths_per_s": nreq / wall2,
+                            "p50_ms": float(np.percentile(lats2, 50)),
+                            "p99_ms": float(np.percentile(lats2, 99))},
+            "sequential_single_path": {"paths_per_s": seq_rate, "sample": k},
+            "vs_sequential": cap / seq_rate,
+            "kernel_launches": info["kernel_launches"]}
+
+
 def summarize(ms, stats):
     iters = sum(s["newton_iters"] for s in stats)
     pcs = sum(s["steps"] for s in stats)
@@ -289,6 +369,8 @@ def main():
                          "host (one graph per step, as in the paper)")
     ap.add_argument("--batch-paths", type=int, default=304,
                     help="paths of the many-path leg (0 skips it)")
+    ap.add_argument("--serve-requests", type=int, default=384,
+                    help="requests of the serving leg (0 skips it)")
     ap.add_argument("--no-sparse", action="store_true",
                     help="skip the n=512 QD solver roofline measurement")
     args = ap.parse_args()
@@ -385,6 +467,10 @@ def main():
                               "achieved": bach, "peak": peak, "unit": "G FP64-ops/s",
                               "frac": bach / peak}}
 
+    serve = None
+    if args.serve_requests > 0 and rank == 0:
+        serve = serve_leg(libph, synth, ctx, args.serve_requests, args.seed)
+
     # end to end through the same call with host buffers
     e2e_v, h2d, d2h = e2e_leg(libph, ctx, f, wl, max(2, args.steps // 2), torch)
 
@@ -443,7 +529,7 @@ def main():
                        "parallelism": f"replicas x{world}", "control": args.control},
             "segments_per_s": s["paths_per_s"], "pc_steps_per_s": s["pc_steps_per_s"],
             "p50_segment_ms": s["p50_segment_ms"], "p99_segment_ms": s["p99_segment_ms"],
-            "path": s["path"], "qd": qd, "batched": batch,
+            "path": s["path"], "qd": qd, "batched": batch, "serving": serve,
             "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": s["launches"], "roofline": roof, "roofline_sparse512_mgs": roof512,

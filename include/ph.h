@@ -189,6 +189,52 @@ ph_status ph_track_paths(ph_ctx *ctx, const ph_system *f, const ph_system *g,
                          const ph_track_params *params, double *x_out, ph_path_stats *stats,
                          ph_step_record *log, int log_cap);
 
+/* A continuous-batching request loop for path-tracking jobs of different sizes
+ * and precisions (the paper tracks one path at a time; a service receives jobs
+ * while others run).  Each job gets its own workspace (point, history, step
+ * size, Jacobian) carved from one device pool of pool_bytes: a job is admitted
+ * only when its footprint fits in the free pool, otherwise it waits on the host
+ * in arrival order; a finished job's region returns to the pool.  Admitted jobs
+ * go to a queue in host-mapped memory that one persistent kernel works: each
+ * block claims the next job, tracks it whole (same algorithm as
+ * ph_track_paths), publishes the result and claims the next, so jobs submitted
+ * while others run start as soon as a block is free and overlap them.  A job's
+ * result does not depend on what runs beside it.  A host thread reaps results,
+ * admits waiting jobs and relaunches the kernel when it has gone idle. */
+typedef struct ph_server ph_server;
+typedef struct {
+  int32_t max_n;        /* largest number of variables of a job                 */
+  int32_t max_blocks;   /* resident blocks, 0 = two per SM                      */
+  int64_t pool_bytes;   /* device pool for the jobs' workspaces                 */
+  int32_t queue_cap;    /* jobs on the device at once (table slots)             */
+  int32_t reserved;     /* 0                                                    */
+} ph_server_config;
+
+ph_status ph_server_create(ph_ctx *ctx, const ph_server_config *cfg, ph_server **out);
+/* Submits one job (f, g, gamma, x0 and params as in ph_track_path, host or
+ * device arrays, copied); returns at once with its id.  PH_EINVAL if f has more
+ * than max_n variables, PH_ENOMEM if its workspace exceeds the whole pool. */
+ph_status ph_server_submit(ph_server *srv, const ph_system *f, const ph_system *g,
+                           const double *gamma, const double *x0,
+                           const ph_track_params *params, int64_t *job_id);
+/* *done = 1 and the results (end point [L][2][n], statistics, submit-to-finish
+ * latency in ms, each optional) once the job has finished; the job is then
+ * forgotten.  *done = 0 while it runs. */
+ph_status ph_server_poll(ph_server *srv, int64_t job_id, int *done, double *x_out,
+                         ph_path_stats *stats, double *latency_ms);
+/* ph_server_poll that waits up to timeout_ms (PH_TIMEOUT if not done by then). */
+ph_status ph_server_wait(ph_server *srv, int64_t job_id, int timeout_ms, double *x_out,
+                         ph_path_stats *stats, double *latency_ms);
+/* Jobs waiting for admission and on the device, kernel launches so far, free
+ * pool bytes (each optional). */
+ph_status ph_server_info(ph_server *srv, int64_t *waiting, int64_t *on_device,
+                         int64_t *kernel_launches, int64_t *pool_free_bytes);
+/* Device workspace a job of this homotopy takes from the pool, in bytes. */
+ph_status ph_server_job_bytes(ph_server *srv, const ph_system *f, const ph_system *g,
+                              int64_t *bytes);
+/* Stops the loop (running jobs finish first) and frees the server. */
+ph_status ph_server_destroy(ph_server *srv);
+
 /* Host-side step-size controller of the path tracker, exported so it can be
  * checked without a GPU: the same code runs inside the device controller.
  * Fig. "Accelerated tracking of one single path". */

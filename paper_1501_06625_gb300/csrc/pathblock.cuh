@@ -1,0 +1,411 @@
+// pathblock.cuh -- one thread block tracks one whole path (the many-path and
+// serving forms).  Everything a block needs is in a Job: the homotopy (the
+// target system's instruction arrays, an optional start system, gamma), the
+// tracking parameters, the start point, where the end point and statistics go,
+// and the job's own workspace in device memory.
+//
+// The step follows the same definitions as the single-path kernels (the same
+// controller code, the same Newton tests, the same reverse-mode evaluation);
+// the MGS inside a block is the unnormalised right-looking form with columns
+// dealt round-robin to the 8 warps, the pivot norms in shared memory, and a
+// block barrier per column step.
+#pragma once
+#include "ctrl.h"
+#include "internal.h"
+#include "mp.cuh"
+#include "pathdev.cuh"
+
+namespace ph {
+
+constexpr int kBT = 256;          // threads per block: 8 warps, 2 per SM sub-partition
+constexpr int kNW = kBT / 32;
+constexpr int kHistB = 16;        // accepted points kept for the predictor
+constexpr int kSG = 4;            // lanes per output in the summation
+
+struct Job {
+  int L, N, n, Mf, Mpf, maxvf, Mg, Mpg, maxvg, emax, nout;
+  const int32_t *nvf, *vidxf, *vexpf, *optrf, *oslotf, *deg;
+  const double *coeff_f;
+  const int32_t *nvg, *vidxg, *vexpg, *optrg, *oslotg;    // null: total-degree start
+  const double *coeff_g;
+  const double *gamma;            // [2L]
+  ph_track_params p;
+  const double *x0;               // [2L][n]
+  double *x_out;                  // [2L][n]
+  ph_path_stats *stats;           // one record (may be null)
+  ph_step_record *log;            // log_cap records (may be null)
+  int log_cap;
+  double *ws;                     // this job's workspace
+  long o_x, o_dx, o_hist, o_ptab, o_spow, o_A, o_W, o_fslots, o_gslots, o_scal, o_t, o_g;
+  long ldA, nsf, nsg;
+};
+
+// Workspace layout (doubles, 256-byte aligned regions) of a job.
+struct JobLayout {
+  long o_x, o_dx, o_hist, o_ptab, o_spow, o_A, o_W, o_fslots, o_gslots, o_scal, o_t, o_g, stride;
+};
+
+inline JobLayout job_layout(int L, int n, long ldA, int emax, long nsf, long nsg) {
+  auto up = [](long v) { return (v + 31) / 32 * 32; };
+  const long pt = 2L * L * n, nc = n + 1, ntab = emax > 2 ? emax - 1 : 1;
+  JobLayout o;
+  o.o_x = 0;
+  o.o_dx = o.o_x + up(pt);
+  o.o_hist = o.o_dx + up(pt);
+  o.o_ptab = o.o_hist + up(pt * kHistB);
+  o.o_spow = o.o_ptab + up(pt * ntab);
+  o.o_A = o.o_spow + up(2 * pt);
+  o.o_W = o.o_A + up(2L * L * nc * ldA);
+  o.o_fslots = o.o_W + up(2L * L * nc * nc);
+  o.o_gslots = o.o_fslots + up(2L * L * nsf);
+  o.o_scal = o.o_gslots + up(2L * L * nsg);
+  o.o_t = o.o_scal + up(3L * L);
+  o.o_g = o.o_t + up(L);
+  o.stride = o.o_g + up(2L * L);
+  return o;
+}
+
+// dynamic shared memory of a block for jobs of up to n variables (doubles)
+inline size_t job_smem_bytes(int L, int n) { return sizeof(double) * (2L * L * n + (long)L * (n + 1)); }
+
+// one part (0 = real, 1 = imaginary) of element i of a complex array laid out
+// [limb][re|im][...] with `plane` doubles between planes
+template <class P>
+PHD typename P::real rp_load(const double *v, long plane, int part, long i) {
+  return r_load<P>(v + part * plane, 2 * plane, i);
+}
+template <class P>
+PHD void rp_store(double *v, long plane, int part, long i, const typename P::real &z) {
+  r_store<P>(v + part * plane, 2 * plane, i, z);
+}
+
+template <class P>
+__device__ typename P::real warp_sum_part(typename Part<P>::acc a) {
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) a = Part<P>::combine(a, Part<P>::shfl(a, m));
+  return Part<P>::value(a);
+}
+
+// MGS of [J | -h] (A) and back substitution.  Returns PH_OK or PH_NONFINITE;
+// on success dx and max |dx_i| (in *s_dxmax).
+template <class P>
+__device__ int block_mgs(int N, int n, long ldA, double *A, double *W, double *dx, double *s_nrm,
+                         double *s_y, double *s_dxmax) {
+  typedef typename P::real real;
+  typedef Part<P> PO;
+  __shared__ int s_bad;
+  const int nc = n + 1;
+  const long Ap = (long)nc * ldA, Wp = (long)nc * nc;
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  if (tid == 0) s_bad = 0;
+  if (w == 0) {                                    // ||a_0||^2
+    typename PO::acc ar = PO::zero(), ai = PO::zero();
+    for (int i = lane; i < N; i += 32) {
+      PO::sq(ar, rp_load<P>(A, Ap, 0, i));
+      PO::sq(ai, rp_load<P>(A, Ap, 1, i));
+    }
+    real s = P::add(warp_sum_part<P>(ar), warp_sum_part<P>(ai));
+    if (lane == 0) r_store<P>(s_nrm, nc, 0, s);
+  }
+  for (int k = 0; k < n; ++k) {
+    __syncthreads();
+    const real r2 = r_load<P>(s_nrm, nc, k);
+    const double lead = P::lead(r2);
+    if (!(lead > 0.0) || !isfinite(lead)) {        // the same value in every thread
+      if (tid == 0) s_bad = 1;
+      break;
+    }
+    const real inv2 = P::recip(r2);
+    const double *ak = A + (long)k * ldA;
+    for (int j = k + 1 + (((w - (k + 1)) % kNW) + kNW) % kNW; j <= n; j += kNW) {
+      double *aj = A + (long)j * ldA;
+      typename PO::acc dr = PO::zero(), di = PO::zero();
+      for (int i = lane; i < N; i += 32) {
+        real akr = rp_load<P>(ak, Ap, 0, i), aki = rp_load<P>(ak, Ap, 1, i);
+        real ajr = rp_load<P>(aj, Ap, 0, i), aji = rp_load<P>(aj, Ap, 1, i);
+        PO::dot2(dr, akr, ajr, aki, aji, 1.0);
+        PO::dot2(di, akr, aji, aki, ajr, -1.0);
+      }
+      const real alr = P::mul(warp_sum_part<P>(dr), inv2);
+      const real ali = P::mul(warp_sum_part<P>(di), inv2);
+      if (lane == 0) {
+        rp_store<P>(W + (long)j * nc, Wp, 0, k, alr);
+        rp_store<P>(W + (long)j * nc, Wp, 1, k, ali);
+      }
+      typename PO::acc nr = PO::zero(), ni = PO::zero();
+      for (int i = lane; i < N; i += 32) {
+        real akr = rp_load<P>(ak, Ap, 0, i), aki = rp_load<P>(ak, Ap, 1, i);
+        real ajr = PO::upd(rp_load<P>(aj, Ap, 0, i), alr, akr, ali, aki, 1.0);
+        real aji = PO::upd(rp_load<P>(aj, Ap, 1, i), alr, aki, ali, akr, -1.0);
+        rp_store<P>(aj, Ap, 0, i, ajr);
+        rp_store<P>(aj, Ap, 1, i, aji);
+        if (j == k + 1) {
+          PO::sq(nr, ajr);
+          PO::sq(ni, aji);
+        }
+      }
+      if (j == k + 1) {
+        real s = P::add(warp_sum_part<P>(nr), warp_sum_part<P>(ni));
+        if (lane == 0) r_store<P>(s_nrm, nc, j, s);
+      }
+    }
+  }
+  __syncthreads();
+  if (s_bad) return PH_NONFINITE;
+  // back substitution on y = alpha_{., n} by warp 0: dx_k = y_k, y_i -= alpha_ik dx_k
+  if (w == 0) {
+    const double *yc = W + (long)n * nc;
+    for (int i = lane; i < n; i += 32) c_store<P>(s_y, n, i, c_load<P>(yc, Wp, i));
+    __syncwarp();
+    for (int k = n - 1; k >= 1; --k) {
+      const real xr = rp_load<P>(s_y, n, 0, k), xi = rp_load<P>(s_y, n, 1, k);
+      const double *Wk = W + (long)k * nc;
+      for (int i = lane; i < k; i += 32) {
+        real wr = rp_load<P>(Wk, Wp, 0, i), wi = rp_load<P>(Wk, Wp, 1, i);
+        rp_store<P>(s_y, n, 0, i, PO::upd(rp_load<P>(s_y, n, 0, i), wr, xr, wi, xi, 1.0));
+        rp_store<P>(s_y, n, 1, i, PO::upd(rp_load<P>(s_y, n, 1, i), wr, xi, wi, xr, -1.0));
+      }
+      __syncwarp();
+    }
+    double m = 0.0;
+    for (int i = lane; i < n; i += 32) {
+      cx<P> v = c_load<P>(s_y, n, i);
+      c_store<P>(dx, n, i, v);
+      double mg = c_mag_lead<P>(v);
+      if (!(mg <= m)) m = mg;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      double o = __shfl_xor_sync(0xffffffffu, m, off);
+      if (!(o <= m)) m = o;
+    }
+    if (lane == 0) *s_dxmax = m;
+  }
+  __syncthreads();
+  return PH_OK;
+}
+
+// Tracks the job's path from its start point to its end with the calling
+// block (kBT threads); writes the end point (the last accepted point), the
+// statistics and the step log.  smem: dynamic shared memory for n variables.
+template <class P>
+__device__ void track_job(const Job &a, double *smem) {
+  typedef typename P::real real;
+  double *s_y = smem;                                   // [2L][n]
+  double *s_nrm = smem + 2 * P::L * a.n;                // [L][n+1]
+  __shared__ ph_ctrl_state s_ctrl;
+  __shared__ real s_w[kHistB];
+  __shared__ double s_t[kHistB];
+  __shared__ int s_head, s_count, s_dec, s_ok, s_upd, s_iters, s_bad;
+  __shared__ double s_tn, s_last, s_res, s_dxn, s_dxmax, s_xmax;
+  __shared__ unsigned long long s_resbits;
+  __shared__ ph_path_stats s_st;
+
+  const int n = a.n, N = a.N, tid = threadIdx.x;
+  const long pt = 2L * P::L * n;
+  double *ws = a.ws;
+  double *x = ws + a.o_x, *dx = ws + a.o_dx, *hist = ws + a.o_hist, *ptab = ws + a.o_ptab;
+  double *spow = ws + a.o_spow, *A = ws + a.o_A, *W = ws + a.o_W, *fslots = ws + a.o_fslots;
+  double *gslots = ws + a.o_gslots, *scal = ws + a.o_scal, *tl = ws + a.o_t;
+  const bool fixed = a.p.fixed_steps > 0;
+  const long Ap = (long)(n + 1) * a.ldA;
+  const bool total_degree = a.optrg == nullptr;
+
+  // start: the start point is the only accepted point
+  if (tid == 0) s_bad = 0;
+  __syncthreads();
+  for (long e = tid; e < pt; e += kBT) {
+    double v = a.x0[e];
+    hist[e] = v;
+    if (!isfinite(v)) s_bad = 1;
+  }
+  if (tid == 0) {
+    ctrl_init(&s_ctrl, &a.p);
+    memset(&s_st, 0, sizeof s_st);
+    s_head = 0;
+    s_count = 1;
+    s_t[0] = 0.0;
+  }
+  __syncthreads();
+  if (s_bad) {
+    for (long e = tid; e < pt; e += kBT) a.x_out[e] = a.x0[e];
+    if (tid == 0 && a.stats) {
+      s_st.status = PH_NONFINITE;
+      *a.stats = s_st;
+    }
+    __syncthreads();
+    return;
+  }
+  for (;;) {
+    if (tid == 0) s_tn = ctrl_next_t(&s_ctrl, &a.p);
+    __syncthreads();
+    const double tn = s_tn;
+    if (tn < 0.0) break;
+    // predictor: Lagrange weights of the last m accepted points at tn
+    const int m = s_count < a.p.pred_order + 1 ? s_count : a.p.pred_order + 1;
+    if (tid < m) {
+      const int sj = (s_head - (m - 1 - tid) + kHistB) % kHistB;
+      const double tj = s_t[sj];
+      real num = P::from(1.0), den = P::from(1.0);
+      for (int l = 0; l < m; ++l) {
+        if (l == tid) continue;
+        const double tq = s_t[(s_head - (m - 1 - l) + kHistB) % kHistB];
+        double s1, e1;
+        real u = P::zero(), v = P::zero();
+        two_sum(tn, -tq, s1, e1);
+        P::set_limb(u, 0, s1);
+        P::set_limb(u, 1, e1);
+        two_sum(tj, -tq, s1, e1);
+        P::set_limb(v, 0, s1);
+        P::set_limb(v, 1, e1);
+        num = P::mul(num, u);
+        den = P::mul(den, v);
+      }
+      s_w[tid] = m == 1 ? P::from(1.0) : P::div(num, den);
+    }
+    if (tid == 0) {
+      tl[0] = tn;
+      for (int l = 1; l < P::L; ++l) tl[l] = 0.0;
+      s_last = a.p.max_res;
+      s_dec = 0;
+      s_ok = fixed ? 1 : 0;
+      s_upd = 0;
+      s_iters = 0;
+    }
+    __syncthreads();
+    for (int i = tid; i < n; i += kBT) {
+      cx<P> acc = c_zero<P>();
+      for (int j = 0; j < m; ++j) {
+        const int sj = (s_head - (m - 1 - j) + kHistB) % kHistB;
+        acc = c_add<P>(acc, c_mul_real<P>(c_load<P>(hist + sj * pt, n, i), s_w[j]));
+      }
+      c_store<P>(x, n, i, acc);
+    }
+    // corrector (Fig. "An accelerated Newton's method")
+    for (int it = 0; it < a.p.max_newton; ++it) {
+      __syncthreads();
+      for (int j = tid; j < n; j += kBT)
+        prep_variable<P>(j, x, n, a.emax, ptab, a.deg, total_degree ? spow : nullptr);
+      if (tid == 0) {
+        prep_factors<P>(tl, a.gamma, a.p.relax_k, scal);
+        s_resbits = 0ull;
+      }
+      __syncthreads();
+      for (int s = tid; s < a.Mf; s += kBT)
+        ad_term<P>(s, a.Mpf, a.nvf, a.vidxf, a.vexpf, a.coeff_f, ptab, n, a.maxvf, fslots, a.nsf);
+      for (int s = tid; s < a.Mg; s += kBT)
+        ad_term<P>(s, a.Mpg, a.nvg, a.vidxg, a.vexpg, a.coeff_g, ptab, n, a.maxvg, gslots, a.nsg);
+      __syncthreads();
+      double mymax = 0.0;
+      for (int o0 = 0; o0 < a.nout; o0 += kBT / kSG) {
+        const int o = o0 + tid / kSG, lane = tid % kSG;
+        const bool act = o < a.nout;
+        cx<P> val = sum_output<P, kSG>(act, o, lane, N, n, a.optrf, a.oslotf, fslots, a.nsf,
+                                       a.optrg, a.oslotg, gslots, a.nsg, spow, scal, 1);
+        if (act && lane == 0) {
+          if (o < n * N) {
+            const int j = o / N, i = o - j * N;
+            c_store<P>(A + (long)j * a.ldA, Ap, i, val);
+          } else {
+            const int i = o - n * N;
+            c_store<P>(A + (long)n * a.ldA, Ap, i, c_neg<P>(val));
+            double mg = c_mag_lead<P>(val);
+            if (!(mg <= mymax)) mymax = mg;
+          }
+        }
+      }
+      atomicMax(&s_resbits, (unsigned long long)__double_as_longlong(mymax));
+      __syncthreads();
+      if (tid == 0) {                              // residual test
+        const double r = __longlong_as_double((long long)s_resbits);
+        s_res = r;
+        s_iters += 1;
+        s_st.newton_iters += 1;
+        s_st.res = r;
+        if (!fixed) {
+          if (!(r <= s_last) || !isfinite(r)) { s_dec = 1; s_ok = 0; }
+          else if (r < a.p.tol_res) { s_dec = 1; s_ok = 1; }
+        }
+      }
+      __syncthreads();
+      if (s_dec) break;
+      const int ms = block_mgs<P>(N, n, a.ldA, A, W, dx, s_nrm, s_y, &s_dxmax);
+      if (ms != PH_OK && !fixed) {
+        if (tid == 0) { s_dec = 1; s_ok = 0; }
+        __syncthreads();
+        break;
+      }
+      for (int i = tid; i < n; i += kBT) {
+        cx<P> d = ms != PH_OK ? c_from<P>(NAN, NAN) : c_load<P>(dx, n, i);
+        c_store<P>(x, n, i, c_add<P>(c_load<P>(x, n, i), d));
+      }
+      if (tid == 0) {                              // update test
+        const double d = ms != PH_OK ? NAN : s_dxmax;
+        s_dxn = d;
+        s_st.dx = d;
+        s_upd += 1;
+        s_st.updates += 1;
+        if (!fixed) {
+          if (!isfinite(d)) { s_dec = 1; s_ok = 0; }
+          else if (d < a.p.tol_dx) { s_dec = 1; s_ok = 1; }
+          else s_last = s_res;
+        }
+        if (!s_dec && s_iters >= a.p.max_newton) { s_dec = 1; s_ok = fixed ? 1 : 0; }
+      }
+      __syncthreads();
+      if (s_dec) break;
+    }
+    __syncthreads();
+    // step control (Fig. "Accelerated tracking of one single path")
+    if (tid == 0) {
+      const int ok = s_ok;
+      s_st.steps += 1;
+      if (ok) s_st.accepted += 1; else s_st.rejected += 1;
+      if (a.log && s_st.steps <= a.log_cap) {
+        ph_step_record r;
+        r.t = tn;
+        r.res = s_res;
+        r.dx = s_dxn;
+        r.accepted = ok;
+        r.updates = s_upd;
+        a.log[s_st.steps - 1] = r;
+      }
+      ctrl_report(&s_ctrl, &a.p, tn, ok);
+      if (ok) {
+        s_head = (s_head + 1) % kHistB;
+        s_t[s_head] = tn;
+        s_count = s_count < kHistB ? s_count + 1 : kHistB;
+      }
+      s_xmax = 0.0;
+    }
+    __syncthreads();
+    if (s_ok) {
+      double mymax = 0.0;
+      for (int i = tid; i < n; i += kBT) {
+        cx<P> xi = c_load<P>(x, n, i);
+        c_store<P>(hist + s_head * pt, n, i, xi);
+        double mg = c_mag_lead<P>(xi);
+        if (!(mg <= mymax)) mymax = mg;
+      }
+      atomicMax((unsigned long long *)&s_xmax, (unsigned long long)__double_as_longlong(mymax));
+      __syncthreads();
+      if (tid == 0 && !fixed && !s_ctrl.done && !(s_xmax <= a.p.max_x)) {
+        s_ctrl.done = 1;
+        s_ctrl.status = PH_DIVERGED;
+      }
+    }
+    __syncthreads();
+    if (s_ctrl.done) break;
+  }
+  // end point: the last accepted point
+  for (long e = tid; e < pt; e += kBT) a.x_out[e] = hist[(long)s_head * pt + e];
+  if (tid == 0 && a.stats) {
+    s_st.status = s_ctrl.status;
+    s_st.t_final = s_t[s_head];
+    s_st.launches = 0;
+    *a.stats = s_st;
+  }
+  __syncthreads();
+}
+
+}  // namespace ph

@@ -45,6 +45,11 @@ class StepRecord(C.Structure):
                 ("accepted", C.c_int32), ("updates", C.c_int32)]
 
 
+class ServerConfig(C.Structure):
+    _fields_ = [("max_n", C.c_int32), ("max_blocks", C.c_int32), ("pool_bytes", C.c_int64),
+                ("queue_cap", C.c_int32), ("reserved", C.c_int32)]
+
+
 class CtrlState(C.Structure):
     _fields_ = [("t", C.c_double), ("dt", C.c_double), ("nsucc", C.c_int32),
                 ("nsteps", C.c_int32), ("done", C.c_int32), ("status", C.c_int32)]
@@ -53,7 +58,9 @@ class CtrlState(C.Structure):
 EXPORTS = ["ph_init", "ph_destroy", "ph_last_error", "ph_system_load", "ph_system_free",
            "ph_eval_jac", "ph_mgs_solve", "ph_track_path", "ph_ctrl_init", "ph_ctrl_next_t",
            "ph_ctrl_report", "ph_version", "ph_profile_newton", "ph_fp64_peak",
-           "ph_mgs_solve_static", "ph_track_paths"]
+           "ph_mgs_solve_static", "ph_track_paths", "ph_server_create", "ph_server_submit",
+           "ph_server_poll", "ph_server_wait", "ph_server_info", "ph_server_destroy",
+           "ph_server_job_bytes"]
 
 
 class PhError(RuntimeError):
@@ -94,6 +101,16 @@ def lib():
             L.ph_version.restype = C.c_char_p
             L.ph_profile_newton.argtypes = [vp, vp, vp, vp, C.c_int, vp, vp, C.c_int, dp]
             L.ph_fp64_peak.argtypes = [vp, C.c_double, dp]
+            L.ph_server_create.argtypes = [vp, C.POINTER(ServerConfig), C.POINTER(vp)]
+            L.ph_server_submit.argtypes = [vp, vp, vp, vp, vp, C.POINTER(TrackParams),
+                                           C.POINTER(C.c_int64)]
+            L.ph_server_poll.argtypes = [vp, C.c_int64, C.POINTER(C.c_int), vp,
+                                         C.POINTER(PathStats), dp]
+            L.ph_server_wait.argtypes = [vp, C.c_int64, C.c_int, vp, C.POINTER(PathStats), dp]
+            L.ph_server_info.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                         C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+            L.ph_server_destroy.argtypes = [vp]
+            L.ph_server_job_bytes.argtypes = [vp, vp, vp, C.POINTER(C.c_int64)]
             L.ph_track_paths.argtypes = [vp, vp, vp, vp, C.c_int, vp, C.POINTER(TrackParams), vp,
                                          C.POINTER(PathStats), C.POINTER(StepRecord), C.c_int]
             L.ph_mgs_solve_static.argtypes = [C.c_int, vp, C.c_int, C.c_int, C.c_int, vp, vp, vp,
@@ -226,6 +243,59 @@ def ph_track_paths(ctx, f, g, gamma, x0, params: dict, x_out, log_cap: int = 0):
                           dx=log[i * log_cap + r].dx, accepted=log[i * log_cap + r].accepted,
                           updates=log[i * log_cap + r].updates) for r in range(nrec)])
     return sds, logs
+
+
+def ph_server_create(ctx, max_n: int, pool_bytes: int, queue_cap: int = 1024,
+                     max_blocks: int = 0):
+    cfg = ServerConfig(max_n, max_blocks, pool_bytes, queue_cap, 0)
+    h = C.c_void_p()
+    _check(ctx, lib().ph_server_create(ctx, C.byref(cfg), C.byref(h)))
+    return h
+
+
+def ph_server_submit(ctx, srv, f, g, gamma, x0, params: dict) -> int:
+    jid = C.c_int64(0)
+    p = make_params(params)
+    _check(ctx, lib().ph_server_submit(srv, f, g, _ptr(gamma), _ptr(x0), C.byref(p),
+                                       C.byref(jid)))
+    return jid.value
+
+
+def ph_server_poll(ctx, srv, job_id: int, x_out=None):
+    """(done, stats dict or None, latency_ms or None)."""
+    done = C.c_int(0)
+    st = PathStats()
+    lat = C.c_double(0.0)
+    _check(ctx, lib().ph_server_poll(srv, job_id, C.byref(done), _ptr(x_out), C.byref(st),
+                                     C.byref(lat)))
+    if not done.value:
+        return False, None, None
+    return True, {k: getattr(st, k) for k, _ in PathStats._fields_}, lat.value
+
+
+def ph_server_wait(ctx, srv, job_id: int, timeout_ms: int, x_out=None):
+    st = PathStats()
+    lat = C.c_double(0.0)
+    _check(ctx, lib().ph_server_wait(srv, job_id, timeout_ms, _ptr(x_out), C.byref(st),
+                                     C.byref(lat)))
+    return {k: getattr(st, k) for k, _ in PathStats._fields_}, lat.value
+
+
+def ph_server_info(srv) -> dict:
+    v = [C.c_int64(0) for _ in range(4)]
+    lib().ph_server_info(srv, *[C.byref(x) for x in v])
+    return dict(waiting=v[0].value, on_device=v[1].value, kernel_launches=v[2].value,
+                pool_free_bytes=v[3].value)
+
+
+def ph_server_job_bytes(srv, f, g=None) -> int:
+    b = C.c_int64(0)
+    lib().ph_server_job_bytes(srv, f, g, C.byref(b))
+    return b.value
+
+
+def ph_server_destroy(srv):
+    return lib().ph_server_destroy(srv)
 
 
 def ph_ctrl_init(state: CtrlState, params: dict):
