@@ -13,6 +13,7 @@ Arrays follow the library's layout: complex vectors are float64 [L][2][m]
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 import threading
@@ -20,7 +21,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SOURCES = ["mp.c", "poly.c", "mgs.c", "track.c"]
+_SOURCES = ["mp.c", "poly.c", "mgs.c", "track.c", "mixed.c"]
 _LIB = None
 _LOCK = threading.Lock()
 
@@ -100,6 +101,11 @@ def lib():
                                     C.POINTER(C.c_int)]
             L.orc_replay.argtypes = [C.c_void_p, C.c_void_p, _dp, _dp, C.POINTER(Params),
                                      C.POINTER(Record), C.c_int, _dp]
+            L.orc_lowprec_solve.argtypes = [C.c_int, C.c_int, C.c_int, _dp, _dp, _dp, _dp]
+            L.orc_newton_mixed.argtypes = [C.c_void_p, C.c_void_p, _dp, C.c_int, C.c_double,
+                                           _dp, C.POINTER(Params), C.c_int, C.c_int,
+                                           C.POINTER(C.c_int), C.POINTER(C.c_int), _dp, _dp,
+                                           _dp]
             L.orc_ctrl_init.argtypes = [C.POINTER(Ctrl), C.POINTER(Params)]
             L.orc_ctrl_next_t.argtypes = [C.POINTER(Ctrl), C.POINTER(Params)]
             L.orc_ctrl_next_t.restype = C.c_double
@@ -266,6 +272,45 @@ def newton(f: System, x, t, gamma, params: dict, g: System | None = None, fixed=
                           float(t), _d(x), C.byref(p), int(fixed), C.byref(it), C.byref(up),
                           C.cast(C.pointer(res), _dp), C.cast(C.pointer(dxn), _dp))
     return bool(ok), x, it.value, up.value, res.value, dxn.value
+
+
+LIN = {"f64": 1, "f32": 2}
+
+
+def lowprec_solve(J, rhs, lin: str):
+    """Least squares J dx = rhs in IEEE double ("f64") or single ("f32") by
+    textbook MGS.  J: complex [N][n] (numpy), rhs: complex [N].  Returns
+    (status, dx complex [n], condition estimate)."""
+    J = np.asarray(J, dtype=np.complex128)
+    N, n = J.shape
+    jp = np.ascontiguousarray(np.stack([J.real.T, J.imag.T]))     # [re|im][col][row]
+    rhs = np.asarray(rhs, dtype=np.complex128)
+    rp = np.ascontiguousarray(np.stack([rhs.real, rhs.imag]))
+    dx = np.zeros((2, n))
+    cond = C.c_double(0.0)
+    st = lib().orc_lowprec_solve(LIN[lin], N, n, _d(jp), _d(rp), _d(dx),
+                                 C.cast(C.pointer(cond), _dp))
+    return st, dx[0] + 1j * dx[1], cond.value
+
+
+def newton_mixed(f: System, x, t, gamma, params: dict, lin: str, g: System | None = None,
+                 fixed=False):
+    """One mixed-precision corrector run (residual and update in working
+    precision, the Newton system in `lin`); returns (success, x, iters, updates,
+    res, dx, condition estimate of the last solve)."""
+    L = f.L
+    x = _f64(x).copy()
+    gm = _gamma(gamma, L)
+    p = make_params(params)
+    it, up = C.c_int(0), C.c_int(0)
+    res, dxn, cond = C.c_double(0), C.c_double(0), C.c_double(math.nan)
+    ok = lib().orc_newton_mixed(f.h, g.h if g else None, _d(gm), int(params.get("relax_k", 1)),
+                                float(t), _d(x), C.byref(p), int(fixed), LIN[lin],
+                                C.byref(it), C.byref(up), C.cast(C.pointer(res), _dp),
+                                C.cast(C.pointer(dxn), _dp), C.cast(C.pointer(cond), _dp))
+    if ok < 0:
+        raise ValueError(f"oracle mixed newton failed: {STATUS_NAMES[-ok]}")
+    return bool(ok), x, it.value, up.value, res.value, dxn.value, cond.value
 
 
 def track(f: System, x0, gamma, params: dict, g: System | None = None, log_cap: int = 20000):

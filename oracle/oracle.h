@@ -128,4 +128,16 @@ int orc_replay(const orc_system *f, const orc_system *g, const double *gamma,
                const double *x0, const orc_params *p, const orc_record *log, int nrec,
                double *x_out);
 
+/* ---- mixed-precision corrector (mixed.c) ---------------------------------- */
+/* Least squares in low precision (lin = 1: double, 2: single) by textbook MGS
+   on [J | rhs]; J is [re|im][col][row] and rhs [re|im][N] in double (rounded to
+   float first when lin = 2); dx is [re|im][n]; *cond = max r_kk / min r_kk. */
+int orc_lowprec_solve(int lin, int N, int n, const double *J, const double *rhs, double *dx,
+                      double *cond);
+/* orc_newton with the Newton system solved by orc_lowprec_solve on the rounded
+   J and -h, the update accumulated in working precision */
+int orc_newton_mixed(const orc_system *f, const orc_system *g, const double *gamma, int k,
+                     double t, double *x, const orc_params *p, int fixed, int lin,
+                     int *iters, int *updates, double *res, double *dxn, double *cond);
+
 #endif
