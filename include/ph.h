@@ -123,6 +123,27 @@ typedef struct {
                          the device; 1: the host launches one step at a time and
                          reads the controller state back after each (the paper's
                          host-side step control, Section 3.1)                    */
+  /* The precision form (no counterpart in the paper, whose corrector runs in
+   * DD/QD throughout).  lin_prec selects the precision of the Newton system:
+   *   0  working precision (DD/QD), the paper's corrector;
+   *   1  IEEE double: the residual h(x,t) is evaluated and the update x += dx
+   *      accumulated in working precision, while the Jacobian is evaluated at
+   *      the rounded x and factored (MGS) in double; the residual is scaled by
+   *      a power of two before it is rounded.  Each iteration contracts the
+   *      error by about kappa(J) u_double instead of squaring it;
+   *   2  the same in IEEE single;
+   *   3  single while the previous factorization's condition estimate
+   *      (max r_kk / min r_kk) is at most cond_f32, else double.
+   * In 2 and 3 a single-precision factorization that is not finite is redone
+   * in double.  A step whose low-precision corrector fails is corrected again
+   * from its predicted point in working precision before it counts as a
+   * failure (step size halved), and steps to t >= endgame_t run in working
+   * precision throughout (the end game).
+   * Only ph_track_paths and the serving loop take lin_prec != 0. */
+  int32_t lin_prec;
+  int32_t reserved;   /* 0                                                        */
+  double endgame_t;   /* <= 0: 1.0 (only the step that lands on t = 1)           */
+  double cond_f32;    /* threshold of lin_prec 3; <= 0: 1e3                       */
 } ph_track_params;
 
 /* Outcome of one tracked path. */
@@ -137,6 +158,12 @@ typedef struct {
   double res;           /* last residual norm seen by the corrector              */
   double dx;            /* last update norm seen by the corrector                */
   int64_t launches;     /* kernels the library launched for this path            */
+  int32_t solves_f64;   /* Newton systems solved in double (lin_prec != 0)        */
+  int32_t solves_f32;   /* ... and in single                                       */
+  int32_t escalated;    /* steps whose low-precision corrector failed and that
+                           were corrected again in working precision             */
+  int32_t reserved;
+  double cond;          /* condition estimate of the last low-precision solve    */
 } ph_path_stats;
 
 /* One step of the schedule actually taken, for replay. */

@@ -99,7 +99,7 @@ void ph_job_fill_system(Job &j, const ph_system *f, const ph_system *g) {
   JobLayout o = job_layout(j.L, j.n, j.ldA, j.emax, j.nsf, j.nsg);
   j.o_x = o.o_x; j.o_dx = o.o_dx; j.o_hist = o.o_hist; j.o_ptab = o.o_ptab; j.o_spow = o.o_spow;
   j.o_A = o.o_A; j.o_W = o.o_W; j.o_fslots = o.o_fslots; j.o_gslots = o.o_gslots;
-  j.o_scal = o.o_scal; j.o_t = o.o_t; j.o_g = o.o_g;
+  j.o_scal = o.o_scal; j.o_t = o.o_t; j.o_g = o.o_g; j.o_h = o.o_h;
 }
 
 long ph_job_ws_doubles(const Job &j) {
@@ -118,7 +118,7 @@ extern "C" ph_status ph_track_paths(ph_ctx *ctx, const ph_system *f, const ph_sy
     return ph_fail(ctx, PH_EINVAL, "ph_track_paths: invalid argument");
   const ph_track_params p = *params;
   if (p.max_newton < 1 || p.max_newton > 64 || p.pred_order < 0 || p.pred_order > 8 ||
-      p.relax_k < 1 || p.relax_k > 64 || p.max_steps < 0 ||
+      p.relax_k < 1 || p.relax_k > 64 || p.max_steps < 0 || p.lin_prec < 0 || p.lin_prec > 3 ||
       (p.fixed_steps <= 0 && !(p.max_dt > 0.0 && p.min_dt > 0.0 && p.min_dt <= p.max_dt)))
     return ph_fail(ctx, PH_EINVAL, "ph_track_paths: invalid parameters");
   if (!g) {

@@ -265,6 +265,52 @@ struct QD {
 };
 
 // ---------------------------------------------------------------- complex
+// ---------------------------------------------------------------- one-limb types
+// IEEE double and single precision, with the same interface as DD and QD, for
+// the Jacobian and its factorization in the mixed-precision corrector.  Arrays
+// stay in double (a single-precision value is stored widened), so every
+// layout above serves all four types: an array of L limbs read as F64 or F32
+// gives its leading limb.
+struct F64 {
+  static constexpr int L = 1;
+  typedef double real;
+  PHD static real zero() { return 0.0; }
+  PHD static real from(double a) { return a; }
+  PHD static double lead(const real &a) { return a; }
+  PHD static double limb(const real &a, int) { return a; }
+  PHD static void set_limb(real &a, int, double v) { a = v; }
+  PHD static real neg(real a) { return -a; }
+  PHD static real add(real a, real b) { return fadd(a, b); }
+  PHD static real sub(real a, real b) { return fsub(a, b); }
+  PHD static real mul(real a, real b) { return fmul(a, b); }
+  PHD static real mul_d(real a, double b) { return fmul(a, b); }
+  PHD static real scale2(real a) { return fmul(a, 2.0); }
+  PHD static real div(real a, real b) { return __ddiv_rn(a, b); }
+  PHD static real recip(real b) { return __drcp_rn(b); }
+  PHD static real sqrt(real a) { return __dsqrt_rn(a); }
+  PHD static real fma(real a, real b, real c) { return ffma(a, b, c); }
+};
+
+struct F32 {
+  static constexpr int L = 1;
+  typedef float real;
+  PHD static real zero() { return 0.0f; }
+  PHD static real from(double a) { return __double2float_rn(a); }
+  PHD static double lead(const real &a) { return (double)a; }
+  PHD static double limb(const real &a, int) { return (double)a; }
+  PHD static void set_limb(real &a, int, double v) { a = __double2float_rn(v); }
+  PHD static real neg(real a) { return -a; }
+  PHD static real add(real a, real b) { return __fadd_rn(a, b); }
+  PHD static real sub(real a, real b) { return __fsub_rn(a, b); }
+  PHD static real mul(real a, real b) { return __fmul_rn(a, b); }
+  PHD static real mul_d(real a, double b) { return __fmul_rn(a, __double2float_rn(b)); }
+  PHD static real scale2(real a) { return __fmul_rn(a, 2.0f); }
+  PHD static real div(real a, real b) { return __fdiv_rn(a, b); }
+  PHD static real recip(real b) { return __frcp_rn(b); }
+  PHD static real sqrt(real a) { return __fsqrt_rn(a); }
+  PHD static real fma(real a, real b, real c) { return __fmaf_rn(a, b, c); }
+};
+
 template <class P> struct cx { typename P::real re, im; };
 
 template <class P> PHD cx<P> c_zero() { return {P::zero(), P::zero()}; }
@@ -336,6 +382,24 @@ template <> struct cops<DD> {
     return z;
   }
 };
+
+// one-limb types: each part of a product is one multiply and one FMA
+template <class P> struct cops1 {
+  typedef typename P::real real;
+  PHD static cx<P> mul(const cx<P> &a, const cx<P> &b) {
+    return {P::fma(a.re, b.re, P::neg(P::mul(a.im, b.im))), P::fma(a.re, b.im, P::mul(a.im, b.re))};
+  }
+  PHD static cx<P> mac(const cx<P> &acc, const cx<P> &a, const cx<P> &b) {
+    return {P::fma(a.re, b.re, P::fma(P::neg(a.im), b.im, acc.re)),
+            P::fma(a.re, b.im, P::fma(a.im, b.re, acc.im))};
+  }
+  PHD static cx<P> conj_mul(const cx<P> &a, const cx<P> &b) {
+    return {P::fma(a.re, b.re, P::mul(a.im, b.im)), P::fma(a.re, b.im, P::neg(P::mul(a.im, b.re)))};
+  }
+  PHD static real abs2(const cx<P> &a) { return P::fma(a.re, a.re, P::mul(a.im, a.im)); }
+};
+template <> struct cops<F64> : cops1<F64> {};
+template <> struct cops<F32> : cops1<F32> {};
 
 template <class P> PHD cx<P> c_mul(const cx<P> &a, const cx<P> &b) { return cops<P>::mul(a, b); }
 template <class P> PHD cx<P> c_conj_mul(const cx<P> &a, const cx<P> &b) { return cops<P>::conj_mul(a, b); }

@@ -36,13 +36,13 @@ struct Job {
   ph_step_record *log;            // log_cap records (may be null)
   int log_cap;
   double *ws;                     // this job's workspace
-  long o_x, o_dx, o_hist, o_ptab, o_spow, o_A, o_W, o_fslots, o_gslots, o_scal, o_t, o_g;
+  long o_x, o_dx, o_hist, o_ptab, o_spow, o_A, o_W, o_fslots, o_gslots, o_scal, o_t, o_g, o_h;
   long ldA, nsf, nsg;
 };
 
 // Workspace layout (doubles, 256-byte aligned regions) of a job.
 struct JobLayout {
-  long o_x, o_dx, o_hist, o_ptab, o_spow, o_A, o_W, o_fslots, o_gslots, o_scal, o_t, o_g, stride;
+  long o_x, o_dx, o_hist, o_ptab, o_spow, o_A, o_W, o_fslots, o_gslots, o_scal, o_t, o_g, o_h, stride;
 };
 
 inline JobLayout job_layout(int L, int n, long ldA, int emax, long nsf, long nsg) {
@@ -61,7 +61,8 @@ inline JobLayout job_layout(int L, int n, long ldA, int emax, long nsf, long nsg
   o.o_scal = o.o_gslots + up(2L * L * nsg);
   o.o_t = o.o_scal + up(3L * L);
   o.o_g = o.o_t + up(L);
-  o.stride = o.o_g + up(2L * L);
+  o.o_h = o.o_g + up(2L * L);
+  o.stride = o.o_h + up(2 * ldA);
   return o;
 }
 
@@ -185,6 +186,60 @@ __device__ int block_mgs(int N, int n, long ldA, double *A, double *W, double *d
   return PH_OK;
 }
 
+// The Newton system of the mixed-precision corrector, solved in precision LP
+// (F64 or F32) by the calling block: the Jacobian at x rounded to LP (power
+// table, reverse-mode terms and summation in LP, written to the workspace's
+// regions in the one-limb layout), the right-hand side -h (hl: its leading
+// limbs, [re|im][ldA]) scaled by 2^-e and rounded to LP, then MGS and back
+// substitution in LP.  On return dx holds d ([re|im][n], widened to double)
+// with J d = -2^-e h, *s_dxmax = max |d_i| and *s_kappa = max r_kk / min r_kk
+// (infinite if the factorization failed).  Returns PH_OK or PH_NONFINITE.
+template <class P, class LP>
+__device__ int lowprec_solve(const Job &a, const double *x, const double *tl, const double *hl,
+                             int e, double *ptab, double *spow, double *scal, double *fslots,
+                             double *gslots, double *A, double *W, double *dx, double *s_nrm,
+                             double *s_y, double *s_dxmax, double *s_kappa) {
+  const int n = a.n, N = a.N, tid = threadIdx.x, nN = n * N;
+  const bool total_degree = a.optrg == nullptr;
+  const long Ap = (long)(n + 1) * a.ldA;
+  __syncthreads();                                 // the working-precision tables are done
+  for (int j = tid; j < n; j += kBT)
+    prep_variable<LP>(j, x, n, a.emax, ptab, a.deg, total_degree ? spow : nullptr);
+  if (tid == 0) prep_factors<LP>(tl, a.gamma, a.p.relax_k, scal);
+  for (int i = tid; i < N; i += kBT)
+    c_store<LP>(A + (long)n * a.ldA, Ap, i,
+                c_from<LP>(ldexp(hl[i], -e), ldexp(hl[a.ldA + i], -e)));
+  __syncthreads();
+  for (int s = tid; s < a.Mf; s += kBT)
+    ad_term<LP>(s, a.Mpf, a.nvf, a.vidxf, a.vexpf, a.coeff_f, ptab, n, a.maxvf, fslots, a.nsf);
+  for (int s = tid; s < a.Mg; s += kBT)
+    ad_term<LP>(s, a.Mpg, a.nvg, a.vidxg, a.vexpg, a.coeff_g, ptab, n, a.maxvg, gslots, a.nsg);
+  __syncthreads();
+  for (int o0 = 0; o0 < nN; o0 += kBT / kSG) {
+    const int o = o0 + tid / kSG, lane = tid % kSG;
+    const bool act = o < nN;
+    cx<LP> val = sum_output<LP, kSG>(act, o, lane, N, n, a.optrf, a.oslotf, fslots, a.nsf,
+                                     a.optrg, a.oslotg, gslots, a.nsg, spow, scal, 1);
+    if (act && lane == 0) {
+      const int j = o / N, i = o - j * N;
+      c_store<LP>(A + (long)j * a.ldA, Ap, i, val);
+    }
+  }
+  __syncthreads();
+  const int ms = block_mgs<LP>(N, n, a.ldA, A, W, dx, s_nrm, s_y, s_dxmax);
+  if (tid == 0) {
+    double mx = 0.0, mn = INFINITY;
+    for (int k = 0; k < n; ++k) {
+      const double v = LP::lead(r_load<LP>(s_nrm, n + 1, k));
+      mx = fmax(mx, v);
+      mn = fmin(mn, v);
+    }
+    *s_kappa = ms == PH_OK ? sqrt(mx / mn) : INFINITY;
+  }
+  __syncthreads();
+  return ms;
+}
+
 // Tracks the job's path from its start point to its end with the calling
 // block (kBT threads); writes the end point (the last accepted point), the
 // statistics and the step log.  smem: dynamic shared memory for n variables.
@@ -200,6 +255,8 @@ __device__ void track_job(const Job &a, double *smem) {
   __shared__ double s_tn, s_last, s_res, s_dxn, s_dxmax, s_xmax;
   __shared__ unsigned long long s_resbits;
   __shared__ ph_path_stats s_st;
+  __shared__ int s_lin, s_scale_e, s_force_wp, s_lp_used;
+  __shared__ double s_cond, s_kappa;
 
   const int n = a.n, N = a.N, tid = threadIdx.x;
   const long pt = 2L * P::L * n;
@@ -210,6 +267,9 @@ __device__ void track_job(const Job &a, double *smem) {
   const bool fixed = a.p.fixed_steps > 0;
   const long Ap = (long)(n + 1) * a.ldA;
   const bool total_degree = a.optrg == nullptr;
+  double *hl = ws + a.o_h;                              // leading limbs of -h: [re|im][ldA]
+  const double endgame = a.p.endgame_t > 0.0 ? a.p.endgame_t : 1.0;
+  const double cond32 = a.p.cond_f32 > 0.0 ? a.p.cond_f32 : 1e3;
 
   // start: the start point is the only accepted point
   if (tid == 0) s_bad = 0;
@@ -222,6 +282,7 @@ __device__ void track_job(const Job &a, double *smem) {
   if (tid == 0) {
     ctrl_init(&s_ctrl, &a.p);
     memset(&s_st, 0, sizeof s_st);
+    s_cond = INFINITY;
     s_head = 0;
     s_count = 1;
     s_t[0] = 0.0;
@@ -266,96 +327,174 @@ __device__ void track_job(const Job &a, double *smem) {
     if (tid == 0) {
       tl[0] = tn;
       for (int l = 1; l < P::L; ++l) tl[l] = 0.0;
-      s_last = a.p.max_res;
-      s_dec = 0;
-      s_ok = fixed ? 1 : 0;
-      s_upd = 0;
-      s_iters = 0;
+      s_force_wp = 0;
     }
-    __syncthreads();
-    for (int i = tid; i < n; i += kBT) {
-      cx<P> acc = c_zero<P>();
-      for (int j = 0; j < m; ++j) {
-        const int sj = (s_head - (m - 1 - j) + kHistB) % kHistB;
-        acc = c_add<P>(acc, c_mul_real<P>(c_load<P>(hist + sj * pt, n, i), s_w[j]));
-      }
-      c_store<P>(x, n, i, acc);
-    }
-    // corrector (Fig. "An accelerated Newton's method")
-    for (int it = 0; it < a.p.max_newton; ++it) {
-      __syncthreads();
-      for (int j = tid; j < n; j += kBT)
-        prep_variable<P>(j, x, n, a.emax, ptab, a.deg, total_degree ? spow : nullptr);
+    // A step whose mixed-precision corrector fails is corrected again from the
+    // predicted point in working precision (pass 1) before it counts as failed.
+    for (int pass = 0;; ++pass) {
       if (tid == 0) {
-        prep_factors<P>(tl, a.gamma, a.p.relax_k, scal);
-        s_resbits = 0ull;
+        s_last = a.p.max_res;
+        s_dec = 0;
+        s_ok = fixed ? 1 : 0;
+        s_upd = 0;
+        s_iters = 0;
+        s_lp_used = 0;
       }
       __syncthreads();
-      for (int s = tid; s < a.Mf; s += kBT)
-        ad_term<P>(s, a.Mpf, a.nvf, a.vidxf, a.vexpf, a.coeff_f, ptab, n, a.maxvf, fslots, a.nsf);
-      for (int s = tid; s < a.Mg; s += kBT)
-        ad_term<P>(s, a.Mpg, a.nvg, a.vidxg, a.vexpg, a.coeff_g, ptab, n, a.maxvg, gslots, a.nsg);
-      __syncthreads();
-      double mymax = 0.0;
-      for (int o0 = 0; o0 < a.nout; o0 += kBT / kSG) {
-        const int o = o0 + tid / kSG, lane = tid % kSG;
-        const bool act = o < a.nout;
-        cx<P> val = sum_output<P, kSG>(act, o, lane, N, n, a.optrf, a.oslotf, fslots, a.nsf,
-                                       a.optrg, a.oslotg, gslots, a.nsg, spow, scal, 1);
-        if (act && lane == 0) {
-          if (o < n * N) {
-            const int j = o / N, i = o - j * N;
-            c_store<P>(A + (long)j * a.ldA, Ap, i, val);
-          } else {
-            const int i = o - n * N;
-            c_store<P>(A + (long)n * a.ldA, Ap, i, c_neg<P>(val));
-            double mg = c_mag_lead<P>(val);
-            if (!(mg <= mymax)) mymax = mg;
+      for (int i = tid; i < n; i += kBT) {
+        cx<P> acc = c_zero<P>();
+        for (int j = 0; j < m; ++j) {
+          const int sj = (s_head - (m - 1 - j) + kHistB) % kHistB;
+          acc = c_add<P>(acc, c_mul_real<P>(c_load<P>(hist + sj * pt, n, i), s_w[j]));
+        }
+        c_store<P>(x, n, i, acc);
+      }
+      // corrector (Fig. "An accelerated Newton's method")
+      for (int it = 0; it < a.p.max_newton; ++it) {
+        __syncthreads();
+        if (tid == 0) {                              // the precision of this iteration's solve
+          int lin = a.p.lin_prec;
+          if (tn >= endgame || s_force_wp) lin = 0;
+          if (lin == 3) lin = s_cond <= cond32 ? 2 : 1;
+          s_lin = lin;
+          s_resbits = 0ull;
+        }
+        for (int j = tid; j < n; j += kBT)
+          prep_variable<P>(j, x, n, a.emax, ptab, a.deg, total_degree ? spow : nullptr);
+        if (tid == 0) prep_factors<P>(tl, a.gamma, a.p.relax_k, scal);
+        __syncthreads();
+        const int lin = s_lin;
+        double mymax = 0.0;
+        if (lin == 0) {
+          // h and J in working precision into A = [J | -h]
+          for (int s = tid; s < a.Mf; s += kBT)
+            ad_term<P>(s, a.Mpf, a.nvf, a.vidxf, a.vexpf, a.coeff_f, ptab, n, a.maxvf, fslots, a.nsf);
+          for (int s = tid; s < a.Mg; s += kBT)
+            ad_term<P>(s, a.Mpg, a.nvg, a.vidxg, a.vexpg, a.coeff_g, ptab, n, a.maxvg, gslots, a.nsg);
+          __syncthreads();
+          for (int o0 = 0; o0 < a.nout; o0 += kBT / kSG) {
+            const int o = o0 + tid / kSG, lane = tid % kSG;
+            const bool act = o < a.nout;
+            cx<P> val = sum_output<P, kSG>(act, o, lane, N, n, a.optrf, a.oslotf, fslots, a.nsf,
+                                           a.optrg, a.oslotg, gslots, a.nsg, spow, scal, 1);
+            if (act && lane == 0) {
+              if (o < n * N) {
+                const int j = o / N, i = o - j * N;
+                c_store<P>(A + (long)j * a.ldA, Ap, i, val);
+              } else {
+                const int i = o - n * N;
+                c_store<P>(A + (long)n * a.ldA, Ap, i, c_neg<P>(val));
+                double mg = c_mag_lead<P>(val);
+                if (!(mg <= mymax)) mymax = mg;
+              }
+            }
+          }
+        } else {
+          // the residual alone in working precision; the leading limbs of -h to hl
+          for (int s = tid; s < a.Mf; s += kBT)
+            val_term<P>(s, a.Mpf, a.nvf, a.vidxf, a.vexpf, a.coeff_f, ptab, n, a.emax, a.maxvf,
+                        fslots, a.nsf);
+          for (int s = tid; s < a.Mg; s += kBT)
+            val_term<P>(s, a.Mpg, a.nvg, a.vidxg, a.vexpg, a.coeff_g, ptab, n, a.emax, a.maxvg,
+                        gslots, a.nsg);
+          __syncthreads();
+          for (int o0 = 0; o0 < N; o0 += kBT / kSG) {
+            const int i = o0 + tid / kSG, lane = tid % kSG;
+            const bool act = i < N;
+            cx<P> val = sum_output<P, kSG>(act, n * N + i, lane, N, n, a.optrf, a.oslotf, fslots,
+                                           a.nsf, a.optrg, a.oslotg, gslots, a.nsg, spow, scal, 1);
+            if (act && lane == 0) {
+              hl[i] = -P::lead(val.re);
+              hl[a.ldA + i] = -P::lead(val.im);
+              double mg = c_mag_lead<P>(val);
+              if (!(mg <= mymax)) mymax = mg;
+            }
           }
         }
-      }
-      atomicMax(&s_resbits, (unsigned long long)__double_as_longlong(mymax));
-      __syncthreads();
-      if (tid == 0) {                              // residual test
-        const double r = __longlong_as_double((long long)s_resbits);
-        s_res = r;
-        s_iters += 1;
-        s_st.newton_iters += 1;
-        s_st.res = r;
-        if (!fixed) {
-          if (!(r <= s_last) || !isfinite(r)) { s_dec = 1; s_ok = 0; }
-          else if (r < a.p.tol_res) { s_dec = 1; s_ok = 1; }
-        }
-      }
-      __syncthreads();
-      if (s_dec) break;
-      const int ms = block_mgs<P>(N, n, a.ldA, A, W, dx, s_nrm, s_y, &s_dxmax);
-      if (ms != PH_OK && !fixed) {
-        if (tid == 0) { s_dec = 1; s_ok = 0; }
+        atomicMax(&s_resbits, (unsigned long long)__double_as_longlong(mymax));
         __syncthreads();
-        break;
-      }
-      for (int i = tid; i < n; i += kBT) {
-        cx<P> d = ms != PH_OK ? c_from<P>(NAN, NAN) : c_load<P>(dx, n, i);
-        c_store<P>(x, n, i, c_add<P>(c_load<P>(x, n, i), d));
-      }
-      if (tid == 0) {                              // update test
-        const double d = ms != PH_OK ? NAN : s_dxmax;
-        s_dxn = d;
-        s_st.dx = d;
-        s_upd += 1;
-        s_st.updates += 1;
-        if (!fixed) {
-          if (!isfinite(d)) { s_dec = 1; s_ok = 0; }
-          else if (d < a.p.tol_dx) { s_dec = 1; s_ok = 1; }
-          else s_last = s_res;
+        if (tid == 0) {                              // residual test
+          const double r = __longlong_as_double((long long)s_resbits);
+          s_res = r;
+          s_iters += 1;
+          s_st.newton_iters += 1;
+          s_st.res = r;
+          if (!fixed) {
+            if (!(r <= s_last) || !isfinite(r)) { s_dec = 1; s_ok = 0; }
+            else if (r < a.p.tol_res) { s_dec = 1; s_ok = 1; }
+          }
+          s_scale_e = (r > 0.0 && isfinite(r)) ? ilogb(r) : 0;
         }
-        if (!s_dec && s_iters >= a.p.max_newton) { s_dec = 1; s_ok = fixed ? 1 : 0; }
+        __syncthreads();
+        if (s_dec) break;
+        int ms;
+        if (lin == 0) {
+          ms = block_mgs<P>(N, n, a.ldA, A, W, dx, s_nrm, s_y, &s_dxmax);
+        } else {
+          ms = lin == 2 ? lowprec_solve<P, F32>(a, x, tl, hl, s_scale_e, ptab, spow, scal, fslots,
+                                                gslots, A, W, dx, s_nrm, s_y, &s_dxmax, &s_kappa)
+                        : PH_NONFINITE;
+          if (lin == 2 && tid == 0) {
+            if (ms == PH_OK) s_st.solves_f32 += 1;
+            s_cond = ms == PH_OK ? s_kappa : INFINITY;
+          }
+          if (lin == 1 || ms != PH_OK) {             // double (also the retry of a failed single)
+            ms = lowprec_solve<P, F64>(a, x, tl, hl, s_scale_e, ptab, spow, scal, fslots, gslots, A,
+                                       W, dx, s_nrm, s_y, &s_dxmax, &s_kappa);
+            if (tid == 0) {
+              s_st.solves_f64 += 1;
+              s_cond = ms == PH_OK ? s_kappa : INFINITY;
+            }
+          }
+          if (tid == 0) {
+            s_st.cond = s_cond;
+            s_lp_used = 1;
+          }
+        }
+        if (ms != PH_OK && !fixed) {
+          if (tid == 0) { s_dec = 1; s_ok = 0; }
+          __syncthreads();
+          break;
+        }
+        const int e = s_scale_e;
+        for (int i = tid; i < n; i += kBT) {
+          cx<P> d;
+          if (ms != PH_OK) {
+            d = c_from<P>(NAN, NAN);
+          } else if (lin == 0) {
+            d = c_load<P>(dx, n, i);
+          } else {
+            d = c_from<P>(ldexp(dx[i], e), ldexp(dx[n + i], e));
+          }
+          c_store<P>(x, n, i, c_add<P>(c_load<P>(x, n, i), d));
+        }
+        if (tid == 0) {                              // update test
+          const double d = ms != PH_OK ? NAN : (lin == 0 ? s_dxmax : ldexp(s_dxmax, e));
+          s_dxn = d;
+          s_st.dx = d;
+          s_upd += 1;
+          s_st.updates += 1;
+          if (!fixed) {
+            if (!isfinite(d)) { s_dec = 1; s_ok = 0; }
+            else if (d < a.p.tol_dx) { s_dec = 1; s_ok = 1; }
+            else s_last = s_res;
+          }
+          if (!s_dec && s_iters >= a.p.max_newton) { s_dec = 1; s_ok = fixed ? 1 : 0; }
+        }
+        __syncthreads();
+        if (s_dec) break;
       }
       __syncthreads();
-      if (s_dec) break;
+      if (pass == 0 && !s_ok && s_lp_used && !fixed) {
+        if (tid == 0) {
+          s_force_wp = 1;
+          s_st.escalated += 1;
+        }
+        __syncthreads();
+        continue;
+      }
+      break;
     }
-    __syncthreads();
     // step control (Fig. "Accelerated tracking of one single path")
     if (tid == 0) {
       const int ok = s_ok;

@@ -86,6 +86,31 @@ __device__ void ad_term(int s, int Mp, const int32_t *__restrict__ nv,
   }
 }
 
+// Value alone of sorted term s (c x^a) by one thread, into its value slot
+// maxv*Mp+s: each variable's power from the power table, which holds x^1 ..
+// x^{emax-1} (x^a, or x^{a-1} x when a = emax >= 2).  The residual of
+// the mixed-precision corrector needs h(x,t) only; this is v complex products
+// per term where the reverse mode takes about 3v.
+template <class P>
+__device__ void val_term(int s, int Mp, const int32_t *__restrict__ nv,
+                         const int32_t *__restrict__ vidx, const int32_t *__restrict__ vexp,
+                         const double *__restrict__ coeff, const double *__restrict__ ptab, int n,
+                         int emax, int maxv, double *__restrict__ slots, long nslots) {
+  const long pl = 2L * P::L * n;
+  const int v = nv[s];
+  cx<P> c = c_load<P>(coeff, Mp, s);
+  for (int p = 0; p < v; ++p) {
+    const int a = vexp[(long)p * Mp + s], j = vidx[(long)p * Mp + s];
+    if (a == 1 || a < emax) {
+      c = c_mul<P>(c, c_load<P>(ptab + (a - 1) * pl, n, j));
+    } else {
+      c = c_mul<P>(c, c_load<P>(ptab + (a - 2) * pl, n, j));
+      c = c_mul<P>(c, c_load<P>(ptab, n, j));
+    }
+  }
+  c_store<P>(slots, nslots, (long)maxv * Mp + s, c);
+}
+
 template <class P>
 PHD cx<P> shfl_down_c(const cx<P> &a, int off, int width) {
   cx<P> z;
@@ -171,6 +196,27 @@ template <class P> struct Part {
     return P::add(a, P::sub(t, P::mul(ar, b)));
   }
 };
+
+// one-limb types: fused multiply-adds
+template <class P> struct Part1 {
+  typedef typename P::real real;
+  struct acc { real v; };
+  PHD static acc zero() { return {P::zero()}; }
+  PHD static void dot2(acc &a, const real &x1, const real &y1, const real &x2, const real &y2,
+                       double sg) {
+    a.v = P::fma(x1, y1, P::fma(sg < 0 ? P::neg(x2) : x2, y2, a.v));
+  }
+  PHD static void sq(acc &a, const real &x) { a.v = P::fma(x, x, a.v); }
+  PHD static acc combine(const acc &a, const acc &b) { return {P::add(a.v, b.v)}; }
+  PHD static acc shfl(const acc &a, int m) { return {__shfl_xor_sync(0xffffffffu, a.v, m)}; }
+  PHD static real value(const acc &a) { return a.v; }
+  PHD static real upd(const real &a, const real &ar, const real &b, const real &ai,
+                      const real &c, double sg) {
+    return P::fma(P::neg(ar), b, P::fma(sg < 0 ? P::neg(ai) : ai, c, a));
+  }
+};
+template <> struct Part<F64> : Part1<F64> {};
+template <> struct Part<F32> : Part1<F32> {};
 
 // double-double: Dot2-style unnormalised (s, c) accumulation
 template <> struct Part<DD> {

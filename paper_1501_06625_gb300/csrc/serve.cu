@@ -413,7 +413,7 @@ extern "C" ph_status ph_server_submit(ph_server *s, const ph_system *f, const ph
   if (f->n > s->cfg.max_n) return ph_fail(ctx, PH_EINVAL, "ph_server_submit: more variables than max_n");
   const ph_track_params &p = *params;
   if (p.max_newton < 1 || p.max_newton > 64 || p.pred_order < 0 || p.pred_order > 8 ||
-      p.relax_k < 1 || p.relax_k > 64 || p.max_steps < 0 ||
+      p.relax_k < 1 || p.relax_k > 64 || p.max_steps < 0 || p.lin_prec < 0 || p.lin_prec > 3 ||
       (p.fixed_steps <= 0 && !(p.max_dt > 0.0 && p.min_dt > 0.0 && p.min_dt <= p.max_dt)))
     return ph_fail(ctx, PH_EINVAL, "ph_server_submit: invalid parameters");
   if (!g) {

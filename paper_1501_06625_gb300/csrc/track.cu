@@ -391,6 +391,8 @@ extern "C" ph_status ph_track_path(ph_ctx *ctx, const ph_system *f, const ph_sys
       p.relax_k < 1 || p.relax_k > 64 || p.control < 0 || p.control > 1 || p.max_steps < 0 ||
       (p.fixed_steps <= 0 && !(p.max_dt > 0.0 && p.min_dt > 0.0 && p.min_dt <= p.max_dt)))
     return ph_fail(ctx, PH_EINVAL, "ph_track_path: invalid parameters");
+  if (p.lin_prec != 0)
+    return ph_fail(ctx, PH_EINVAL, "ph_track_path: lin_prec != 0 is taken by ph_track_paths and the serving loop");
   if (!g) {
     if (f->N != f->n) return ph_fail(ctx, PH_EINVAL, "ph_track_path: the total-degree start system needs N == n");
     for (int d : f->h_deg)

@@ -30,14 +30,17 @@ class TrackParams(C.Structure):
     _fields_ = [("max_dt", C.c_double), ("min_dt", C.c_double), ("tol_res", C.c_double),
                 ("tol_dx", C.c_double), ("max_res", C.c_double), ("max_x", C.c_double),
                 ("max_steps", C.c_int32), ("max_newton", C.c_int32), ("pred_order", C.c_int32),
-                ("relax_k", C.c_int32), ("fixed_steps", C.c_int32), ("control", C.c_int32)]
+                ("relax_k", C.c_int32), ("fixed_steps", C.c_int32), ("control", C.c_int32),
+                ("lin_prec", C.c_int32), ("reserved", C.c_int32), ("endgame_t", C.c_double),
+                ("cond_f32", C.c_double)]
 
 
 class PathStats(C.Structure):
     _fields_ = [("status", C.c_int32), ("steps", C.c_int32), ("accepted", C.c_int32),
                 ("rejected", C.c_int32), ("newton_iters", C.c_int32), ("updates", C.c_int32),
                 ("t_final", C.c_double), ("res", C.c_double), ("dx", C.c_double),
-                ("launches", C.c_int64)]
+                ("launches", C.c_int64), ("solves_f64", C.c_int32), ("solves_f32", C.c_int32),
+                ("escalated", C.c_int32), ("reserved", C.c_int32), ("cond", C.c_double)]
 
 
 class StepRecord(C.Structure):

@@ -91,7 +91,9 @@ class SystemSpec:
     Polynomial i owns terms term_ptr[i]..term_ptr[i+1]-1; term k owns the
     (variable, exponent) pairs var_ptr[k]..var_ptr[k+1]-1 (exponent >= 1, the
     variables of a term distinct); a term with no pair is a constant.
-    coeff[k] is the complex coefficient of term k, a double.
+    coeff[k] is the complex coefficient of term k, a double; coeff_lo, when
+    given, holds a second limb (a coefficient is then coeff + coeff_lo
+    exactly, which a planted constant term needs).
     """
 
     N: int
@@ -101,6 +103,7 @@ class SystemSpec:
     var_idx: np.ndarray
     var_exp: np.ndarray
     coeff: np.ndarray
+    coeff_lo: np.ndarray | None = None
 
     @property
     def M(self) -> int:
@@ -111,6 +114,12 @@ class SystemSpec:
         out = np.zeros((L, 2, self.M))
         out[0, 0] = self.coeff.real
         out[0, 1] = self.coeff.imag
+        if self.coeff_lo is not None:
+            if L < 2 and np.any(self.coeff_lo != 0):
+                raise ValueError("coefficients need two limbs")
+            if L >= 2:
+                out[1, 0] = self.coeff_lo.real
+                out[1, 1] = self.coeff_lo.imag
         return out
 
     def degrees(self) -> np.ndarray:
@@ -175,6 +184,54 @@ def sparse_system(rng: Rng, n: int, extra_terms: int = 3, vars_per_term: int = 2
     return build_system(n, n, polys)
 
 
+def planted_system(rng: Rng, n: int, terms_per_poly: int, vars_per_term: int,
+                   exps: tuple[int, ...], log10_mag: float) -> tuple[SystemSpec, np.ndarray]:
+    """A dense system (the recipe of dense_system) whose coefficient moduli
+    spread log-uniformly over log10_mag decades within each polynomial, with a
+    planted root x*.  Each polynomial is scaled so that its largest modulus is
+    1: the moduli are 10^{log10_mag (u - u_max)}, u uniform.  (Unscaled moduli up
+    to 10^log10_mag against the unit-size start system would put a boundary
+    layer of width ~10^-log10_mag at t = 0 that no step size crosses; scaling
+    an equation changes neither its roots nor the spread within it.)  Each
+    coordinate of x* is drawn from {1, i, -1, -i}, so every term's value
+    c (x*)^a is c with its parts swapped or negated, exactly; each polynomial
+    gets the constant term b_i = -sum_k c_ik (x*)^{a_ik}, summed exactly in
+    rationals and stored as two limbs, so f(x*) = 0 holds exactly.
+    Returns (system, x*)."""
+    from fractions import Fraction
+    units = (1 + 0j, 1j, -1 + 0j, -1j)
+    xs = np.array([rng.choice(units) for _ in range(n)])
+    polys, lo = [], []
+    for _ in range(n):
+        drawn = []
+        for _ in range(terms_per_poly):
+            vs = rng.sample(n, vars_per_term)
+            mono = [(v, rng.choice(exps)) for v in vs]
+            drawn.append((mono, rng.unit_complex(), rng.uniform()))
+        umax = max(u for _, _, u in drawn)
+        terms = []
+        bre, bim = Fraction(0), Fraction(0)
+        for mono, e, u in drawn:
+            c = e * 10.0 ** (log10_mag * (u - umax))
+            w = c
+            for v, k in mono:
+                w = w * xs[v] ** k                 # exact: a swap or negation of parts
+            bre -= Fraction(w.real)
+            bim -= Fraction(w.imag)
+            terms.append((c, mono))
+            lo.append(0j)
+        hre, him = float(bre), float(bim)
+        lre, lim = float(bre - Fraction(hre)), float(bim - Fraction(him))
+        if Fraction(hre) + Fraction(lre) != bre or Fraction(him) + Fraction(lim) != bim:
+            raise ValueError("the constant term does not fit in two limbs")
+        terms.append((complex(hre, him), []))
+        lo.append(complex(lre, lim))
+        polys.append(terms)
+    spec = build_system(n, n, polys)
+    spec.coeff_lo = np.asarray(lo, dtype=np.complex128)
+    return spec, xs
+
+
 def cyclic_system(n: int) -> SystemSpec:
     """Cyclic n-roots (Section 4.2, Eq. (8)): f_i = sum_j prod_{k=j}^{j+i-1}
     x_{k mod n} for i = 1..n-1, and f_n = x_0 x_1 ... x_{n-1} - 1."""
@@ -198,7 +255,8 @@ def default_params(L: int, **over) -> dict:
     p = dict(max_dt=0.1, min_dt=1e-12 if L == 2 else 1e-20,
              tol_res=1e-24 if L == 2 else 1e-52, tol_dx=1e-24 if L == 2 else 1e-52,
              max_res=1e8, max_x=1e8, max_steps=10000, max_newton=3 if L == 2 else 4,
-             pred_order=4, relax_k=1, fixed_steps=0, control=0)
+             pred_order=4, relax_k=1, fixed_steps=0, control=0, lin_prec=0, endgame_t=0.0,
+             cond_f32=0.0)
     p.update(over)
     return p
 
@@ -272,6 +330,21 @@ def sparse512(seed: int = 1, prec="qd") -> Workload:
     gamma = rng.unit_complex()
     return Workload(f"sparse512_{'dd' if L == 2 else 'qd'}", seed, L, f, gamma,
                     np.ones(512, dtype=np.complex128), default_params(L))
+
+
+def precision128(seed: int = 1, prec="qd") -> tuple[Workload, np.ndarray]:
+    """n=128; 128 terms per polynomial over 16 distinct variables, exponents in
+    {1,2,3}, coefficient moduli spread log-uniformly over 12 decades within each
+    polynomial and a planted root x* (planted_system).  Returns the workload (its start point is
+    the all-ones root; the planted root's own start root comes from tracking x*
+    backwards) and x*."""
+    L = _limbs(prec)
+    rng = Rng(seed)
+    f, xs = planted_system(rng, 128, 128, 16, (1, 2, 3), 12.0)
+    gamma = rng.unit_complex()
+    wl = Workload(f"precision128_{'dd' if L == 2 else 'qd'}", seed, L, f, gamma,
+                  np.ones(128, dtype=np.complex128), default_params(L))
+    return wl, xs
 
 
 def random_x(rng: Rng, n: int, radius: float = 1.0) -> np.ndarray:

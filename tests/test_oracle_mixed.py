@@ -128,3 +128,33 @@ def test_mixed_corrector_cube_root(orc, L, lin):
     ok2, x2, it2, *_ = orc.newton(f, start, 1.0, gam, params)
     assert ok2 and it <= it2 + (4 if lin == "f64" else 12)
     assert abs(est - 1.0) < 1e-6                 # a 1 x 1 system: r_00 / r_00
+
+
+def test_planted_root_is_exact(orc):
+    """The planted generator's constant terms make f(x*) = 0 exactly: checked
+    by evaluating every polynomial at x* in rationals, and by the oracle."""
+    from fractions import Fraction
+    rng = synth.Rng(9)
+    spec, xs = synth.planted_system(rng, 6, 7, 3, (1, 2, 3), 12.0)
+    for i in range(spec.N):
+        sre, sim = Fraction(0), Fraction(0)
+        for k in range(spec.term_ptr[i], spec.term_ptr[i + 1]):
+            cre = Fraction(spec.coeff[k].real) + Fraction(spec.coeff_lo[k].real)
+            cim = Fraction(spec.coeff[k].imag) + Fraction(spec.coeff_lo[k].imag)
+            ure, uim = Fraction(1), Fraction(0)
+            for q in range(spec.var_ptr[k], spec.var_ptr[k + 1]):
+                z = xs[spec.var_idx[q]]
+                for _ in range(int(spec.var_exp[q])):
+                    ure, uim = ure * Fraction(z.real) - uim * Fraction(z.imag), \
+                        ure * Fraction(z.imag) + uim * Fraction(z.real)
+            sre += cre * ure - cim * uim
+            sim += cre * uim + cim * ure
+        assert sre == 0 and sim == 0
+    for i in range(spec.N):                     # moduli in [1e-12, 1], the largest 1
+        ks = [k for k in range(spec.term_ptr[i], spec.term_ptr[i + 1])
+              if spec.var_ptr[k + 1] > spec.var_ptr[k]]
+        m = np.abs(spec.coeff[ks])
+        assert abs(m.max() - 1.0) < 1e-15 and m.min() >= 1e-12 * (1 - 1e-15)
+    for L in (2, 4):
+        h, _ = orc.eval_h(orc.System(spec, L), soa_from_complex(xs, L), t=1.0)
+        assert not np.any(h)
