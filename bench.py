@@ -256,7 +256,68 @@ def batch_starts(wl, count, seed=7):
     return out
 
 
-def serve_leg(libph, synth, ctx, nreq, seed):
+def batched_run(libph, ctx, f, wl, x0, params, torch, dev, flush):
+    """One ph_track_paths call over device-resident start points, timed with
+    CUDA events on the library's stream; returns (ms, stats)."""
+    stream = torch.cuda.current_stream(dev)
+    bx0 = torch.tensor(x0, dtype=torch.float64, device=dev)
+    bxo = torch.empty_like(bx0)
+    bgam = torch.tensor(wl.gamma_soa(), dtype=torch.float64, device=dev)
+    flush.zero_()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stats, _ = libph.ph_track_paths(ctx.h, f, None, bgam, bx0, params, bxo)
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1), stats
+
+
+def precision_leg(libph, synth, ctx, torch, dev, flush, seed, paths):
+    """The precision form against the plain form on the same batch of paths
+    (distinct total-degree start roots, the same segment of adaptive steps,
+    the same tolerances on every corrector): lin_prec 0 (all DD/QD), 1 (Newton
+    systems in double) and 3 (single where it costs no convergence, else
+    double); in QD also lin_prec 1 with one Newton iteration more, which the
+    double corrector's linear tail near 1e-52 needs.  Workload: precision128
+    (n = 128, coefficient moduli over 12 decades per equation, planted root),
+    first step size 1e-3 and 5 (DD) / 6 (QD) Newton iterations, where the
+    plain form accepts every step of its segment."""
+    out = {}
+    cases = [("dd", 6, 5, ((0, 0), (1, 0), (3, 0))),
+             ("qd", 3, 6, ((0, 0), (1, 0), (3, 0), (1, 1)))]
+    for prec, seg, mn, runs in cases:
+        wl = synth.precision128(seed, prec)[0]
+        f = ctx.load(wl.f, wl.L)
+        x0 = batch_starts(wl, paths)
+        row = {"paths": paths, "segment_steps": seg, "max_dt": 1e-3, "max_newton": mn}
+        base = None
+        for lin, extra in runs:
+            params = dict(wl.params, max_steps=seg - 1, max_dt=1e-3, max_newton=mn + extra,
+                          lin_prec=lin)
+            ms, st = batched_run(libph, ctx, f, wl, x0, params, torch, dev, flush)
+            it = sum(x["newton_iters"] for x in st)
+            acc = sum(x["accepted"] for x in st)
+            r = {"ms": ms, "corrector_steps_per_s": it / (ms * 1e-3),
+                 "accepted_steps_per_s": acc / (ms * 1e-3), "accepted_steps": acc,
+                 "segments_per_s": paths / (ms * 1e-3),
+                 "solves_f64": sum(x["solves_f64"] for x in st),
+                 "solves_f32": sum(x["solves_f32"] for x in st),
+                 "escalated": sum(x["escalated"] for x in st)}
+            conds = [x["cond"] for x in st if lin and np.isfinite(x["cond"]) and x["cond"] > 0]
+            if conds:
+                r["cond_estimate_median"] = float(np.median(conds))
+                r["cond_estimate_max"] = float(np.max(conds))
+            if base is None:
+                base = r
+            else:
+                r["accepted_steps_vs_plain"] = r["accepted_steps_per_s"] / base["accepted_steps_per_s"]
+            row[f"lin{lin}" + (f"_newton+{extra}" if extra else "")] = r
+        out[f"precision128_{prec}"] = row
+    return out
+
+
+def serve_leg(libph, synth, ctx, nreq, seed, lin=0, seq_rate=None):
     """A stream of path-tracking requests through the continuous-batching loop
     (ph_server_*).  A pool of 16 systems per (recipe, precision): n =
     round(exp(U[ln 16, ln 64])); the dense recipe (n terms per polynomial over
@@ -290,7 +351,7 @@ def serve_leg(libph, synth, ctx, nreq, seed):
         z = np.exp(2j * np.pi * rng.integers(0, d) / d)
         x0 = np.zeros((L, 2, spec.n))
         x0[0, 0], x0[0, 1] = z.real, z.imag
-        reqs.append((f, gam, x0, synth.default_params(L, max_steps=19)))
+        reqs.append((f, gam, x0, synth.default_params(L, max_steps=19, lin_prec=lin)))
 
     srv = libph.ph_server_create(ctx.h, max_n=64, pool_bytes=8 << 30, queue_cap=1024)
     try:
@@ -318,11 +379,13 @@ def serve_leg(libph, synth, ctx, nreq, seed):
         libph.ph_server_destroy(srv)
 
     k = min(16, nreq)
-    t0 = time.perf_counter()
-    for f, gam, x0, params in reqs[:k]:
-        libph.ph_track_path(ctx.h, f, None, gam, x0, params, np.zeros_like(x0))
-    seq_rate = k / (time.perf_counter() - t0)
-    return {"requests": nreq,
+    if seq_rate is None:                        # the plain single-path form
+        t0 = time.perf_counter()
+        for f, gam, x0, params in reqs[:k]:
+            libph.ph_track_path(ctx.h, f, None, gam, x0, dict(params, lin_prec=0),
+                                np.zeros_like(x0))
+        seq_rate = k / (time.perf_counter() - t0)
+    return {"requests": nreq, "lin_prec": lin,
             "mix": "n log-uniform in [16,64]; dense/sparse 50/50; DD/QD 70/30; "
                    "20 adaptive steps per request; 16 systems per recipe and precision",
             "closed_loop": {"paths_per_s": cap, "corrector_steps_per_s": iters / wall,
@@ -331,7 +394,8 @@ def serve_leg(libph, synth, ctx, nreq, seed):
             "poisson_0.8": {"offered_per_s": 0.8 * cap, "paths_per_s": nreq / wall2,
                             "p50_ms": float(np.percentile(lats2, 50)),
                             "p99_ms": float(np.percentile(lats2, 99))},
-            "sequential_single_path": {"paths_per_s": seq_rate, "sample": k},
+            "sequential_single_path": {"paths_per_s": seq_rate, "sample": k,
+                                       "form": "ph_track_path, all DD/QD"},
             "vs_sequential": cap / seq_rate,
             "kernel_launches": info["kernel_launches"]}
 
@@ -369,6 +433,8 @@ def main():
                          "host (one graph per step, as in the paper)")
     ap.add_argument("--batch-paths", type=int, default=304,
                     help="paths of the many-path leg (0 skips it)")
+    ap.add_argument("--precision-paths", type=int, default=152,
+                    help="paths of the precision-form leg (0 skips it)")
     ap.add_argument("--serve-requests", type=int, default=384,
                     help="requests of the serving leg (0 skips it)")
     ap.add_argument("--no-sparse", action="store_true",
@@ -467,9 +533,16 @@ def main():
                               "achieved": bach, "peak": peak, "unit": "G FP64-ops/s",
                               "frac": bach / peak}}
 
-    serve = None
+    serve = serve_mixed = None
     if args.serve_requests > 0 and rank == 0:
         serve = serve_leg(libph, synth, ctx, args.serve_requests, args.seed)
+        serve_mixed = serve_leg(libph, synth, ctx, args.serve_requests, args.seed, lin=3,
+                                seq_rate=serve["sequential_single_path"]["paths_per_s"])
+
+    precision = None
+    if args.precision_paths > 0 and rank == 0:
+        precision = precision_leg(libph, synth, ctx, torch, dev, flush, args.seed,
+                                  args.precision_paths)
 
     # end to end through the same call with host buffers
     e2e_v, h2d, d2h = e2e_leg(libph, ctx, f, wl, max(2, args.steps // 2), torch)
@@ -530,6 +603,7 @@ def main():
             "segments_per_s": s["paths_per_s"], "pc_steps_per_s": s["pc_steps_per_s"],
             "p50_segment_ms": s["p50_segment_ms"], "p99_segment_ms": s["p99_segment_ms"],
             "path": s["path"], "qd": qd, "batched": batch, "serving": serve,
+            "serving_mixed": serve_mixed, "precision": precision,
             "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": s["launches"], "roofline": roof, "roofline_sparse512_mgs": roof512,

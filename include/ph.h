@@ -132,13 +132,23 @@ typedef struct {
    *      a power of two before it is rounded.  Each iteration contracts the
    *      error by about kappa(J) u_double instead of squaring it;
    *   2  the same in IEEE single;
-   *   3  single while the previous factorization's condition estimate
-   *      (max r_kk / min r_kk) is at most cond_f32, else double.
+   *   3  automatic: single where it costs no convergence, else double.  A
+   *      solve is single when the previous factorization's condition
+   *      estimate kappa (max r_kk / min r_kk) is at most cond_f32 and, after
+   *      the step's first iteration, the current error, estimated as the
+   *      square of the last update norm, is at least kappa 2^-24 (the single
+   *      solve's relative error), so Newton's quadratic convergence holds.
    * In 2 and 3 a single-precision factorization that is not finite is redone
-   * in double.  A step whose low-precision corrector fails is corrected again
-   * from its predicted point in working precision before it counts as a
-   * failure (step size halved), and steps to t >= endgame_t run in working
-   * precision throughout (the end game).
+   * in double.  A step whose low-precision corrector fails is
+   * corrected once more from its predicted point one precision up before it
+   * counts as a failure (step size halved): in double if it solved in single
+   * under lin_prec 2; in working precision if a double solve had
+   * kappa u_double above 1e-6 or the corrector failed after an update below
+   * sqrt(tol_dx), where the working-precision corrector might have succeeded.
+   * A corrector that fails while its updates are still large follows the
+   * working-precision iterates to kappa u_low, and so does their failure.
+   * Steps to t >= endgame_t run in working precision throughout (the end
+   * game).
    * Only ph_track_paths and the serving loop take lin_prec != 0. */
   int32_t lin_prec;
   int32_t reserved;   /* 0                                                        */
@@ -161,7 +171,7 @@ typedef struct {
   int32_t solves_f64;   /* Newton systems solved in double (lin_prec != 0)        */
   int32_t solves_f32;   /* ... and in single                                       */
   int32_t escalated;    /* steps whose low-precision corrector failed and that
-                           were corrected again in working precision             */
+                           were corrected again one precision up                 */
   int32_t reserved;
   double cond;          /* condition estimate of the last low-precision solve    */
 } ph_path_stats;

@@ -21,6 +21,10 @@ constexpr int kBT = 256;          // threads per block: 8 warps, 2 per SM sub-pa
 constexpr int kNW = kBT / 32;
 constexpr int kHistB = 16;        // accepted points kept for the predictor
 constexpr int kSG = 4;            // lanes per output in the summation
+// A failed step is corrected again in working precision only if one of its
+// double-precision solves had kappa u_double above this: below it the double
+// corrector contracts like the working-precision one.
+constexpr double kEscalateRho = 1e-6;
 
 struct Job {
   int L, N, n, Mf, Mpf, maxvf, Mg, Mpg, maxvg, emax, nout;
@@ -255,7 +259,8 @@ __device__ void track_job(const Job &a, double *smem) {
   __shared__ double s_tn, s_last, s_res, s_dxn, s_dxmax, s_xmax;
   __shared__ unsigned long long s_resbits;
   __shared__ ph_path_stats s_st;
-  __shared__ int s_lin, s_scale_e, s_force_wp, s_lp_used;
+  __shared__ int s_lin, s_scale_e, s_force, s_escalate, s_lp_solves;
+  __shared__ double s_dxmin;
   __shared__ double s_cond, s_kappa;
 
   const int n = a.n, N = a.N, tid = threadIdx.x;
@@ -327,10 +332,17 @@ __device__ void track_job(const Job &a, double *smem) {
     if (tid == 0) {
       tl[0] = tn;
       for (int l = 1; l < P::L; ++l) tl[l] = 0.0;
-      s_force_wp = 0;
+      s_force = 0;
     }
-    // A step whose mixed-precision corrector fails is corrected again from the
-    // predicted point in working precision (pass 1) before it counts as failed.
+    // A step whose mixed-precision corrector fails is corrected once more from
+    // the predicted point one precision up (pass 1) before it counts as failed,
+    // wherever the working-precision corrector might have decided otherwise:
+    // in double if it solved in single by request (lin_prec 2); in working
+    // precision if a double solve had kappa u_double above kEscalateRho (the
+    // estimate is only a lower bound of kappa) or if it failed after reaching
+    // the path (an update below sqrt(tol_dx)).  A corrector that failed while
+    // its updates were still large takes the same iterates, to kappa u_low, as
+    // the working-precision one, which fails too: the step size halves.
     for (int pass = 0;; ++pass) {
       if (tid == 0) {
         s_last = a.p.max_res;
@@ -338,7 +350,9 @@ __device__ void track_job(const Job &a, double *smem) {
         s_ok = fixed ? 1 : 0;
         s_upd = 0;
         s_iters = 0;
-        s_lp_used = 0;
+        s_escalate = 0;
+        s_lp_solves = 0;
+        s_dxmin = INFINITY;
       }
       __syncthreads();
       for (int i = tid; i < n; i += kBT) {
@@ -354,8 +368,13 @@ __device__ void track_job(const Job &a, double *smem) {
         __syncthreads();
         if (tid == 0) {                              // the precision of this iteration's solve
           int lin = a.p.lin_prec;
-          if (tn >= endgame || s_force_wp) lin = 0;
-          if (lin == 3) lin = s_cond <= cond32 ? 2 : 1;
+          if (tn >= endgame || s_force == 2) lin = 0;
+          // automatic: single on a step's first iteration and while the current
+          // error, estimated as the square of the last update, is at least the
+          // single-precision solve's relative error kappa u_single
+          if (lin == 3)
+            lin = s_cond <= cond32 && (it == 0 || s_dxn * s_dxn >= s_cond * 0x1p-24) ? 2 : 1;
+          if (s_force == 1 && lin == 2) lin = 1;
           s_lin = lin;
           s_resbits = 0ull;
         }
@@ -434,6 +453,7 @@ __device__ void track_job(const Job &a, double *smem) {
           ms = lin == 2 ? lowprec_solve<P, F32>(a, x, tl, hl, s_scale_e, ptab, spow, scal, fslots,
                                                 gslots, A, W, dx, s_nrm, s_y, &s_dxmax, &s_kappa)
                         : PH_NONFINITE;
+          double u_lin = 0x1p-24;                    // unit roundoff of the solve used
           if (lin == 2 && tid == 0) {
             if (ms == PH_OK) s_st.solves_f32 += 1;
             s_cond = ms == PH_OK ? s_kappa : INFINITY;
@@ -441,6 +461,7 @@ __device__ void track_job(const Job &a, double *smem) {
           if (lin == 1 || ms != PH_OK) {             // double (also the retry of a failed single)
             ms = lowprec_solve<P, F64>(a, x, tl, hl, s_scale_e, ptab, spow, scal, fslots, gslots, A,
                                        W, dx, s_nrm, s_y, &s_dxmax, &s_kappa);
+            u_lin = 0x1p-53;
             if (tid == 0) {
               s_st.solves_f64 += 1;
               s_cond = ms == PH_OK ? s_kappa : INFINITY;
@@ -448,7 +469,12 @@ __device__ void track_job(const Job &a, double *smem) {
           }
           if (tid == 0) {
             s_st.cond = s_cond;
-            s_lp_used = 1;
+            s_lp_solves += 1;
+            if (u_lin > 0x1p-53) {
+              if (a.p.lin_prec == 2) s_escalate = max(s_escalate, 1);  // single by request
+            } else if (!(s_cond * u_lin <= kEscalateRho)) {
+              s_escalate = 2;
+            }
           }
         }
         if (ms != PH_OK && !fixed) {
@@ -480,14 +506,20 @@ __device__ void track_job(const Job &a, double *smem) {
             else s_last = s_res;
           }
           if (!s_dec && s_iters >= a.p.max_newton) { s_dec = 1; s_ok = fixed ? 1 : 0; }
+          s_dxmin = fmin(s_dxmin, d);
         }
         __syncthreads();
         if (s_dec) break;
       }
       __syncthreads();
-      if (pass == 0 && !s_ok && s_lp_used && !fixed) {
+      // a low-precision corrector that failed after reaching the path (an update
+      // below sqrt(tol_dx)) was held back by its precision: the working-
+      // precision corrector would have squared that update
+      if (tid == 0 && !s_ok && s_lp_solves > 0 && s_dxmin <= sqrt(a.p.tol_dx)) s_escalate = 2;
+      __syncthreads();
+      if (pass == 0 && !s_ok && s_escalate && !fixed) {
         if (tid == 0) {
-          s_force_wp = 1;
+          s_force = s_escalate;
           s_st.escalated += 1;
         }
         __syncthreads();
