@@ -433,6 +433,8 @@ def main():
                          "host (one graph per step, as in the paper)")
     ap.add_argument("--batch-paths", type=int, default=304,
                     help="paths of the many-path leg (0 skips it)")
+    ap.add_argument("--batch-steps", type=int, default=None,
+                    help="steps per path of the many-path leg (default: the segment)")
     ap.add_argument("--precision-paths", type=int, default=152,
                     help="paths of the precision-form leg (0 skips it)")
     ap.add_argument("--serve-requests", type=int, default=384,
@@ -511,19 +513,22 @@ def main():
         bx0 = torch.tensor(batch_starts(wl, args.batch_paths), dtype=torch.float64, device=dev)
         bxo = torch.empty_like(bx0)
         bgam = torch.tensor(wl.gamma_soa(), dtype=torch.float64, device=dev)
-        libph.ph_track_paths(ctx.h, f, None, bgam, bx0, seg_params(wl), bxo)   # warm-up
+        bparams = seg_params(wl)
+        if args.batch_steps:
+            bparams["max_steps"] = args.batch_steps - 1
+        libph.ph_track_paths(ctx.h, f, None, bgam, bx0, bparams, bxo)   # warm-up
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        bstats, _ = libph.ph_track_paths(ctx.h, f, None, bgam, bx0, seg_params(wl), bxo)
+        bstats, _ = libph.ph_track_paths(ctx.h, f, None, bgam, bx0, bparams, bxo)
         e1.record(stream)
         e1.synchronize()
         bms = e0.elapsed_time(e1)
         bit = sum(x["newton_iters"] for x in bstats)
         bops = bit * (ad_ops(wl.f, wl.L) + sum_ops(wl.f, wl.L) + mgs_ops(wl.f.N, wl.n, wl.L))
         bach = bops / (bms * 1e-3) / 1e9
-        batch = {"paths": args.batch_paths, "ms": bms,
+        batch = {"paths": args.batch_paths, "steps_per_path": bparams["max_steps"] + 1, "ms": bms,
                  "corrector_steps_per_s": bit / (bms * 1e-3),
                  "pc_steps_per_s": sum(x["steps"] for x in bstats) / (bms * 1e-3),
                  "segments_per_s": args.batch_paths / (bms * 1e-3),

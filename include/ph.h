@@ -139,12 +139,16 @@ typedef struct {
    *      square of the last update norm, is at least kappa 2^-24 (the single
    *      solve's relative error), so Newton's quadratic convergence holds.
    * In 2 and 3 a single-precision factorization that is not finite is redone
-   * in double.  A step whose low-precision corrector fails is
+   * in double.  On adaptive steps a low-precision corrector gets one
+   * iteration beyond max_newton when its previous update was below
+   * sqrt(tol_dx) (the working-precision corrector would have squared that
+   * update below tol_dx and succeeded).  A step whose low-precision corrector
+   * fails is
    * corrected once more from its predicted point one precision up before it
    * counts as a failure (step size halved): in double if it solved in single
    * under lin_prec 2; in working precision if a double solve had
-   * kappa u_double above 1e-6 or the corrector failed after an update below
-   * sqrt(tol_dx), where the working-precision corrector might have succeeded.
+   * kappa u_double above 1e-6 or the corrector failed although an update
+   * below sqrt(tol_dx) was followed by another.
    * A corrector that fails while its updates are still large follows the
    * working-precision iterates to kappa u_low, and so does their failure.
    * Steps to t >= endgame_t run in working precision throughout (the end

@@ -259,8 +259,7 @@ __device__ void track_job(const Job &a, double *smem) {
   __shared__ double s_tn, s_last, s_res, s_dxn, s_dxmax, s_xmax;
   __shared__ unsigned long long s_resbits;
   __shared__ ph_path_stats s_st;
-  __shared__ int s_lin, s_scale_e, s_force, s_escalate, s_lp_solves;
-  __shared__ double s_dxmin;
+  __shared__ int s_lin, s_scale_e, s_force, s_escalate, s_onpath;
   __shared__ double s_cond, s_kappa;
 
   const int n = a.n, N = a.N, tid = threadIdx.x;
@@ -339,10 +338,11 @@ __device__ void track_job(const Job &a, double *smem) {
     // wherever the working-precision corrector might have decided otherwise:
     // in double if it solved in single by request (lin_prec 2); in working
     // precision if a double solve had kappa u_double above kEscalateRho (the
-    // estimate is only a lower bound of kappa) or if it failed after reaching
-    // the path (an update below sqrt(tol_dx)).  A corrector that failed while
-    // its updates were still large takes the same iterates, to kappa u_low, as
-    // the working-precision one, which fails too: the step size halves.
+    // estimate is only a lower bound of kappa) or if it failed although an
+    // update below sqrt(tol_dx) was followed by another one (the working-
+    // precision corrector would have succeeded there).  A corrector that fails
+    // while its updates are still large takes the working-precision iterates,
+    // to kappa u_low, and fails as that one would: the step size halves.
     for (int pass = 0;; ++pass) {
       if (tid == 0) {
         s_last = a.p.max_res;
@@ -351,8 +351,7 @@ __device__ void track_job(const Job &a, double *smem) {
         s_upd = 0;
         s_iters = 0;
         s_escalate = 0;
-        s_lp_solves = 0;
-        s_dxmin = INFINITY;
+        s_onpath = 0;
       }
       __syncthreads();
       for (int i = tid; i < n; i += kBT) {
@@ -364,7 +363,12 @@ __device__ void track_job(const Job &a, double *smem) {
         c_store<P>(x, n, i, acc);
       }
       // corrector (Fig. "An accelerated Newton's method")
-      for (int it = 0; it < a.p.max_newton; ++it) {
+      // One iteration beyond max_newton for a low-precision corrector whose
+      // previous update was below sqrt(tol_dx): the working-precision corrector
+      // would have squared that update below tol_dx and succeeded by now, while
+      // the low-precision one contracts only by kappa u_low per iteration.
+      const int max_it = fixed ? a.p.max_newton : a.p.max_newton + 1;
+      for (int it = 0; it < max_it; ++it) {
         __syncthreads();
         if (tid == 0) {                              // the precision of this iteration's solve
           int lin = a.p.lin_prec;
@@ -469,7 +473,6 @@ __device__ void track_job(const Job &a, double *smem) {
           }
           if (tid == 0) {
             s_st.cond = s_cond;
-            s_lp_solves += 1;
             if (u_lin > 0x1p-53) {
               if (a.p.lin_prec == 2) s_escalate = max(s_escalate, 1);  // single by request
             } else if (!(s_cond * u_lin <= kEscalateRho)) {
@@ -496,6 +499,8 @@ __device__ void track_job(const Job &a, double *smem) {
         }
         if (tid == 0) {                              // update test
           const double d = ms != PH_OK ? NAN : (lin == 0 ? s_dxmax : ldexp(s_dxmax, e));
+          const bool prev_on_path = lin != 0 && s_upd >= 1 && s_dxn <= sqrt(a.p.tol_dx);
+          if (prev_on_path) s_onpath = 1;
           s_dxn = d;
           s_st.dx = d;
           s_upd += 1;
@@ -505,17 +510,19 @@ __device__ void track_job(const Job &a, double *smem) {
             else if (d < a.p.tol_dx) { s_dec = 1; s_ok = 1; }
             else s_last = s_res;
           }
-          if (!s_dec && s_iters >= a.p.max_newton) { s_dec = 1; s_ok = fixed ? 1 : 0; }
-          s_dxmin = fmin(s_dxmin, d);
+          if (!s_dec && s_iters >= a.p.max_newton && !(prev_on_path && s_iters < max_it)) {
+            s_dec = 1;
+            s_ok = fixed ? 1 : 0;
+          }
         }
         __syncthreads();
         if (s_dec) break;
       }
       __syncthreads();
-      // a low-precision corrector that failed after reaching the path (an update
-      // below sqrt(tol_dx)) was held back by its precision: the working-
-      // precision corrector would have squared that update
-      if (tid == 0 && !s_ok && s_lp_solves > 0 && s_dxmin <= sqrt(a.p.tol_dx)) s_escalate = 2;
+      // a low-precision corrector that failed after an update below
+      // sqrt(tol_dx) followed by another: the working-precision corrector
+      // would have succeeded
+      if (tid == 0 && !s_ok && s_onpath) s_escalate = 2;
       __syncthreads();
       if (pass == 0 && !s_ok && s_escalate && !fixed) {
         if (tid == 0) {
