@@ -200,6 +200,12 @@ SEGMENT = {2: 50, 4: 20}       # predictor-corrector steps per bench step
 CONTROL = {"control": 0}       # 1: host-side step control (for profiling runs)
 
 
+# DRAM bytes (read + write) of one k_mgs<DD> launch on the dense64 DD system,
+# from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# current kernel: the 64 x 65 matrix and the projection coefficients, read once.
+MGS_DENSE64_DD_TRAFFIC = 232960
+
+
 def seg_params(wl):
     return dict(wl.params, max_steps=SEGMENT[wl.L] - 1, control=CONTROL["control"])
 
@@ -565,7 +571,8 @@ def main():
     dms = kms[names.index(dom)]
     achieved = ops[dom] / (dms * 1e-3) / 1e9
     roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
-            "unit": "G FP64-ops/s", "frac": achieved / peak, "traffic": None,
+            "unit": "G FP64-ops/s", "frac": achieved / peak,
+            "traffic": MGS_DENSE64_DD_TRAFFIC if dom == "mgs" else None,
             "peak_source": "measured DFMA rate on this GPU in this run (ph_fp64_peak)",
             "kernel_ms": dict(zip(names, kms)), "ops_per_launch": ops[dom]}
 
