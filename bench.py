@@ -572,7 +572,7 @@ def main():
     achieved = ops[dom] / (dms * 1e-3) / 1e9
     roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
             "unit": "G FP64-ops/s", "frac": achieved / peak,
-            "traffic": MGS_DENSE64_DD_TRAFFIC if dom == "mgs" else None,
+            "traffic": MGS_DENSE64_DD_TRAFFIC if dom == "mgs" and wl.L == 2 else None,
             "peak_source": "measured DFMA rate on this GPU in this run (ph_fp64_peak)",
             "kernel_ms": dict(zip(names, kms)), "ops_per_launch": ops[dom]}
 
