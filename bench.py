@@ -323,6 +323,48 @@ def precision_leg(libph, synth, ctx, torch, dev, flush, seed, paths):
     return out
 
 
+# The paper's summation-kernel times on its K20C (Section 3.3, the tables for
+# cyclic 128- and 352-roots, ms per evaluation at the best number of threads
+# per sum): context, not targets.
+PAPER_CYCLIC_SUM_MS = {(128, 2): 0.53, (128, 4): 1.35, (352, 2): 9.69, (352, 4): 24.61}
+
+
+def cyclic_leg(libph, synth, ctx, torch, dev, peak):
+    """Cyclic n-roots (Section 4.2, Eq. (8)), n = 128 and 352, in DD and QD:
+    one corrector iteration's kernels at a random point of the unit torus
+    (t = 0.5, total-degree homotopy), event-timed on the library's stream: ms per
+    evaluation of h and its Jacobian (power table + monomial AD + summation), of
+    the summation alone (the paper's own timing of this system) and per MGS solve,
+    and the AD kernel's fraction of the measured FP64 rate."""
+    out = {}
+    for n in (128, 352):
+        spec = synth.cyclic_system(n)
+        rng = np.random.default_rng(n)
+        z = np.exp(2j * np.pi * rng.random(n))
+        for L in (2, 4):
+            f = ctx.load(spec, L)
+            xs = np.zeros((L, 2, n))
+            xs[0, 0], xs[0, 1] = z.real, z.imag
+            x = torch.tensor(xs, dtype=torch.float64, device=dev)
+            gam = torch.zeros((L, 2), dtype=torch.float64, device=dev)
+            gam[0, 0], gam[0, 1] = 0.6, 0.8
+            tl = torch.zeros(L, dtype=torch.float64, device=dev)
+            tl[0] = 0.5
+            kms = libph.ph_profile_newton(ctx.h, f, None, gam, 1, tl, x, 3 if n > 200 else 10)
+            ev = kms[0] + kms[1] + kms[2]
+            ad = ad_ops(spec, L)
+            r = {"eval_ms": ev, "mgs_ms": kms[3], "kernel_ms": dict(zip(
+                     ["prep", "monomial_ad", "summation", "mgs"], kms)),
+                 "monomials": int(spec.M),
+                 "ad_frac_of_fp64_peak": ad / (kms[1] * 1e-3) / 1e9 / peak,
+                 "summation_ms": kms[2],
+                 "paper_k20c_summation_ms": PAPER_CYCLIC_SUM_MS[(n, L)],
+                 "summation_vs_paper_k20c": PAPER_CYCLIC_SUM_MS[(n, L)] / kms[2]}
+            out[f"cyclic{n}_{'dd' if L == 2 else 'qd'}"] = r
+            ctx.free(f)
+    return out
+
+
 def serve_leg(libph, synth, ctx, nreq, seed, lin=0, seq_rate=None):
     """A stream of path-tracking requests through the continuous-batching loop
     (ph_server_*).  A pool of 16 systems per (recipe, precision): n =
@@ -445,6 +487,7 @@ def main():
                     help="paths of the precision-form leg (0 skips it)")
     ap.add_argument("--serve-requests", type=int, default=384,
                     help="requests of the serving leg (0 skips it)")
+    ap.add_argument("--no-cyclic", action="store_true", help="skip the cyclic n-roots leg")
     ap.add_argument("--no-sparse", action="store_true",
                     help="skip the n=512 QD solver roofline measurement")
     args = ap.parse_args()
@@ -550,6 +593,10 @@ def main():
         serve_mixed = serve_leg(libph, synth, ctx, args.serve_requests, args.seed, lin=3,
                                 seq_rate=serve["sequential_single_path"]["paths_per_s"])
 
+    cyclic = None
+    if not args.no_cyclic and rank == 0:
+        cyclic = cyclic_leg(libph, synth, ctx, torch, dev, peak)
+
     precision = None
     if args.precision_paths > 0 and rank == 0:
         precision = precision_leg(libph, synth, ctx, torch, dev, flush, args.seed,
@@ -615,7 +662,7 @@ def main():
             "segments_per_s": s["paths_per_s"], "pc_steps_per_s": s["pc_steps_per_s"],
             "p50_segment_ms": s["p50_segment_ms"], "p99_segment_ms": s["p99_segment_ms"],
             "path": s["path"], "qd": qd, "batched": batch, "serving": serve,
-            "serving_mixed": serve_mixed, "precision": precision,
+            "serving_mixed": serve_mixed, "precision": precision, "cyclic": cyclic,
             "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": s["launches"], "roofline": roof, "roofline_sparse512_mgs": roof512,

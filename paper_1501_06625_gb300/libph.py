@@ -348,6 +348,11 @@ class Context:
         self.systems.append(s)
         return s
 
+    def free(self, s):
+        """Frees one loaded system before the context closes."""
+        self.systems.remove(s)
+        ph_system_free(s)
+
     def close(self):
         if self.h:
             for s in self.systems:

@@ -234,16 +234,33 @@ def planted_system(rng: Rng, n: int, terms_per_poly: int, vars_per_term: int,
 
 def cyclic_system(n: int) -> SystemSpec:
     """Cyclic n-roots (Section 4.2, Eq. (8)): f_i = sum_j prod_{k=j}^{j+i-1}
-    x_{k mod n} for i = 1..n-1, and f_n = x_0 x_1 ... x_{n-1} - 1."""
-    polys = []
-    for i in range(1, n):
-        terms = []
-        for j in range(n):
-            vs = sorted((j + k) % n for k in range(i))
-            terms.append((1.0, [(v, 1) for v in vs]))
-        polys.append(terms)
-    polys.append([(1.0, [(v, 1) for v in range(n)]), (-1.0, [])])
-    return build_system(n, n, polys)
+    x_{k mod n} for i = 1..n-1, and f_n = x_0 x_1 ... x_{n-1} - 1.  Built with
+    array operations: n = 352 has about 21.7 million (variable, exponent)
+    pairs.  The variables of each term are listed in increasing order."""
+    if n < 2:
+        raise ValueError("cyclic n-roots needs n >= 2")
+    lengths = [np.full(n, i, dtype=np.int64) for i in range(1, n)]
+    lengths.append(np.array([n, 0], dtype=np.int64))          # x_0..x_{n-1}, then -1
+    tl = np.concatenate(lengths)                               # variables per term
+    M = tl.size
+    var_ptr = np.zeros(M + 1, dtype=np.int64)
+    np.cumsum(tl, out=var_ptr[1:])
+    var_idx = np.empty(int(var_ptr[-1]), dtype=np.int32)
+    pos = 0
+    for i in range(1, n):                                      # terms of f_i: windows of i
+        j = np.arange(n)[:, None]
+        win = (j + np.arange(i)[None, :]) % n
+        win.sort(axis=1)
+        var_idx[pos:pos + n * i] = win.ravel()
+        pos += n * i
+    var_idx[pos:pos + n] = np.arange(n)
+    term_ptr = np.zeros(n + 1, dtype=np.int64)
+    term_ptr[1:n] = n * np.arange(1, n)
+    term_ptr[n] = M
+    coeff = np.ones(M, dtype=np.complex128)
+    coeff[-1] = -1.0
+    return SystemSpec(n, n, term_ptr.astype(np.int32), var_ptr.astype(np.int32), var_idx,
+                      np.ones(var_idx.size, dtype=np.int32), coeff)
 
 
 def default_params(L: int, **over) -> dict:
