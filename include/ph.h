@@ -276,6 +276,17 @@ ph_status ph_server_job_bytes(ph_server *srv, const ph_system *f, const ph_syste
 /* Stops the loop (running jobs finish first) and frees the server. */
 ph_status ph_server_destroy(ph_server *srv);
 
+/* The variant of the least-squares solve this context uses for an N x n
+ * system of precision prec: *cluster = 0 for the grid kernel (one block per
+ * column, pivots handed over through L2), C > 0 for the cluster kernel (the
+ * matrix in the shared memory of one cluster of C blocks).  The choice is
+ * measured once per context and shape on a scratch matrix (the fastest of the
+ * two; the grid kernel where the matrix does not fit a cluster);
+ * ms_grid / ms_cluster (optional) receive the measured times, -1 where only
+ * one variant applies.  The paper has no counterpart (it has one MGS kernel). */
+ph_status ph_mgs_variant(ph_ctx *ctx, ph_prec prec, int N, int n, int *cluster, double *ms_grid,
+                         double *ms_cluster);
+
 /* Host-side step-size controller of the path tracker, exported so it can be
  * checked without a GPU: the same code runs inside the device controller.
  * Fig. "Accelerated tracking of one single path". */

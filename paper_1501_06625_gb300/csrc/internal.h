@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
+#include <utility>
 #include <string>
 #include <vector>
 
@@ -67,6 +69,11 @@ struct ph_ctx {
   DevBuf out_h, out_J, out_dx;                      // staged outputs
   DevBuf slots, ptab, scal, A, R, nrm2, irkk, dxv, state, hist, xw, logbuf, ystage, flags, spow;
   DevBuf bws, bq, bx0, bxo, bstats, blog;           // many-path tracking
+  // the MGS variant chosen for each shape (key (L, N, n)): 0 the grid kernel,
+  // C > 0 the cluster kernel with C CTAs; scratch buffers of the choice
+  std::map<long long, int> mgs_variant;
+  std::map<long long, std::pair<float, float>> mgs_times;   // ms: grid, cluster
+  DevBuf tuneA, tuneW, tuneN, tuneF, tuneX, tuneS;
 };
 
 // A loaded polynomial system: the instruction layout of Section 3.2 (terms
@@ -126,3 +133,16 @@ cudaError_t ph_mgs_launch(ph_ctx *ctx, int L, int N, int n, double *A, long ldA,
                           PathState *st, const int *skip, double *resid);
 
 int ph_mgs_grid(ph_ctx *ctx, int L, int N, int n);
+
+// The MGS variant for a shape, measured once per context on a scratch matrix
+// (outside stream capture; during a capture an unmeasured shape gets the grid
+// kernel): 0 = grid kernel, C > 0 = cluster kernel with C CTAs.
+int ph_mgs_tune(ph_ctx *ctx, int L, int N, int n);
+
+// mgs_cluster.cu: the same solve on one thread-block cluster (A is read, not
+// modified).  ph_mgs_cluster_size: 16 or 8 CTAs, or 0 if the matrix does not
+// fit in a cluster's shared memory.
+int ph_mgs_cluster_size(int L, int N, int n);
+cudaError_t ph_mgs_cluster_launch(cudaStream_t stream, int C, int L, int N, int n, const double *A,
+                                  long ldA, double *W, double *dx, PathState *st, const int *skip,
+                                  double *resid);

@@ -47,6 +47,8 @@ namespace {
 
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;
 constexpr int kThreads = 128;
+constexpr int kRowCache = 4;        // pivot rows a lane keeps in registers (N <= 256)
+constexpr int kDowndateBits = 20;   // cancellation beyond which a norm is recomputed
 
 PHD unsigned long long global_timer_ns() {
   unsigned long long t;
@@ -150,7 +152,7 @@ __device__ typename P::real col_norm2(const double *col, long Ap, int N, int par
 }
 
 // W: alpha_kj at W[(2l+c) Wp + j nc + k] (column j of the alphas);
-// nrm2: ||a_k||^2 [L][nc]; ready: [nc] pivot flags.
+// nrm2: [L][nc] ||a_j||^2, then [L][nc] 1/||a_j||^2; ready: [nc] pivot flags.
 template <class P>
 __global__ void __launch_bounds__(kThreads) k_mgs(int N, int n, double *__restrict__ A, long ldA,
                                                   double *__restrict__ W, double *__restrict__ nrm2,
@@ -165,6 +167,7 @@ __global__ void __launch_bounds__(kThreads) k_mgs(int N, int n, double *__restri
   extern __shared__ double s_y[];                // back substitution: [L][2][n]
   const int nc = n + 1;
   const long Ap = (long)nc * ldA, Wp = (long)nc * nc;
+  double *ninv = nrm2 + (long)P::L * nc;
   const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
   const int w = tid >> 5, lane = tid & 31;
   const int part = w >> 1;                       // 0 = real, 1 = imaginary
@@ -172,26 +175,53 @@ __global__ void __launch_bounds__(kThreads) k_mgs(int N, int n, double *__restri
   const int tag = st->mgs_epoch + 1;
   const int last_own = b + ((n - b) / G) * G;    // largest column this block owns
 
-  if (b == 0) {
-    real s = col_norm2<P>(A, Ap, N, part, r0, sh_acc, sh_r);
-    if (tid == 0) r_store<P>(nrm2, nc, 0, s);
-    publish(&ready[0], tag);
+  // the norms of this block's columns; column 0 first, published at once
+  for (int j = b; j <= n; j += G) {
+    real s = col_norm2<P>(A + (long)j * ldA, Ap, N, part, r0, sh_acc, sh_r);
+    if (tid == 0) {
+      r_store<P>(nrm2, nc, j, s);
+      if (j == 0) r_store<P>(ninv, nc, 0, P::recip(s));
+    }
+    if (j == 0) publish(&ready[0], tag);
   }
   for (int k = 0; k < last_own; ++k) {
     if (!wait_flag(&ready[k], tag, st)) break;
     const real r2 = r_load_cg<P>(nrm2, nc, k);
+    const real inv2 = r_load_cg<P>(ninv, nc, k);
     const double lead = P::lead(r2);
-    if (!(lead > 0.0) || !isfinite(lead)) {      // every block reads the same value
-      if (tid == 0) atomicExch(&st->mgs_status, PH_NONFINITE);
+    if (!(lead > 0.0) || !isfinite(lead) || !isfinite(P::lead(inv2))) {
+      if (tid == 0) atomicExch(&st->mgs_status, PH_NONFINITE);   // the same value in every block
       break;
     }
-    const real inv2 = P::recip(r2);
     const double *ak = A + (long)k * ldA;
+    // this lane's first kRowCache rows of the pivot column, loaded once per
+    // pivot and kept in registers for every column's dot product and update
+    real ck_r[kRowCache], ck_i[kRowCache];
+#pragma unroll
+    for (int q = 0; q < kRowCache; ++q) {
+      const int i = r0 + 64 * q;
+      if (i < N) {
+        ck_r[q] = load_part_cg<P>(ak, Ap, 0, i);
+        ck_i[q] = load_part_cg<P>(ak, Ap, 1, i);
+      }
+    }
     for (int j = k + 1 + (((b - (k + 1)) % G) + G) % G; j <= n; j += G) {
       double *aj = A + (long)j * ldA;
+      // ||a_j||^2 before this update, read before the barriers of the reduction
+      // below (thread 0 overwrites it after them)
+      const real old = r_load<P>(nrm2, nc, j);
       // this warp's part of a_k^H a_j:  re = akr ajr + aki aji,  im = akr aji - aki ajr
       typename PO::acc a = PO::zero();
-      for (int i = r0; i < N; i += 64) {
+#pragma unroll
+      for (int q = 0; q < kRowCache; ++q) {
+        const int i = r0 + 64 * q;
+        if (i < N) {
+          real ajr = load_part<P>(aj, Ap, 0, i), aji = load_part<P>(aj, Ap, 1, i);
+          if (part == 0) PO::dot2(a, ck_r[q], ajr, ck_i[q], aji, 1.0);
+          else PO::dot2(a, ck_r[q], aji, ck_i[q], ajr, -1.0);
+        }
+      }
+      for (int i = r0 + 64 * kRowCache; i < N; i += 64) {
         real akr = load_part_cg<P>(ak, Ap, 0, i), aki = load_part_cg<P>(ak, Ap, 1, i);
         real ajr = load_part<P>(aj, Ap, 0, i), aji = load_part<P>(aj, Ap, 1, i);
         if (part == 0) PO::dot2(a, akr, ajr, aki, aji, 1.0);
@@ -209,19 +239,41 @@ __global__ void __launch_bounds__(kThreads) k_mgs(int N, int n, double *__restri
         }
       }
       // a_j -= alpha a_k:  re: ajr - alr akr + ali aki;  im: aji - alr aki - ali akr
-      for (int i = r0; i < N; i += 64) {
+#pragma unroll
+      for (int q = 0; q < kRowCache; ++q) {
+        const int i = r0 + 64 * q;
+        if (i < N) {
+          if (part == 0)
+            store_part<P>(aj, Ap, 0, i,
+                          PO::upd(load_part<P>(aj, Ap, 0, i), alr, ck_r[q], ali, ck_i[q], 1.0));
+          else
+            store_part<P>(aj, Ap, 1, i,
+                          PO::upd(load_part<P>(aj, Ap, 1, i), alr, ck_i[q], ali, ck_r[q], -1.0));
+        }
+      }
+      for (int i = r0 + 64 * kRowCache; i < N; i += 64) {
         real akr = load_part_cg<P>(ak, Ap, 0, i), aki = load_part_cg<P>(ak, Ap, 1, i);
         if (part == 0)
           store_part<P>(aj, Ap, 0, i, PO::upd(load_part<P>(aj, Ap, 0, i), alr, akr, ali, aki, 1.0));
         else
           store_part<P>(aj, Ap, 1, i, PO::upd(load_part<P>(aj, Ap, 1, i), alr, aki, ali, akr, -1.0));
       }
-      if (j == k + 1) {
+      // ||a_j||^2 after the update, downdated: a_j - alpha a_k is orthogonal to
+      // a_k, so its squared norm is ||a_j||^2 - |alpha|^2 ||a_k||^2.  Where that
+      // difference cancels more than kDowndateBits leading bits, it is recomputed
+      // from the column.  Every thread takes the same decision (the same
+      // inputs), so the barriers inside col_norm2 are uniform.
+      real s = P::sub(old, P::mul(P::add(P::mul(alr, alr), P::mul(ali, ali)), r2));
+      const bool recompute = !(P::lead(s) > ldexp(P::lead(old), -kDowndateBits));
+      if (recompute) {
         __syncthreads();                           // both parts of the column written
-        real s = col_norm2<P>(aj, Ap, N, part, r0, sh_acc, sh_r);
-        if (tid == 0) r_store<P>(nrm2, nc, j, s);
-        publish(&ready[j], tag);
+        s = col_norm2<P>(aj, Ap, N, part, r0, sh_acc, sh_r);
       }
+      if (tid == 0) {
+        r_store<P>(nrm2, nc, j, s);
+        if (j == k + 1) r_store<P>(ninv, nc, j, P::recip(s));
+      }
+      if (j == k + 1) publish(&ready[j], tag);
     }
   }
   // completion: block 0 waits for every block, then solves R dx = Q^H rhs
@@ -306,14 +358,107 @@ int ph_mgs_grid(ph_ctx *ctx, int L, int N, int n) {
   return g < 1 ? 1 : g;
 }
 
+namespace {
+
+// A diagonally dominant complex matrix in the leading limbs, for timing: the
+// time of a solve depends on the shape, not on the values (beyond their being
+// finite and the matrix nonsingular).
+__global__ void k_tune_fill(double *A, int N, long ldA, long Ap, long total) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    const long pl = e / Ap, r = e - pl * Ap;
+    const long j = r / ldA, i = r - j * ldA;
+    double v = 0.0;
+    if (pl < 2 && i < N) {
+      unsigned h = (unsigned)(i * 7919 + j * 104729 + pl * 31);
+      h ^= h >> 13;
+      h *= 0x5bd1e995u;
+      h ^= h >> 15;
+      v = ((double)(h & 0xffffu) / 65536.0 - 0.5) * 0.1;
+      if (pl == 0 && i == j) v += 4.0;
+    }
+    A[e] = v;
+  }
+}
+
+}  // namespace
+
+long ph_lda(int N);
+
+int ph_mgs_tune(ph_ctx *ctx, int L, int N, int n) {
+  const long long key = ((long long)L << 48) | ((long long)N << 24) | (long long)n;
+  auto it = ctx->mgs_variant.find(key);
+  if (it != ctx->mgs_variant.end()) return it->second;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(ctx->stream, &cs) != cudaSuccess ||
+      cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return 0;
+  }
+  const int C = ph_mgs_cluster_size(L, N, n);
+  cudaGetLastError();
+  int choice = 0;
+  if (C > 0) {
+    const int nc = n + 1;
+    const long ldA = ph_lda(N), Ap = (long)nc * ldA, total = 2L * L * Ap;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = ctx->tuneA.ensure(sizeof(double) * total);
+    if (e == cudaSuccess) e = ctx->tuneW.ensure(sizeof(double) * 2 * L * (size_t)nc * nc);
+    if (e == cudaSuccess) e = ctx->tuneN.ensure(sizeof(double) * 2 * L * (size_t)nc);
+    if (e == cudaSuccess) e = ctx->tuneF.ensure(sizeof(int) * (size_t)nc);
+    if (e == cudaSuccess) e = ctx->tuneX.ensure(sizeof(double) * 2 * L * (size_t)n);
+    if (e == cudaSuccess) e = ctx->tuneS.ensure(sizeof(PathState));
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    float best[2] = {1e30f, 1e30f};
+    PathState *st = ctx->tuneS.as<PathState>();
+    double *A = ctx->tuneA.as<double>();
+    for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
+      for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {   // rep 0 warms up
+        k_tune_fill<<<64, 256, 0, ctx->stream>>>(A, N, ldA, Ap, total);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemsetAsync(st, 0, sizeof(PathState), ctx->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(ctx->tuneF.p, 0, sizeof(int) * nc, ctx->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
+        if (e == cudaSuccess)
+          e = v == 0 ? (L == 2 ? launch_p<DD>(ctx->sm_count, ctx->stream, N, n, A, ldA,
+                                              ctx->tuneW.as<double>(), ctx->tuneN.as<double>(),
+                                              ctx->tuneX.as<double>(), ctx->tuneF.as<int>(), st,
+                                              nullptr, nullptr)
+                                 : launch_p<QD>(ctx->sm_count, ctx->stream, N, n, A, ldA,
+                                              ctx->tuneW.as<double>(), ctx->tuneN.as<double>(),
+                                              ctx->tuneX.as<double>(), ctx->tuneF.as<int>(), st,
+                                              nullptr, nullptr))
+                     : ph_mgs_cluster_launch(ctx->stream, C, L, N, n, A, ldA,
+                                             ctx->tuneW.as<double>(), ctx->tuneX.as<double>(), st,
+                                             nullptr, nullptr);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && rep > 0 && ms < best[v]) best[v] = ms;
+      }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e == cudaSuccess && best[1] < best[0]) choice = C;
+    if (e == cudaSuccess) ctx->mgs_times[key] = std::make_pair(best[0], best[1]);
+    cudaGetLastError();
+  }
+  ctx->mgs_variant[key] = choice;
+  return choice;
+}
+
 cudaError_t ph_mgs_launch(ph_ctx *ctx, int L, int N, int n, double *A, long ldA, double *dx,
                           PathState *st, const int *skip, double *resid) {
   const int nc = n + 1;
   cudaError_t e;
   if ((e = ctx->R.ensure(sizeof(double) * 2 * L * (size_t)nc * nc)) != cudaSuccess) return e;
-  if ((e = ctx->nrm2.ensure(sizeof(double) * L * (size_t)nc)) != cudaSuccess) return e;
+  if ((e = ctx->nrm2.ensure(sizeof(double) * 2 * L * (size_t)nc)) != cudaSuccess) return e;
   if ((e = ctx->flags.ensure(sizeof(int) * (size_t)nc)) != cudaSuccess) return e;
   double *W = ctx->R.as<double>(), *nrm2 = ctx->nrm2.as<double>();
+  const int C = ph_mgs_tune(ctx, L, N, n);
+  if (C > 0) return ph_mgs_cluster_launch(ctx->stream, C, L, N, n, A, ldA, W, dx, st, skip, resid);
   if (L == 2)
     return launch_p<DD>(ctx->sm_count, ctx->stream, N, n, A, ldA, W, nrm2, dx,
                         ctx->flags.as<int>(), st, skip, resid);
@@ -332,4 +477,19 @@ cudaError_t ph_mgs_launch_buffers(int sm_count, cudaStream_t stream, int L, int 
   if (L == 2)
     return launch_p<DD>(sm_count, stream, N, n, A, ldA, W, nrm2, dx, ready, st, nullptr, resid);
   return launch_p<QD>(sm_count, stream, N, n, A, ldA, W, nrm2, dx, ready, st, nullptr, resid);
+}
+
+extern "C" ph_status ph_mgs_variant(ph_ctx *ctx, ph_prec prec, int N, int n, int *cluster,
+                                    double *ms_grid, double *ms_cluster) {
+  if (!ctx) return PH_EINVAL;
+  const int L = (int)prec;
+  if ((L != 2 && L != 4) || n < 1 || N < n || !cluster)
+    return ph_fail(ctx, PH_EINVAL, "ph_mgs_variant: invalid argument");
+  cudaSetDevice(ctx->device);
+  *cluster = ph_mgs_tune(ctx, L, N, n);
+  const long long key = ((long long)L << 48) | ((long long)N << 24) | (long long)n;
+  auto it = ctx->mgs_times.find(key);
+  if (ms_grid) *ms_grid = it != ctx->mgs_times.end() ? it->second.first : -1.0;
+  if (ms_cluster) *ms_cluster = it != ctx->mgs_times.end() ? it->second.second : -1.0;
+  return PH_OK;
 }

@@ -55,7 +55,7 @@ extern "C" ph_status ph_mgs_solve_static(int device, void *cuda_stream, ph_prec 
   const size_t o_A = o_st + align256(sizeof(PathState));
   const size_t o_W = o_A + align256(sizeof(double) * 2 * L * (size_t)Ap);
   const size_t o_n = o_W + align256(sizeof(double) * 2 * L * (size_t)nc * nc);
-  const size_t o_i = o_n + align256(sizeof(double) * L * (size_t)nc);
+  const size_t o_i = o_n + align256(sizeof(double) * 2 * L * (size_t)nc);
   const size_t o_x = o_i + align256(sizeof(int) * (size_t)nc);
   const size_t o_r = o_x + align256(sizeof(double) * 2 * L * (size_t)n);
   const size_t need = o_r + align256(sizeof(double));

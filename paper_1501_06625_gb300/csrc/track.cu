@@ -338,6 +338,7 @@ static ph_status build_graph(ph_ctx *ctx, TrackCache *c, const ph_system *f, con
                              double *hist, double *xw, double *A, long ldA, double *dx,
                              ph_step_record *log, int log_cap) {
   drop_graph(c->tg);
+  ph_mgs_tune(ctx, f->L, f->N, f->n);                // measured now: the capture cannot
   if (!c->cap) PH_CUDA(ctx, cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
   TrackGraph &tg = c->tg;
   PH_CUDA(ctx, cudaGraphCreate(&tg.graph, 0));
@@ -437,7 +438,7 @@ extern "C" ph_status ph_track_path(ph_ctx *ctx, const ph_system *f, const ph_sys
     PH_CUDA(ctx, ctx->spow.ensure(sizeof(double) * 4 * L * (size_t)n));
     PH_CUDA(ctx, ctx->slots.ensure(sizeof(double) * 2 * L * (size_t)(fs + gs + 1)));
     PH_CUDA(ctx, ctx->R.ensure(sizeof(double) * 2 * L * (size_t)(n + 1) * (n + 1)));
-    PH_CUDA(ctx, ctx->nrm2.ensure(sizeof(double) * L * (size_t)(n + 1)));
+    PH_CUDA(ctx, ctx->nrm2.ensure(sizeof(double) * 2 * L * (size_t)(n + 1)));
     PH_CUDA(ctx, ctx->irkk.ensure(sizeof(double) * L * (size_t)n));
     PH_CUDA(ctx, ctx->flags.ensure(sizeof(int) * (size_t)(n + 1)));
   }

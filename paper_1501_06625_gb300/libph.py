@@ -63,7 +63,7 @@ EXPORTS = ["ph_init", "ph_destroy", "ph_last_error", "ph_system_load", "ph_syste
            "ph_ctrl_report", "ph_version", "ph_profile_newton", "ph_fp64_peak",
            "ph_mgs_solve_static", "ph_track_paths", "ph_server_create", "ph_server_submit",
            "ph_server_poll", "ph_server_wait", "ph_server_info", "ph_server_destroy",
-           "ph_server_job_bytes"]
+           "ph_server_job_bytes", "ph_mgs_variant"]
 
 
 class PhError(RuntimeError):
@@ -103,6 +103,8 @@ def lib():
             L.ph_ctrl_report.restype = None
             L.ph_version.restype = C.c_char_p
             L.ph_profile_newton.argtypes = [vp, vp, vp, vp, C.c_int, vp, vp, C.c_int, dp]
+            L.ph_mgs_variant.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int),
+                                         C.POINTER(C.c_double), C.POINTER(C.c_double)]
             L.ph_fp64_peak.argtypes = [vp, C.c_double, dp]
             L.ph_server_create.argtypes = [vp, C.POINTER(ServerConfig), C.POINTER(vp)]
             L.ph_server_submit.argtypes = [vp, vp, vp, vp, vp, C.POINTER(TrackParams),
@@ -320,6 +322,14 @@ def ph_profile_newton(ctx, f, g, gamma, k, t, x, reps: int = 10):
     out = (C.c_double * 4)()
     _check(ctx, lib().ph_profile_newton(ctx, f, g, _ptr(gamma), k, _ptr(t), _ptr(x), reps, out))
     return list(out)
+
+
+def ph_mgs_variant(ctx, prec: int, N: int, n: int):
+    """(cluster size or 0 for the grid kernel, ms grid, ms cluster) of the MGS solve."""
+    c = C.c_int(0)
+    g, k = C.c_double(0.0), C.c_double(0.0)
+    _check(ctx, lib().ph_mgs_variant(ctx, prec, N, n, C.byref(c), C.byref(g), C.byref(k)))
+    return c.value, g.value, k.value
 
 
 def ph_fp64_peak(ctx, ms_target: float = 50.0) -> float:
