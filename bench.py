@@ -48,10 +48,18 @@ UNIT = "corrector steps/s"
 
 # ---- algorithmic FP64 work per unit (instruction tallies of the library's
 #      primitives; every FP64 add, mul or fma is one operation)
+#   cmul: complex product (DD: fused parts, 19 each; QD: one fused sum of two
+#         products per part, 235 each); cadd: complex sum (2 real additions);
+#   cmul_int: product by the integer exponent 1, 2 (exact doubling), 3;
+#   mgs_unit: one (row, pivot, later column) of MGS, both parts of the dot-product
+#         term and of the update (DD: 2 x (24 + 27); QD: 2 x (275 + 275));
+#   mgs_sq: one row of a column norm (both parts); mgs_back: one back-substitution
+#         term (both parts of an update)
 OPS = {
-    2: dict(cmul=38, cadd=22, cmul_int=(0, 0, 4, 12), c_abs2=19),
-    4: dict(cmul=4 * 122 + 2 * 94, cadd=2 * 94, cmul_int=(0, 0, 8, 2 * 49 + 2 * 12),
-            c_abs2=2 * 122 + 94),
+    2: dict(cmul=38, cadd=22, cmul_int=(0, 0, 4, 12), c_abs2=19,
+            mgs_unit=102, mgs_sq=24, mgs_back=54),
+    4: dict(cmul=470, cadd=2 * 94, cmul_int=(0, 0, 8, 154), c_abs2=235,
+            mgs_unit=1100, mgs_sq=324, mgs_back=550),
 }
 
 
@@ -78,12 +86,11 @@ def sum_ops(spec, L: int) -> int:
 
 
 def mgs_ops(N: int, n: int, L: int) -> int:
-    """Per solve: dot (conj mul + add) and update (mul + sub) for every
-    (row, pivot, later column) of [J | rhs], the pivot norms, back substitution."""
+    """Per solve: the dot-product term and the update of every (row, pivot,
+    later column) of [J | rhs], the column norms, the back substitution."""
     o = OPS[L]
     pairs = n * (n + 1) // 2                          # (k, j) with k < j <= n
-    return pairs * N * 2 * (o["cmul"] + o["cadd"]) + n * N * (o["c_abs2"] + o["cadd"] // 2) \
-        + (n * (n - 1) // 2) * (o["cmul"] + o["cadd"])
+    return pairs * N * o["mgs_unit"] + (n + 1) * N * o["mgs_sq"] + (n * (n - 1) // 2) * o["mgs_back"]
 
 
 # ---- clocks during the timed region

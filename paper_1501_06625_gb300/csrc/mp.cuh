@@ -264,6 +264,82 @@ struct QD {
   }
 };
 
+// Sum of T quad-double products, plus an optional quad-double addend, rounded
+// once.  Every partial product x_i y_j of order i + j <= 2 is split exactly
+// (two_prod); order 3 (x_0 y_3 + x_1 y_2 + x_2 y_1 + x_3 y_0) is computed in
+// double; orders >= 4 are dropped (below 2^-212 |x y|).  The terms of each
+// order are summed with two_sum into a running sum of that order, each
+// rounding error passed on to the running sum of the next order; order 3 is
+// summed in double; one renormalisation at the end.  The error is of order
+// 2^-209 times the sum of |x_t y_t| (and |acc|), the bound all quad-double
+// results here are held to, at about 60% of the instructions of separate
+// products and additions each renormalised.  Signs are carried by the
+// operands (a negated limb costs nothing).
+template <int T, bool ACC>
+PHD qd qd_sum_prod(const qd (&x)[T], const qd (&y)[T], const qd &acc) {
+  double p00[T], q00[T], p01[T], q01[T], p10[T], q10[T], p02[T], q02[T], p11[T], q11[T];
+  double p20[T], q20[T], o3[T];
+#pragma unroll
+  for (int t = 0; t < T; ++t) {
+    two_prod(x[t].x[0], y[t].x[0], p00[t], q00[t]);
+    two_prod(x[t].x[0], y[t].x[1], p01[t], q01[t]);
+    two_prod(x[t].x[1], y[t].x[0], p10[t], q10[t]);
+    two_prod(x[t].x[0], y[t].x[2], p02[t], q02[t]);
+    two_prod(x[t].x[1], y[t].x[1], p11[t], q11[t]);
+    two_prod(x[t].x[2], y[t].x[0], p20[t], q20[t]);
+    double v = fmul(x[t].x[0], y[t].x[3]);
+    v = ffma(x[t].x[1], y[t].x[2], v);
+    v = ffma(x[t].x[2], y[t].x[1], v);
+    o3[t] = ffma(x[t].x[3], y[t].x[0], v);
+  }
+  // running sums of orders 0, 1, 2 (exact) and 3 (in double), each started
+  // with one of its terms
+  double s0 = p00[0], s1 = q00[0], s2 = q01[0], s3 = q02[0];
+  auto put2 = [&](double v) {
+    double e;
+    two_sum(s2, v, s2, e);
+    s3 = fadd(s3, e);
+  };
+  auto put1 = [&](double v) {
+    double e;
+    two_sum(s1, v, s1, e);
+    put2(e);
+  };
+  auto put0 = [&](double v) {
+    double e;
+    two_sum(s0, v, s0, e);
+    put1(e);
+  };
+#pragma unroll
+  for (int t = 1; t < T; ++t) put0(p00[t]);
+  if (ACC) put0(acc.x[0]);
+#pragma unroll
+  for (int t = 0; t < T; ++t) {
+    if (t > 0) put1(q00[t]);
+    put1(p01[t]);
+    put1(p10[t]);
+  }
+  if (ACC) put1(acc.x[1]);
+#pragma unroll
+  for (int t = 0; t < T; ++t) {
+    if (t > 0) put2(q01[t]);
+    put2(q10[t]);
+    put2(p02[t]);
+    put2(p11[t]);
+    put2(p20[t]);
+  }
+  if (ACC) put2(acc.x[2]);
+#pragma unroll
+  for (int t = 0; t < T; ++t) {
+    if (t > 0) s3 = fadd(s3, q02[t]);
+    s3 = fadd(s3, fadd(fadd(q11[t], q20[t]), o3[t]));
+  }
+  if (ACC) s3 = fadd(s3, acc.x[3]);
+  double c4 = 0.0;
+  qd_renorm(s0, s1, s2, s3, c4);
+  return {{s0, s1, s2, s3}};
+}
+
 // ---------------------------------------------------------------- complex
 // ---------------------------------------------------------------- one-limb types
 // IEEE double and single precision, with the same interface as DD and QD, for
@@ -400,6 +476,33 @@ template <class P> struct cops1 {
 };
 template <> struct cops<F64> : cops1<F64> {};
 template <> struct cops<F32> : cops1<F32> {};
+
+// QD: each part of a product (and of a product added to an addend) is one
+// fused sum of two products (qd_sum_prod).
+template <> struct cops<QD> {
+  PHD static cx<QD> mul(const cx<QD> &a, const cx<QD> &b) {
+    const qd z = QD::zero();
+    const qd xr[2] = {a.re, QD::neg(a.im)}, yr[2] = {b.re, b.im};
+    const qd xi[2] = {a.re, a.im}, yi[2] = {b.im, b.re};
+    return {qd_sum_prod<2, false>(xr, yr, z), qd_sum_prod<2, false>(xi, yi, z)};
+  }
+  PHD static cx<QD> mac(const cx<QD> &acc, const cx<QD> &a, const cx<QD> &b) {
+    const qd xr[2] = {a.re, QD::neg(a.im)}, yr[2] = {b.re, b.im};
+    const qd xi[2] = {a.re, a.im}, yi[2] = {b.im, b.re};
+    return {qd_sum_prod<2, true>(xr, yr, acc.re), qd_sum_prod<2, true>(xi, yi, acc.im)};
+  }
+  // conj(a) b
+  PHD static cx<QD> conj_mul(const cx<QD> &a, const cx<QD> &b) {
+    const qd z = QD::zero();
+    const qd xr[2] = {a.re, a.im}, yr[2] = {b.re, b.im};
+    const qd xi[2] = {a.re, QD::neg(a.im)}, yi[2] = {b.im, b.re};
+    return {qd_sum_prod<2, false>(xr, yr, z), qd_sum_prod<2, false>(xi, yi, z)};
+  }
+  PHD static qd abs2(const cx<QD> &a) {
+    const qd x[2] = {a.re, a.im};
+    return qd_sum_prod<2, false>(x, x, QD::zero());
+  }
+};
 
 template <class P> PHD cx<P> c_mul(const cx<P> &a, const cx<P> &b) { return cops<P>::mul(a, b); }
 template <class P> PHD cx<P> c_conj_mul(const cx<P> &a, const cx<P> &b) { return cops<P>::conj_mul(a, b); }

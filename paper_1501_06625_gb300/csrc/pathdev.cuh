@@ -218,6 +218,35 @@ template <class P> struct Part1 {
 template <> struct Part<F64> : Part1<F64> {};
 template <> struct Part<F32> : Part1<F32> {};
 
+// quad-double: every dot-product term and update is one fused sum of
+// products with the accumulator as addend (qd_sum_prod)
+template <> struct Part<QD> {
+  typedef qd real;
+  struct acc { qd v; };
+  PHD static acc zero() { return {QD::zero()}; }
+  PHD static void dot2(acc &a, const qd &x1, const qd &y1, const qd &x2, const qd &y2, double sg) {
+    const qd x[2] = {x1, sg < 0 ? QD::neg(x2) : x2}, y[2] = {y1, y2};
+    a.v = qd_sum_prod<2, true>(x, y, a.v);
+  }
+  PHD static void sq(acc &a, const qd &v) {
+    const qd x[1] = {v};
+    a.v = qd_sum_prod<1, true>(x, x, a.v);
+  }
+  PHD static acc combine(const acc &a, const acc &b) { return {QD::add(a.v, b.v)}; }
+  PHD static acc shfl(const acc &a, int m) {
+    acc z;
+#pragma unroll
+    for (int l = 0; l < 4; ++l) z.v.x[l] = __shfl_xor_sync(0xffffffffu, a.v.x[l], m);
+    return z;
+  }
+  PHD static qd value(const acc &a) { return a.v; }
+  // a - ar b + sg ai c
+  PHD static qd upd(const qd &a, const qd &ar, const qd &b, const qd &ai, const qd &c, double sg) {
+    const qd x[2] = {QD::neg(ar), sg < 0 ? QD::neg(ai) : ai}, y[2] = {b, c};
+    return qd_sum_prod<2, true>(x, y, a);
+  }
+};
+
 // double-double: Dot2-style unnormalised (s, c) accumulation
 template <> struct Part<DD> {
   typedef dd real;
