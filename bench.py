@@ -455,6 +455,20 @@ def serve_leg(libph, synth, ctx, nreq, seed, lin=0, seq_rate=None):
             "kernel_launches": info["kernel_launches"]}
 
 
+def combine_ranks(dist, torch, tot_ms: float, iters: int, device):
+    """Whole-job figures of a replicas run: the slowest rank's timed ms and the
+    corrector steps of all ranks (each rank tracks its own path; the only
+    collectives are these two reductions).  Without a process group, the
+    rank's own figures."""
+    if dist is None:
+        return tot_ms, float(iters)
+    t = torch.tensor([tot_ms, float(iters)], dtype=torch.float64, device=device)
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(t[1])
+
+
 def summarize(ms, stats):
     iters = sum(s["newton_iters"] for s in stats)
     pcs = sum(s["steps"] for s in stats)
@@ -542,14 +556,7 @@ def main():
     s = summarize(ms, stats)
     iters = sum(x["newton_iters"] for x in stats)
     tot_ms = sum(ms)
-    if dist:
-        t = torch.tensor([tot_ms, float(iters), float(len(ms))], dtype=torch.float64, device=dev)
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        tot_ms_max, iters_all = float(tmax[0]), float(t[1])
-    else:
-        tot_ms_max, iters_all = tot_ms, float(iters)
+    tot_ms_max, iters_all = combine_ranks(dist, torch, tot_ms, iters, dev)
     value = iters_all / (tot_ms_max / 1e3)
 
     # QD leg (same path, quad double)
