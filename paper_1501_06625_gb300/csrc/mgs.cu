@@ -164,6 +164,7 @@ __global__ void __launch_bounds__(kThreads) k_mgs(int N, int n, double *__restri
   typedef Part<P> PO;
   __shared__ typename PO::acc sh_acc[4];
   __shared__ real sh_r[2];
+  __shared__ int sh_rec;
   extern __shared__ double s_y[];                // back substitution: [L][2][n]
   const int nc = n + 1;
   const long Ap = (long)nc * ldA, Wp = (long)nc * nc;
@@ -205,6 +206,13 @@ __global__ void __launch_bounds__(kThreads) k_mgs(int N, int n, double *__restri
         ck_i[q] = load_part_cg<P>(ak, Ap, 1, i);
       }
     }
+    // warp 1 also updates warp 0's rows of the next pivot's column (below):
+    // their first pivot row
+    real c0_r = P::zero(), c0_i = P::zero();
+    if (w == 1 && lane < N) {
+      c0_r = load_part_cg<P>(ak, Ap, 0, lane);
+      c0_i = load_part_cg<P>(ak, Ap, 1, lane);
+    }
     for (int j = k + 1 + (((b - (k + 1)) % G) + G) % G; j <= n; j += G) {
       double *aj = A + (long)j * ldA;
       // ||a_j||^2 before this update, read before the barriers of the reduction
@@ -238,40 +246,65 @@ __global__ void __launch_bounds__(kThreads) k_mgs(int N, int n, double *__restri
           W[(2 * l + 1) * Wp + (long)j * nc + k] = P::limb(ali, l);
         }
       }
-      // a_j -= alpha a_k:  re: ajr - alr akr + ali aki;  im: aji - alr aki - ali akr
+      // The norm of a_j after the update follows from alpha alone: a_j - alpha
+      // a_k is orthogonal to a_k, so ||a_j||^2 - |alpha|^2 ||a_k||^2.  Where the
+      // difference cancels more than kDowndateBits leading bits, the norm is
+      // recomputed from the updated column; that decision reaches every thread
+      // through shared memory.  For the next pivot's column (on the critical
+      // chain) warp 0 computes the norm and its inverse while the other warps
+      // update the column, warp 1 taking warp 0's rows of the real part too; for
+      // other columns every warp updates its own rows and warp 0 then downdates.
+      const bool crit = j == k + 1;
+      if (!(crit && w == 0)) {
+        // a_j -= alpha a_k:  re: ajr - alr akr + ali aki;  im: aji - alr aki - ali akr
 #pragma unroll
-      for (int q = 0; q < kRowCache; ++q) {
-        const int i = r0 + 64 * q;
-        if (i < N) {
+        for (int q = 0; q < kRowCache; ++q) {
+          const int i = r0 + 64 * q;
+          if (i < N) {
+            if (part == 0)
+              store_part<P>(aj, Ap, 0, i,
+                            PO::upd(load_part<P>(aj, Ap, 0, i), alr, ck_r[q], ali, ck_i[q], 1.0));
+            else
+              store_part<P>(aj, Ap, 1, i,
+                            PO::upd(load_part<P>(aj, Ap, 1, i), alr, ck_i[q], ali, ck_r[q], -1.0));
+          }
+        }
+        for (int i = r0 + 64 * kRowCache; i < N; i += 64) {
+          real akr = load_part_cg<P>(ak, Ap, 0, i), aki = load_part_cg<P>(ak, Ap, 1, i);
           if (part == 0)
-            store_part<P>(aj, Ap, 0, i,
-                          PO::upd(load_part<P>(aj, Ap, 0, i), alr, ck_r[q], ali, ck_i[q], 1.0));
+            store_part<P>(aj, Ap, 0, i, PO::upd(load_part<P>(aj, Ap, 0, i), alr, akr, ali, aki, 1.0));
           else
-            store_part<P>(aj, Ap, 1, i,
-                          PO::upd(load_part<P>(aj, Ap, 1, i), alr, ck_i[q], ali, ck_r[q], -1.0));
+            store_part<P>(aj, Ap, 1, i, PO::upd(load_part<P>(aj, Ap, 1, i), alr, aki, ali, akr, -1.0));
+        }
+        if (crit && w == 1) {                      // warp 0's rows of the real part
+          for (int i = lane; i < N; i += 64) {
+            real akr = c0_r, aki = c0_i;
+            if (i != lane) {
+              akr = load_part_cg<P>(ak, Ap, 0, i);
+              aki = load_part_cg<P>(ak, Ap, 1, i);
+            }
+            store_part<P>(aj, Ap, 0, i, PO::upd(load_part<P>(aj, Ap, 0, i), alr, akr, ali, aki, 1.0));
+          }
         }
       }
-      for (int i = r0 + 64 * kRowCache; i < N; i += 64) {
-        real akr = load_part_cg<P>(ak, Ap, 0, i), aki = load_part_cg<P>(ak, Ap, 1, i);
-        if (part == 0)
-          store_part<P>(aj, Ap, 0, i, PO::upd(load_part<P>(aj, Ap, 0, i), alr, akr, ali, aki, 1.0));
-        else
-          store_part<P>(aj, Ap, 1, i, PO::upd(load_part<P>(aj, Ap, 1, i), alr, aki, ali, akr, -1.0));
+      if (w == 0) {
+        const real s = P::sub(old, P::mul(P::add(P::mul(alr, alr), P::mul(ali, ali)), r2));
+        const bool rec = !(P::lead(s) > ldexp(P::lead(old), -kDowndateBits));
+        if (lane == 0) {
+          sh_rec = rec;
+          if (!rec) {
+            r_store<P>(nrm2, nc, j, s);
+            if (crit) r_store<P>(ninv, nc, j, P::recip(s));
+          }
+        }
       }
-      // ||a_j||^2 after the update, downdated: a_j - alpha a_k is orthogonal to
-      // a_k, so its squared norm is ||a_j||^2 - |alpha|^2 ||a_k||^2.  Where that
-      // difference cancels more than kDowndateBits leading bits, it is recomputed
-      // from the column.  Every thread takes the same decision (the same
-      // inputs), so the barriers inside col_norm2 are uniform.
-      real s = P::sub(old, P::mul(P::add(P::mul(alr, alr), P::mul(ali, ali)), r2));
-      const bool recompute = !(P::lead(s) > ldexp(P::lead(old), -kDowndateBits));
-      if (recompute) {
-        __syncthreads();                           // both parts of the column written
-        s = col_norm2<P>(aj, Ap, N, part, r0, sh_acc, sh_r);
-      }
-      if (tid == 0) {
-        r_store<P>(nrm2, nc, j, s);
-        if (j == k + 1) r_store<P>(ninv, nc, j, P::recip(s));
+      __syncthreads();
+      if (sh_rec) {                                // the same value in every thread
+        const real s = col_norm2<P>(aj, Ap, N, part, r0, sh_acc, sh_r);
+        if (tid == 0) {
+          r_store<P>(nrm2, nc, j, s);
+          if (j == k + 1) r_store<P>(ninv, nc, j, P::recip(s));
+        }
       }
       if (j == k + 1) publish(&ready[j], tag);
     }
