@@ -48,14 +48,16 @@ UNIT = "corrector steps/s"
 
 # ---- algorithmic FP64 work per unit (instruction tallies of the library's
 #      primitives; every FP64 add, mul or fma is one operation)
-#   cmul: complex product (DD: fused parts, 19 each; QD: one fused sum of two
-#         products per part, 235 each); cadd: complex sum (2 real additions);
+#   cmul: complex product (D: a product and an FMA per part; DD: fused parts,
+#         19 each; QD: one fused sum of two products per part, 235 each);
+#         cadd: complex sum (2 real additions);
 #   cmul_int: product by the integer exponent 1, 2 (exact doubling), 3;
 #   mgs_unit: one (row, pivot, later column) of MGS, both parts of the dot-product
 #         term and of the update (DD: 2 x (24 + 27); QD: 2 x (275 + 275));
 #   mgs_sq: one row of a column norm (both parts); mgs_back: one back-substitution
 #         term (both parts of an update)
 OPS = {
+    1: dict(cmul=4, cadd=2, cmul_int=(0, 0, 2, 2), c_abs2=2, mgs_unit=8, mgs_sq=2, mgs_back=4),
     2: dict(cmul=38, cadd=22, cmul_int=(0, 0, 4, 12), c_abs2=19,
             mgs_unit=102, mgs_sq=24, mgs_back=54),
     4: dict(cmul=470, cadd=2 * 94, cmul_int=(0, 0, 8, 154), c_abs2=235,
@@ -333,11 +335,12 @@ def precision_leg(libph, synth, ctx, torch, dev, flush, seed, paths):
 # The paper's summation-kernel times on its K20C (Section 3.3, the tables for
 # cyclic 128- and 352-roots, ms per evaluation at the best number of threads
 # per sum): context, not targets.
-PAPER_CYCLIC_SUM_MS = {(128, 2): 0.53, (128, 4): 1.35, (352, 2): 9.69, (352, 4): 24.61}
+PAPER_CYCLIC_SUM_MS = {(128, 1): 0.34, (128, 2): 0.53, (128, 4): 1.35,
+                       (352, 1): 6.32, (352, 2): 9.69, (352, 4): 24.61}
 
 
 def cyclic_leg(libph, synth, ctx, torch, dev, peak):
-    """Cyclic n-roots (Section 4.2, Eq. (8)), n = 128 and 352, in DD and QD:
+    """Cyclic n-roots (Section 4.2, Eq. (8)), n = 128 and 352, in D, DD and QD:
     one corrector iteration's kernels at a random point of the unit torus
     (t = 0.5, total-degree homotopy), event-timed on the library's stream: ms per
     evaluation of h and its Jacobian (power table + monomial AD + summation), of
@@ -348,7 +351,7 @@ def cyclic_leg(libph, synth, ctx, torch, dev, peak):
         spec = synth.cyclic_system(n)
         rng = np.random.default_rng(n)
         z = np.exp(2j * np.pi * rng.random(n))
-        for L in (2, 4):
+        for L in (1, 2, 4):
             f = ctx.load(spec, L)
             xs = np.zeros((L, 2, n))
             xs[0, 0], xs[0, 1] = z.real, z.imag
@@ -367,7 +370,7 @@ def cyclic_leg(libph, synth, ctx, torch, dev, peak):
                  "summation_ms": kms[2],
                  "paper_k20c_summation_ms": PAPER_CYCLIC_SUM_MS[(n, L)],
                  "summation_vs_paper_k20c": PAPER_CYCLIC_SUM_MS[(n, L)] / kms[2]}
-            out[f"cyclic{n}_{'dd' if L == 2 else 'qd'}"] = r
+            out[f"cyclic{n}_{ {1: 'd', 2: 'dd', 4: 'qd'}[L] }"] = r
             ctx.free(f)
     return out
 

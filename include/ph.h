@@ -31,7 +31,7 @@
 extern "C" {
 #endif
 
-typedef enum { PH_DD = 2, PH_QD = 4 } ph_prec;     /* value = limbs per real */
+typedef enum { PH_D = 1, PH_DD = 2, PH_QD = 4 } ph_prec;     /* value = limbs per real */
 
 typedef enum {
   PH_OK = 0,

@@ -20,7 +20,7 @@
 
 int orc_mgs_solve(int L, int N, int n, const double *J, const double *rhs, double *dx,
                   double *Q, double *R, double *resid_norm) {
-  if ((L != 2 && L != 4) || n < 1 || N < n) return ORC_EINVAL;
+  if ((L != 1 && L != 2 && L != 4) || n < 1 || N < n) return ORC_EINVAL;
   int nc = n + 1;
   orc_cplx *A = malloc(sizeof(orc_cplx) * (size_t)N * nc);
   orc_cplx *Rm = calloc((size_t)nc * nc, sizeof(orc_cplx));

@@ -171,6 +171,9 @@ orc_real orc_r_div(int L, orc_real a, orc_real b) {
    each step doubles the number of correct bits (53, 106, 212, 424). */
 orc_real orc_r_sqrt(int L, orc_real a) {
   if (a.v[0] <= 0.0) return orc_r_from(0.0);
+  /* one limb: IEEE 754 requires sqrt correctly rounded, which is the exact
+     root rounded once; Newton steps in rounded doubles could move it */
+  if (L == 1) return orc_r_from(sqrt(a.v[0]));
   orc_real s = orc_r_from(sqrt(a.v[0]));
   for (int it = 0; it < 3; it++) {
     orc_real res = orc_r_sub(L, a, orc_r_mul(L, s, s));
@@ -271,7 +274,7 @@ void orc_c_store(int L, double *v, long stride, long i, orc_cplx z) {
    complex ops on [L][2][count]:   0 add, 1 sub, 2 mul, 3 conj_mul, 4 abs2
    (abs2 writes a real [L][count]). */
 int orc_vec_real(int op, int L, int count, const double *x, const double *y, double *z) {
-  if (L != 2 && L != 4) return ORC_EINVAL;
+  if (L != 1 && L != 2 && L != 4) return ORC_EINVAL;
   for (int i = 0; i < count; i++) {
     orc_real a, b, c;
     memset(&a, 0, sizeof a);
@@ -297,7 +300,7 @@ int orc_vec_real(int op, int L, int count, const double *x, const double *y, dou
 }
 
 int orc_vec_cplx(int op, int L, int count, const double *x, const double *y, double *z) {
-  if (L != 2 && L != 4) return ORC_EINVAL;
+  if (L != 1 && L != 2 && L != 4) return ORC_EINVAL;
   for (int i = 0; i < count; i++) {
     orc_cplx a = orc_c_load(L, x, count, i), b, c;
     if (y) b = orc_c_load(L, y, count, i); else memset(&b, 0, sizeof b);

@@ -35,7 +35,7 @@ int orc_system_new(int L, int N, int n, const int32_t *term_ptr, const int32_t *
                    const int32_t *var_idx, const int32_t *var_exp, const double *coeff,
                    orc_system **out) {
   *out = NULL;
-  if ((L != 2 && L != 4) || N < 1 || n < 1 || N < n) return ORC_EINVAL;
+  if ((L != 1 && L != 2 && L != 4) || N < 1 || n < 1 || N < n) return ORC_EINVAL;
   if (term_ptr[0] != 0) return ORC_EINVAL;
   for (int i = 0; i < N; i++) if (term_ptr[i + 1] < term_ptr[i]) return ORC_EINVAL;
   int M = term_ptr[N];

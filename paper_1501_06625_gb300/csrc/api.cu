@@ -155,7 +155,8 @@ long ph_lda(int N) { return ((long)N + 31) / 32 * 32; }
 extern "C" ph_status ph_mgs_solve(ph_ctx *ctx, ph_prec prec, int N, int n, const double *J,
                                   const double *rhs, double *dx, double *resid_norm) {
   if (!ctx) return PH_EINVAL;
-  if (prec != PH_DD && prec != PH_QD) return ph_fail(ctx, PH_EINVAL, "ph_mgs_solve: bad precision");
+  if (prec != PH_D && prec != PH_DD && prec != PH_QD)
+    return ph_fail(ctx, PH_EINVAL, "ph_mgs_solve: bad precision");
   if (n < 1 || N < n) return ph_fail(ctx, PH_EINVAL, "ph_mgs_solve: need N >= n >= 1");
   if ((long)N * (n + 1) > (1L << 28)) return ph_fail(ctx, PH_EINVAL, "ph_mgs_solve: matrix too large");
   if (!J || !rhs || !dx) return ph_fail(ctx, PH_EINVAL, "ph_mgs_solve: NULL array");

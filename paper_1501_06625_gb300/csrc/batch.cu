@@ -136,7 +136,8 @@ extern "C" ph_status ph_track_paths(ph_ctx *ctx, const ph_system *f, const ph_sy
   ph_job_fill_system(a.base, f, g);
   a.ws_stride = ph_job_ws_doubles(a.base);
   const size_t smem = job_smem_bytes(L, n);
-  const int bps = L == 2 ? blocks_per_sm<DD>(smem) : blocks_per_sm<QD>(smem);
+  const int bps = L == 1 ? blocks_per_sm<F64>(smem)
+                : L == 2 ? blocks_per_sm<DD>(smem) : blocks_per_sm<QD>(smem);
   int grid = ctx->sm_count * bps;
   if (grid > npaths) grid = npaths;
   PH_CUDA(ctx, ctx->bws.ensure(sizeof(double) * (size_t)a.ws_stride * grid));
@@ -177,7 +178,8 @@ extern "C" ph_status ph_track_paths(ph_ctx *ctx, const ph_system *f, const ph_sy
   a.log = dlog;
   a.next = ctx->bq.as<unsigned int>();
   a.ws = ctx->bws.as<double>();
-  PH_CUDA(ctx, L == 2 ? launch_paths<DD>(a, grid, smem, ctx->stream)
+  PH_CUDA(ctx, L == 1 ? launch_paths<F64>(a, grid, smem, ctx->stream)
+               : L == 2 ? launch_paths<DD>(a, grid, smem, ctx->stream)
                       : launch_paths<QD>(a, grid, smem, ctx->stream));
   if (host_out) PH_CUDA(ctx, cudaMemcpyAsync(x_out, dxo, xbytes, cudaMemcpyDeviceToHost, ctx->stream));
   if (stats)

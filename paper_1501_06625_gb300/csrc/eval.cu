@@ -253,6 +253,9 @@ cudaError_t ph_eval_launch_part(ph_ctx *ctx, const ph_system *f, const ph_system
                                 double *h, double *J, long ldJ, long Jplane, double *rhs,
                                 long rhs_plane, const int *skip, unsigned long long *res_bits,
                                 int parts) {
+  if (f->L == 1)
+    return eval_impl<F64>(ctx, f, g, gamma, k, t, x, h, J, ldJ, Jplane, rhs, rhs_plane, skip,
+                          res_bits, parts);
   if (f->L == 2)
     return eval_impl<DD>(ctx, f, g, gamma, k, t, x, h, J, ldJ, Jplane, rhs, rhs_plane, skip,
                          res_bits, parts);

@@ -417,6 +417,9 @@ __global__ void k_tune_fill(double *A, int N, long ldA, long Ap, long total) {
 }  // namespace
 
 long ph_lda(int N);
+cudaError_t ph_mgs_launch_buffers(int sm_count, cudaStream_t stream, int L, int N, int n,
+                                  double *A, long ldA, double *W, double *nrm2, double *dx,
+                                  int *ready, PathState *st, double *resid);
 
 int ph_mgs_tune(ph_ctx *ctx, int L, int N, int n) {
   const long long key = ((long long)L << 48) | ((long long)N << 24) | (long long)n;
@@ -454,14 +457,10 @@ int ph_mgs_tune(ph_ctx *ctx, int L, int N, int n) {
         if (e == cudaSuccess) e = cudaMemsetAsync(ctx->tuneF.p, 0, sizeof(int) * nc, ctx->stream);
         if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
         if (e == cudaSuccess)
-          e = v == 0 ? (L == 2 ? launch_p<DD>(ctx->sm_count, ctx->stream, N, n, A, ldA,
-                                              ctx->tuneW.as<double>(), ctx->tuneN.as<double>(),
-                                              ctx->tuneX.as<double>(), ctx->tuneF.as<int>(), st,
-                                              nullptr, nullptr)
-                                 : launch_p<QD>(ctx->sm_count, ctx->stream, N, n, A, ldA,
-                                              ctx->tuneW.as<double>(), ctx->tuneN.as<double>(),
-                                              ctx->tuneX.as<double>(), ctx->tuneF.as<int>(), st,
-                                              nullptr, nullptr))
+          e = v == 0 ? ph_mgs_launch_buffers(ctx->sm_count, ctx->stream, L, N, n, A, ldA,
+                                             ctx->tuneW.as<double>(), ctx->tuneN.as<double>(),
+                                             ctx->tuneX.as<double>(), ctx->tuneF.as<int>(), st,
+                                             nullptr)
                      : ph_mgs_cluster_launch(ctx->stream, C, L, N, n, A, ldA,
                                              ctx->tuneW.as<double>(), ctx->tuneX.as<double>(), st,
                                              nullptr, nullptr);
@@ -492,6 +491,9 @@ cudaError_t ph_mgs_launch(ph_ctx *ctx, int L, int N, int n, double *A, long ldA,
   double *W = ctx->R.as<double>(), *nrm2 = ctx->nrm2.as<double>();
   const int C = ph_mgs_tune(ctx, L, N, n);
   if (C > 0) return ph_mgs_cluster_launch(ctx->stream, C, L, N, n, A, ldA, W, dx, st, skip, resid);
+  if (L == 1)
+    return launch_p<F64>(ctx->sm_count, ctx->stream, N, n, A, ldA, W, nrm2, dx,
+                         ctx->flags.as<int>(), st, skip, resid);
   if (L == 2)
     return launch_p<DD>(ctx->sm_count, ctx->stream, N, n, A, ldA, W, nrm2, dx,
                         ctx->flags.as<int>(), st, skip, resid);
@@ -507,6 +509,8 @@ cudaError_t ph_mgs_launch(ph_ctx *ctx, int L, int N, int n, double *A, long ldA,
 cudaError_t ph_mgs_launch_buffers(int sm_count, cudaStream_t stream, int L, int N, int n,
                                   double *A, long ldA, double *W, double *nrm2, double *dx,
                                   int *ready, PathState *st, double *resid) {
+  if (L == 1)
+    return launch_p<F64>(sm_count, stream, N, n, A, ldA, W, nrm2, dx, ready, st, nullptr, resid);
   if (L == 2)
     return launch_p<DD>(sm_count, stream, N, n, A, ldA, W, nrm2, dx, ready, st, nullptr, resid);
   return launch_p<QD>(sm_count, stream, N, n, A, ldA, W, nrm2, dx, ready, st, nullptr, resid);
@@ -516,7 +520,7 @@ extern "C" ph_status ph_mgs_variant(ph_ctx *ctx, ph_prec prec, int N, int n, int
                                     double *ms_grid, double *ms_cluster) {
   if (!ctx) return PH_EINVAL;
   const int L = (int)prec;
-  if ((L != 2 && L != 4) || n < 1 || N < n || !cluster)
+  if ((L != 1 && L != 2 && L != 4) || n < 1 || N < n || !cluster)
     return ph_fail(ctx, PH_EINVAL, "ph_mgs_variant: invalid argument");
   cudaSetDevice(ctx->device);
   *cluster = ph_mgs_tune(ctx, L, N, n);

@@ -301,12 +301,13 @@ int max_cluster(int N, int n) {
 // The cluster size the cluster solve would use for this shape (16 or 8), or 0
 // when the matrix does not fit in the shared memory of a cluster.
 int ph_mgs_cluster_size(int L, int N, int n) {
-  return L == 2 ? max_cluster<DD>(N, n) : max_cluster<QD>(N, n);
+  return L == 1 ? max_cluster<F64>(N, n) : L == 2 ? max_cluster<DD>(N, n) : max_cluster<QD>(N, n);
 }
 
 cudaError_t ph_mgs_cluster_launch(cudaStream_t stream, int C, int L, int N, int n, const double *A,
                                   long ldA, double *W, double *dx, PathState *st, const int *skip,
                                   double *resid) {
+  if (L == 1) return launch_cl<F64>(stream, C, N, n, A, ldA, W, dx, st, skip, resid);
   if (L == 2) return launch_cl<DD>(stream, C, N, n, A, ldA, W, dx, st, skip, resid);
   return launch_cl<QD>(stream, C, N, n, A, ldA, W, dx, st, skip, resid);
 }

@@ -45,7 +45,7 @@ long ph_lda(int N);
 extern "C" ph_status ph_mgs_solve_static(int device, void *cuda_stream, ph_prec prec, int N,
                                          int n, const double *J, const double *rhs, double *dx,
                                          double *resid_norm) {
-  if (prec != PH_DD && prec != PH_QD) return PH_EINVAL;
+  if (prec != PH_D && prec != PH_DD && prec != PH_QD) return PH_EINVAL;
   if (n < 1 || N < n || !J || !rhs || !dx) return PH_EINVAL;
   if (device < 0 || device >= kMaxDevices) return PH_EINVAL;
   const int L = (int)prec, nc = n + 1;

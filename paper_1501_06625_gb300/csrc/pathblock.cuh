@@ -319,10 +319,10 @@ __device__ void track_job(const Job &a, double *smem) {
         real u = P::zero(), v = P::zero();
         two_sum(tn, -tq, s1, e1);
         P::set_limb(u, 0, s1);
-        P::set_limb(u, 1, e1);
+        if (P::L > 1) P::set_limb(u, 1, e1);
         two_sum(tj, -tq, s1, e1);
         P::set_limb(v, 0, s1);
-        P::set_limb(v, 1, e1);
+        if (P::L > 1) P::set_limb(v, 1, e1);
         num = P::mul(num, u);
         den = P::mul(den, v);
       }

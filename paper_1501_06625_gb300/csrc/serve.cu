@@ -163,7 +163,8 @@ __global__ void __launch_bounds__(kBT, 1) k_serve(Slot *slots, const int *queue,
     __syncthreads();
     j.x0 = x0d;
     j.gamma = gd;
-    if (j.L == 2) track_job<DD>(j, smem);
+    if (j.L == 1) track_job<F64>(j, smem);
+    else if (j.L == 2) track_job<DD>(j, smem);
     else track_job<QD>(j, smem);
     __threadfence_system();
     __syncthreads();

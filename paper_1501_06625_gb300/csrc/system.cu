@@ -43,7 +43,8 @@ extern "C" ph_status ph_system_load(ph_ctx *ctx, ph_prec prec, int N, int n,
   if (!ctx) return PH_EINVAL;
   if (!out) return ph_fail(ctx, PH_EINVAL, "ph_system_load: out is NULL");
   *out = nullptr;
-  if (prec != PH_DD && prec != PH_QD) return ph_fail(ctx, PH_EINVAL, "ph_system_load: prec must be PH_DD or PH_QD");
+  if (prec != PH_D && prec != PH_DD && prec != PH_QD)
+    return ph_fail(ctx, PH_EINVAL, "ph_system_load: prec must be PH_D, PH_DD or PH_QD");
   if (n < 1 || N < n) return ph_fail(ctx, PH_EINVAL, "ph_system_load: need N >= n >= 1");
   if ((long)n * N > (1L << 30)) return ph_fail(ctx, PH_EINVAL, "ph_system_load: system too large");
   if (!term_ptr || !var_ptr) return ph_fail(ctx, PH_EINVAL, "ph_system_load: NULL pointer array");

@@ -92,9 +92,9 @@ __global__ void k_predict(PathState *st, const double *__restrict__ hist, double
       real a, b;
       double s, e;
       two_sum(tn, -tl, s, e);          // t_new - t_l exactly
-      a = P::zero(); P::set_limb(a, 0, s); P::set_limb(a, 1, e);
+      a = P::zero(); P::set_limb(a, 0, s); if (P::L > 1) P::set_limb(a, 1, e);
       two_sum(tj, -tl, s, e);
-      b = P::zero(); P::set_limb(b, 0, s); P::set_limb(b, 1, e);
+      b = P::zero(); P::set_limb(b, 0, s); if (P::L > 1) P::set_limb(b, 1, e);
       num = P::mul(num, a);
       den = P::mul(den, b);
     }
@@ -310,7 +310,8 @@ static cudaError_t record_step(ph_ctx *ctx, cudaStream_t s, const ph_system *f,
   cudaError_t e = cudaSuccess;
   k_step_begin<<<1, 1, 0, s>>>(st, p, L);
   int pb = 128, pg = (n + pb - 1) / pb;
-  if (L == 2) k_predict<DD><<<pg, pb, 0, s>>>(st, hist, xw, n, p.pred_order);
+  if (L == 1) k_predict<F64><<<pg, pb, 0, s>>>(st, hist, xw, n, p.pred_order);
+  else if (L == 2) k_predict<DD><<<pg, pb, 0, s>>>(st, hist, xw, n, p.pred_order);
   else k_predict<QD><<<pg, pb, 0, s>>>(st, hist, xw, n, p.pred_order);
   for (int it = 0; it < p.max_newton && e == cudaSuccess; ++it) {
     e = ph_eval_launch(ctx, f, g, gamma, p.relax_k, st->t_dev, xw, nullptr, A, ldA, Ap,
@@ -319,13 +320,17 @@ static cudaError_t record_step(ph_ctx *ctx, cudaStream_t s, const ph_system *f,
     k_check_res<<<1, 1, 0, s>>>(st, p);
     e = ph_mgs_launch(ctx, L, N, n, A, ldA, dx, st, &st->skip_nt, nullptr);
     if (e != cudaSuccess) break;
-    if (L == 2) k_update<DD><<<(n + 127) / 128, 128, 0, s>>>(st, xw, dx, n, p.fixed_steps > 0);
+    if (L == 1) k_update<F64><<<(n + 127) / 128, 128, 0, s>>>(st, xw, dx, n, p.fixed_steps > 0);
+    else if (L == 2) k_update<DD><<<(n + 127) / 128, 128, 0, s>>>(st, xw, dx, n, p.fixed_steps > 0);
     else k_update<QD><<<(n + 127) / 128, 128, 0, s>>>(st, xw, dx, n, p.fixed_steps > 0);
     k_check_dx<<<1, 1, 0, s>>>(st, p);
   }
   if (e == cudaSuccess) {
     int eb = n < 256 ? 128 : 256;
-    if (L == 2) k_step_end<DD><<<1, eb, 0, s>>>(st, p, hist, xw, n, log, log_cap, cond, use_cond);
+    if (L == 1)
+      k_step_end<F64><<<1, eb, 0, s>>>(st, p, hist, xw, n, log, log_cap, cond, use_cond);
+    else if (L == 2)
+      k_step_end<DD><<<1, eb, 0, s>>>(st, p, hist, xw, n, log, log_cap, cond, use_cond);
     else k_step_end<QD><<<1, eb, 0, s>>>(st, p, hist, xw, n, log, log_cap, cond, use_cond);
     e = cudaGetLastError();
   }

@@ -19,7 +19,7 @@ from . import build as _build
 _LIB = None
 _LOCK = threading.Lock()
 
-PH_DD, PH_QD = 2, 4
+PH_D, PH_DD, PH_QD = 1, 2, 4
 (PH_OK, PH_EINVAL, PH_ENOMEM, PH_ECUDA, PH_DIVERGED, PH_MAXSTEPS, PH_STEPMIN, PH_NONFINITE,
  PH_TIMEOUT) = range(9)
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "DIVERGED", "MAXSTEPS", "STEPMIN",

@@ -114,12 +114,11 @@ class SystemSpec:
         out = np.zeros((L, 2, self.M))
         out[0, 0] = self.coeff.real
         out[0, 1] = self.coeff.imag
-        if self.coeff_lo is not None:
-            if L < 2 and np.any(self.coeff_lo != 0):
-                raise ValueError("coefficients need two limbs")
-            if L >= 2:
-                out[1, 0] = self.coeff_lo.real
-                out[1, 1] = self.coeff_lo.imag
+        # in one limb a two-limb coefficient is its leading limb, which is its
+        # correctly rounded double
+        if self.coeff_lo is not None and L >= 2:
+            out[1, 0] = self.coeff_lo.real
+            out[1, 1] = self.coeff_lo.imag
         return out
 
     def degrees(self) -> np.ndarray:
@@ -268,10 +267,11 @@ def default_params(L: int, **over) -> dict:
     method roughly squares the error per iteration, so from a predictor error
     e0 the residual test after m - 1 updates needs e0^(2^(m-1)) below the
     tolerance: 3 iterations reach 1e-24 (DD) from e0 ~ 1e-6, while 1e-52 (QD)
-    needs a fourth."""
-    p = dict(max_dt=0.1, min_dt=1e-12 if L == 2 else 1e-20,
-             tol_res=1e-24 if L == 2 else 1e-52, tol_dx=1e-24 if L == 2 else 1e-52,
-             max_res=1e8, max_x=1e8, max_steps=10000, max_newton=3 if L == 2 else 4,
+    needs a fourth.  Complex double (L = 1) stops at 1e-11, about 10^5 units
+    in the last place, where the rounding of a residual evaluation stays below."""
+    tol = {1: 1e-11, 2: 1e-24, 4: 1e-52}[L]
+    p = dict(max_dt=0.1, min_dt={1: 1e-8, 2: 1e-12, 4: 1e-20}[L], tol_res=tol, tol_dx=tol,
+             max_res=1e8, max_x=1e8, max_steps=10000, max_newton=4 if L == 4 else 3,
              pred_order=4, relax_k=1, fixed_steps=0, control=0, lin_prec=0, endgame_t=0.0,
              cond_f32=0.0)
     p.update(over)
@@ -308,6 +308,8 @@ class Workload:
 
 
 def _limbs(prec) -> int:
+    if prec in (1, "d", "D"):
+        return 1
     if prec in (2, "dd", "DD"):
         return 2
     if prec in (4, "qd", "QD"):

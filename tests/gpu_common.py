@@ -5,9 +5,9 @@ from __future__ import annotations
 
 import numpy as np
 
-TOL_EVAL = {2: 1e-28, 4: 1e-58}      # values and Jacobian, relative to sum |terms|
-TOL_END = {2: 1e-24, 4: 1e-52}       # path end points under the same schedule
-U = {2: 2.0 ** -104, 4: 2.0 ** -208}
+TOL_EVAL = {1: 1e-12, 2: 1e-28, 4: 1e-58}   # values and Jacobian, relative to sum |terms|
+TOL_END = {1: 1e-10, 2: 1e-24, 4: 1e-52}    # path end points under the same schedule
+U = {1: 2.0 ** -53, 2: 2.0 ** -104, 4: 2.0 ** -208}
 
 
 def limb_diff(a: np.ndarray, b: np.ndarray) -> np.ndarray:
