@@ -344,8 +344,10 @@ def cyclic_leg(libph, synth, ctx, torch, dev, peak):
     one corrector iteration's kernels at a random point of the unit torus
     (t = 0.5, total-degree homotopy), event-timed on the library's stream: ms per
     evaluation of h and its Jacobian (power table + monomial AD + summation), of
-    the summation alone (the paper's own timing of this system) and per MGS solve,
-    and the AD kernel's fraction of the measured FP64 rate."""
+    the summation alone (the paper's own timing of this system; also with each
+    number of lanes per output, 1 to 32, as the paper's tables vary its threads
+    per sum) and per MGS solve, and the AD kernel's fraction of the measured
+    FP64 rate."""
     out = {}
     for n in (128, 352):
         spec = synth.cyclic_system(n)
@@ -361,6 +363,7 @@ def cyclic_leg(libph, synth, ctx, torch, dev, peak):
             tl = torch.zeros(L, dtype=torch.float64, device=dev)
             tl[0] = 0.5
             kms = libph.ph_profile_newton(ctx.h, f, None, gam, 1, tl, x, 3 if n > 200 else 10)
+            lanes, by_lanes = libph.ph_sum_lanes(ctx.h, f)
             ev = kms[0] + kms[1] + kms[2]
             ad = ad_ops(spec, L)
             r = {"eval_ms": ev, "mgs_ms": kms[3], "kernel_ms": dict(zip(
@@ -368,6 +371,8 @@ def cyclic_leg(libph, synth, ctx, torch, dev, peak):
                  "monomials": int(spec.M),
                  "ad_frac_of_fp64_peak": ad / (kms[1] * 1e-3) / 1e9 / peak,
                  "summation_ms": kms[2],
+                 "summation_lanes": lanes,
+                 "summation_ms_by_lanes": dict(zip(["1", "2", "4", "8", "16", "32"], by_lanes)),
                  "paper_k20c_summation_ms": PAPER_CYCLIC_SUM_MS[(n, L)],
                  "summation_vs_paper_k20c": PAPER_CYCLIC_SUM_MS[(n, L)] / kms[2]}
             out[f"cyclic{n}_{ {1: 'd', 2: 'dd', 4: 'qd'}[L] }"] = r

@@ -287,6 +287,15 @@ ph_status ph_server_destroy(ph_server *srv);
 ph_status ph_mgs_variant(ph_ctx *ctx, ph_prec prec, int N, int n, int *cluster, double *ms_grid,
                          double *ms_cluster);
 
+/* The number of lanes (threads) per output of the summation kernel used for f
+ * (with g): *lanes = 1, 2, 4, 8, 16 or 32, chosen by timing each on the
+ * system's first evaluation (Section 3.3 of the paper times its summation with
+ * 1 to 32 threads per sum; here the choice is made per system and GPU).
+ * ms (optional, 6 doubles) receives the measured times for 1 .. 32 lanes, -1
+ * where not measured. */
+ph_status ph_sum_lanes(ph_ctx *ctx, const ph_system *f, const ph_system *g, int *lanes,
+                       double *ms);
+
 /* Host-side step-size controller of the path tracker, exported so it can be
  * checked without a GPU: the same code runs inside the device controller.
  * Fig. "Accelerated tracking of one single path". */

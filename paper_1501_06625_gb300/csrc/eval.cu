@@ -207,6 +207,97 @@ void ad_launch(const ph_system *sy, const double *ptab, int n, double *slots, lo
   }
 }
 
+// the summation kernel with G lanes per output
+template <class P, int G>
+void sum_launch_g(const ph_system *f, const ph_system *g, int N, int n, const double *fslots,
+                  long fs, const double *gslots, long gs, const double *spow, const double *scal,
+                  int homotopy, double *J, long ldJ, long Jplane, double *h, double *rhs,
+                  long rhs_plane, unsigned long long *res_bits, const int *skip, cudaStream_t st) {
+  const long threads = (long)f->nout * G;
+  k_sum<P, G><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
+      N, n, f->nout, f->out_ptr.as<int32_t>(), f->out_slot.as<int32_t>(), fslots, fs,
+      g ? g->out_ptr.as<int32_t>() : nullptr, g ? g->out_slot.as<int32_t>() : nullptr, gslots, gs,
+      spow, scal, homotopy, J, ldJ, Jplane, h, rhs, rhs_plane, res_bits, skip);
+}
+
+constexpr int kSumLanes[6] = {1, 2, 4, 8, 16, 32};
+
+template <class P>
+void sum_launch(int G, const ph_system *f, const ph_system *g, int N, int n, const double *fslots,
+                long fs, const double *gslots, long gs, const double *spow, const double *scal,
+                int homotopy, double *J, long ldJ, long Jplane, double *h, double *rhs,
+                long rhs_plane, unsigned long long *res_bits, const int *skip, cudaStream_t st) {
+#define PH_SUM_CASE(g_)                                                                          \
+  case g_:                                                                                       \
+    sum_launch_g<P, g_>(f, g, N, n, fslots, fs, gslots, gs, spow, scal, homotopy, J, ldJ,        \
+                        Jplane, h, rhs, rhs_plane, res_bits, skip, st);                           \
+    break;
+  switch (G) {
+    PH_SUM_CASE(1)
+    PH_SUM_CASE(2)
+    PH_SUM_CASE(4)
+    PH_SUM_CASE(16)
+    PH_SUM_CASE(32)
+    default:
+      sum_launch_g<P, 8>(f, g, N, n, fslots, fs, gslots, gs, spow, scal, homotopy, J, ldJ, Jplane,
+                         h, rhs, rhs_plane, res_bits, skip, st);
+  }
+#undef PH_SUM_CASE
+}
+
+// Times the summation with each lane count on the context's buffers (their
+// contents do not matter for the time; the outputs go to a scratch matrix) and
+// keeps the fastest on f.  Nothing is measured during a stream capture.
+template <class P>
+void tune_sum(ph_ctx *ctx, const ph_system *f, const ph_system *g) {
+  if (f->sum_lanes > 0) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(ctx->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return;
+  }
+  const int L = P::L, n = f->n, N = f->N;
+  const long fs = (long)(f->maxv + 1) * f->Mp;
+  const long gs = g ? (long)(g->maxv + 1) * g->Mp : 0;
+  cudaError_t e = ctx->slots.ensure(sizeof(double) * 2 * L * (size_t)(fs + gs + 1));
+  if (e == cudaSuccess) e = ctx->spow.ensure(sizeof(double) * 4 * L * (size_t)n);
+  if (e == cudaSuccess) e = ctx->scal.ensure(sizeof(double) * 3 * L);
+  const long ldJ = N, Jplane = (long)n * N;
+  if (e == cudaSuccess) e = ctx->tuneA.ensure(sizeof(double) * 2 * L * (size_t)Jplane);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  double *fslots = ctx->slots.as<double>(), *gslots = fslots + 2 * L * fs;
+  float best = 1e30f;
+  int choice = 8;
+  for (int v = 0; v < 6 && e == cudaSuccess; ++v) {
+    float tmin = 1e30f;
+    for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {     // rep 0 warms up
+      e = cudaEventRecord(e0, ctx->stream);
+      sum_launch<P>(kSumLanes[v], f, g, N, n, fslots, fs, gslots, gs, ctx->spow.as<double>(),
+                    ctx->scal.as<double>(), 1, ctx->tuneA.as<double>(), ldJ, Jplane, nullptr,
+                    nullptr, 0, nullptr, nullptr, ctx->stream);
+      if (e == cudaSuccess) e = cudaGetLastError();
+      if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.0f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e == cudaSuccess && rep > 0 && ms < tmin) tmin = ms;
+    }
+    if (e == cudaSuccess) {
+      f->sum_ms[v] = tmin;
+      if (tmin < best) {
+        best = tmin;
+        choice = kSumLanes[v];
+      }
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaGetLastError();
+  f->sum_lanes = e == cudaSuccess ? choice : 8;
+}
+
 template <class P>
 cudaError_t eval_impl(ph_ctx *ctx, const ph_system *f, const ph_system *g, const double *gamma,
                       int k, const double *t, const double *x, double *h, double *J, long ldJ,
@@ -236,13 +327,11 @@ cudaError_t eval_impl(ph_ctx *ctx, const ph_system *f, const ph_system *g, const
     if (f->M > 0) ad_launch<P>(f, ptab, n, fslots, fs, skip, st);
     if (g && g->M > 0) ad_launch<P>(g, ptab, n, gslots, gs, skip, st);
   }
-  constexpr int G = 8;
-  const long threads = (long)f->nout * G;
-  if (parts & 4)
-  k_sum<P, G><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
-      N, n, f->nout, f->out_ptr.as<int32_t>(), f->out_slot.as<int32_t>(), fslots, fs,
-      g ? g->out_ptr.as<int32_t>() : nullptr, g ? g->out_slot.as<int32_t>() : nullptr, gslots, gs,
-      spow, scal, gamma != nullptr, J, ldJ, Jplane, h, rhs, rhs_plane, res_bits, skip);
+  if (parts & 4) {
+    tune_sum<P>(ctx, f, g);
+    sum_launch<P>(f->sum_lanes > 0 ? f->sum_lanes : 8, f, g, N, n, fslots, fs, gslots, gs, spow,
+                  scal, gamma != nullptr, J, ldJ, Jplane, h, rhs, rhs_plane, res_bits, skip, st);
+  }
   return cudaGetLastError();
 }
 
@@ -261,6 +350,25 @@ cudaError_t ph_eval_launch_part(ph_ctx *ctx, const ph_system *f, const ph_system
                          res_bits, parts);
   return eval_impl<QD>(ctx, f, g, gamma, k, t, x, h, J, ldJ, Jplane, rhs, rhs_plane, skip,
                        res_bits, parts);
+}
+
+void ph_sum_tune(ph_ctx *ctx, const ph_system *f, const ph_system *g) {
+  if (f->L == 1) tune_sum<F64>(ctx, f, g);
+  else if (f->L == 2) tune_sum<DD>(ctx, f, g);
+  else tune_sum<QD>(ctx, f, g);
+}
+
+extern "C" ph_status ph_sum_lanes(ph_ctx *ctx, const ph_system *f, const ph_system *g, int *lanes,
+                                  double *ms) {
+  if (!ctx) return PH_EINVAL;
+  if (!f || f->ctx != ctx || !lanes || (g && (g->ctx != ctx || g->L != f->L || g->n != f->n)))
+    return ph_fail(ctx, PH_EINVAL, "ph_sum_lanes: invalid argument");
+  cudaSetDevice(ctx->device);
+  ph_sum_tune(ctx, f, g);
+  *lanes = f->sum_lanes > 0 ? f->sum_lanes : 8;
+  if (ms)
+    for (int v = 0; v < 6; ++v) ms[v] = f->sum_ms[v];
+  return PH_OK;
 }
 
 cudaError_t ph_eval_launch(ph_ctx *ctx, const ph_system *f, const ph_system *g,

@@ -90,6 +90,11 @@ struct ph_system {
   std::vector<Bucket> buckets;
   std::vector<int> h_deg;
   int max_deg = 0;
+  // lanes per output of the summation kernel (#Th of the paper's Section 3.3),
+  // chosen by timing on the first evaluation (0: not yet), and the times (ms)
+  // of 1, 2, 4, 8, 16 and 32 lanes
+  mutable int sum_lanes = 0;
+  mutable float sum_ms[6] = {-1, -1, -1, -1, -1, -1};
 };
 
 // ---- helpers (api.cu)
@@ -123,6 +128,10 @@ cudaError_t ph_eval_launch_part(ph_ctx *ctx, const ph_system *f, const ph_system
                                 double *h, double *J, long ldJ, long Jplane, double *rhs,
                                 long rhs_plane, const int *skip, unsigned long long *res_bits,
                                 int parts);
+
+// eval.cu: the summation kernel's lanes per output for f (and g), measured
+// on the first evaluation outside a stream capture (called before a capture).
+void ph_sum_tune(ph_ctx *ctx, const ph_system *f, const ph_system *g);
 
 // mgs.cu: least squares on the augmented matrix A = [J | rhs] held in
 //   A (plane stride (n+1)*ldA, leading dim ldA); dx [2L][n] out;

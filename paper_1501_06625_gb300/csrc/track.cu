@@ -344,6 +344,7 @@ static ph_status build_graph(ph_ctx *ctx, TrackCache *c, const ph_system *f, con
                              ph_step_record *log, int log_cap) {
   drop_graph(c->tg);
   ph_mgs_tune(ctx, f->L, f->N, f->n);                // measured now: the capture cannot
+  ph_sum_tune(ctx, f, g);
   if (!c->cap) PH_CUDA(ctx, cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
   TrackGraph &tg = c->tg;
   PH_CUDA(ctx, cudaGraphCreate(&tg.graph, 0));

@@ -63,7 +63,7 @@ EXPORTS = ["ph_init", "ph_destroy", "ph_last_error", "ph_system_load", "ph_syste
            "ph_ctrl_report", "ph_version", "ph_profile_newton", "ph_fp64_peak",
            "ph_mgs_solve_static", "ph_track_paths", "ph_server_create", "ph_server_submit",
            "ph_server_poll", "ph_server_wait", "ph_server_info", "ph_server_destroy",
-           "ph_server_job_bytes", "ph_mgs_variant"]
+           "ph_server_job_bytes", "ph_mgs_variant", "ph_sum_lanes"]
 
 
 class PhError(RuntimeError):
@@ -105,6 +105,7 @@ def lib():
             L.ph_profile_newton.argtypes = [vp, vp, vp, vp, C.c_int, vp, vp, C.c_int, dp]
             L.ph_mgs_variant.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int),
                                          C.POINTER(C.c_double), C.POINTER(C.c_double)]
+            L.ph_sum_lanes.argtypes = [vp, vp, vp, C.POINTER(C.c_int), dp]
             L.ph_fp64_peak.argtypes = [vp, C.c_double, dp]
             L.ph_server_create.argtypes = [vp, C.POINTER(ServerConfig), C.POINTER(vp)]
             L.ph_server_submit.argtypes = [vp, vp, vp, vp, vp, C.POINTER(TrackParams),
@@ -330,6 +331,14 @@ def ph_mgs_variant(ctx, prec: int, N: int, n: int):
     g, k = C.c_double(0.0), C.c_double(0.0)
     _check(ctx, lib().ph_mgs_variant(ctx, prec, N, n, C.byref(c), C.byref(g), C.byref(k)))
     return c.value, g.value, k.value
+
+
+def ph_sum_lanes(ctx, f, g=None):
+    """(lanes per output the summation uses, [ms for 1, 2, 4, 8, 16, 32 lanes])."""
+    lanes = C.c_int(0)
+    ms = (C.c_double * 6)()
+    _check(ctx, lib().ph_sum_lanes(ctx, f, g, C.byref(lanes), ms))
+    return lanes.value, list(ms)
 
 
 def ph_fp64_peak(ctx, ms_target: float = 50.0) -> float:

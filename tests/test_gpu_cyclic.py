@@ -87,3 +87,21 @@ def test_cyclic_root_of_unity(ctx, L):
     # each f_i is a sum of n products of unit modulus, rounded x_k: |f_i| is
     # the rounding of the inputs and of the sum, far below the tolerance
     assert mag.max() <= TOL_EVAL[L] * n, mag.max()
+
+
+@pytest.mark.parametrize("L", [1, 2, 4])
+def test_summation_lanes_tuned(ctx, L):
+    """The summation's lanes per output are chosen by timing 1 .. 32 lanes (the
+    paper's #Th); the choice is the fastest measured, and the evaluation with
+    it still matches the oracle."""
+    n = 16
+    spec = synth.cyclic_system(n)
+    f = ctx.load(spec, L)
+    x = soa_from_complex(synth.random_x(synth.Rng(5), n), L)
+    h, J = _eval(ctx, L, f, n, x, t=0.0)
+    lanes, ms = libph.ph_sum_lanes(ctx.h, f)
+    assert lanes in (1, 2, 4, 8, 16, 32)
+    assert all(m > 0 for m in ms)
+    assert ms[[1, 2, 4, 8, 16, 32].index(lanes)] == min(ms)
+    ho, Jo = oracle.eval_h(oracle.System(spec, L), x)
+    assert_eval_close(L, spec, x, h, J, ho, Jo)
