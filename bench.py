@@ -340,7 +340,7 @@ PAPER_CYCLIC_SUM_MS = {(128, 1): 0.34, (128, 2): 0.53, (128, 4): 1.35,
 
 
 def cyclic_leg(libph, synth, ctx, torch, dev, peak):
-    """Cyclic n-roots (Section 4.2, Eq. (8)), n = 128 and 352, in D, DD and QD:
+    """Cyclic n-roots (Section 4.2, Eq. (10)), n = 128 and 352, in D, DD and QD:
     one corrector iteration's kernels at a random point of the unit torus
     (t = 0.5, total-degree homotopy), event-timed on the library's stream: ms per
     evaluation of h and its Jacobian (power table + monomial AD + summation), of

@@ -59,8 +59,8 @@ ph_status ph_destroy(ph_ctx *ctx);
 const char *ph_last_error(ph_ctx *ctx);
 
 /* Loads a polynomial system of N polynomials in n variables, N >= n (Section
- * 2, input specification), given fully expanded (Section 3.1: "fully expanded
- * distributed symbolic representation"):
+ * 2, input specification), given fully expanded (Section 3.1: every polynomial
+ * as the list of its monomials and their coefficients):
  *   polynomial i owns terms term_ptr[i] .. term_ptr[i+1]-1   (term_ptr: N+1);
  *   term k owns the pairs var_ptr[k] .. var_ptr[k+1]-1        (var_ptr: M+1);
  *   pair p is variable var_idx[p] in [0, n) with exponent var_exp[p] >= 1;
@@ -103,8 +103,7 @@ ph_status ph_eval_jac(ph_ctx *ctx, const ph_system *f, const ph_system *g,
 ph_status ph_mgs_solve(ph_ctx *ctx, ph_prec prec, int N, int n, const double *J,
                        const double *rhs, double *dx, double *resid_norm);
 
-/* Path-tracking parameters (Section 2 and Fig. "Accelerated tracking of one
- * single path"; the paper leaves the values open). */
+/* Path-tracking parameters (Section 2 and Fig. 3; the paper leaves the values open). */
 typedef struct {
   double max_dt;      /* largest step size h_max, also the first step size      */
   double min_dt;      /* smallest step size h_min: halving below it ends the
@@ -191,8 +190,7 @@ typedef struct {
 
 /* Tracks one solution path of h(x,t) = gamma (1-t)^k g(x) + t^k f(x) from the
  * start solution x0 of g at t = 0 to t = 1 (Section 2, input-output
- * specification; Fig. "An accelerated Newton's method" and Fig. "Accelerated
- * tracking of one single path"):
+ * specification; Fig. 2 and Fig. 3):
  *   t := min(1, t + dt); predict x by extrapolation through the last accepted
  *   points (degree min(pred_order, #accepted - 1), Section 3.1); run Newton's
  *   method (fail if the residual grows, succeed if ||h|| < tol_res or
@@ -298,7 +296,7 @@ ph_status ph_sum_lanes(ph_ctx *ctx, const ph_system *f, const ph_system *g, int 
 
 /* Host-side step-size controller of the path tracker, exported so it can be
  * checked without a GPU: the same code runs inside the device controller.
- * Fig. "Accelerated tracking of one single path". */
+ * Fig. 3. */
 typedef struct {
   double t, dt;
   int32_t nsucc, nsteps, done, status;

@@ -1,7 +1,7 @@
 /*
  * mixed.c -- the oracle's mixed-precision corrector: the precision form of the
  * path tracker.  The paper's corrector works in double-double or quad-double
- * throughout (Section 3.1, Fig. "An accelerated Newton's method"); the
+ * throughout (Section 3.1, Fig. 2); the
  * precision form keeps only the residual and the accumulated update in that
  * working precision and solves the Newton system in IEEE double or single.
  * TEST INFRASTRUCTURE: see oracle.h.

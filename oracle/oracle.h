@@ -105,7 +105,7 @@ typedef struct {
   int32_t accepted, updates;
 } orc_record;
 
-/* step-size controller state (Fig. "Accelerated tracking of one single path") */
+/* step-size controller state (Fig. 3) */
 typedef struct {
   double t, dt;
   int32_t nsucc, nsteps, done, status;

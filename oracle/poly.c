@@ -4,8 +4,8 @@
  * with its Jacobian.  TEST INFRASTRUCTURE: see oracle.h.
  *
  * A system is given fully expanded, as a list of terms c * prod_j x_j^{a_j}
- * per polynomial (Section 3.1: "fully expanded distributed symbolic
- * representation").  Values and partial derivatives are computed by symbolic
+ * per polynomial (Section 3.1: every polynomial as its list of monomials with
+ * their coefficients).  Values and partial derivatives are computed by symbolic
  * differentiation,
  *   d/dx_j [c prod_l x_l^{a_l}] = (c a_j) x_j^{a_j - 1} prod_{l != j} x_l^{a_l},
  * each product evaluated by plain repeated multiplication, coefficient first,

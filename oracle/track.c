@@ -6,12 +6,12 @@
  *   by the polynomial of degree p through the last p+1 accepted points
  *   (t_j, x_i(t_j)); here in Newton's divided-difference form, evaluated by
  *   Horner's rule, in working precision.  p = min(pred_order, #accepted - 1).
- * Corrector (Fig. "An accelerated Newton's method"): at most max_newton
+ * Corrector (Fig. 2): at most max_newton
  *   iterations of: evaluate h and J; fail if ||h|| grew past the previous
  *   residual (the first bound is max_res); succeed if ||h|| < tol_res; solve
  *   J dx = -h; x := x + dx; succeed if ||dx|| < tol_dx.  Norms are max norms
  *   of |z| taken in double from the leading limbs (Section 3.1).
- * Step control (Fig. "Accelerated tracking of one single path"): t := min(1,
+ * Step control (Fig. 3): t := min(1,
  *   t + dt); predict; correct; on success keep the point, count it, and after
  *   more than two successes in a row double dt (capped at max_dt); on failure
  *   reset the count and halve dt.  Readings where the figure is silent: a

@@ -1,6 +1,6 @@
-// ctrl.h -- step-size control of the path tracker (Fig. "Accelerated tracking
-// of one single path"), compiled for both the host (exported as ph_ctrl_* so it
-// can be checked without a GPU) and the device controller kernel.
+// ctrl.h -- step-size control of the path tracker (Fig. 3), compiled for both
+// the host (exported as ph_ctrl_* so it can be checked without a GPU) and the
+// device controller kernel.
 //
 // t := min(1, t + dt) is tried; on success t advances, the success count grows
 // and, once more than two successes are in a row, dt doubles up to max_dt; on

@@ -34,12 +34,12 @@ struct DevBuf {
 // Device-side state of one tracked path and of its current corrector run.
 // Lives in device memory; the step kernels read and update it.
 struct PathState {
-  // step-size controller (Fig. "Accelerated tracking of one single path")
+  // step-size controller (Fig. 3)
   ph_ctrl_state ctrl;
   // the step being tried
   double t_new;
   int32_t hist_count, hist_head;
-  // corrector (Fig. "An accelerated Newton's method")
+  // corrector (Fig. 2)
   int32_t nt_done, nt_success, nt_iters, nt_updates;
   double last_res, res, dxn;
   unsigned long long res_bits, dx_bits, x_bits;

@@ -362,7 +362,7 @@ __device__ void track_job(const Job &a, double *smem) {
         }
         c_store<P>(x, n, i, acc);
       }
-      // corrector (Fig. "An accelerated Newton's method")
+      // corrector (Fig. 2)
       // One iteration beyond max_newton for a low-precision corrector whose
       // previous update was below sqrt(tol_dx): the working-precision corrector
       // would have squared that update below tol_dx and succeeded by now, while
@@ -534,7 +534,7 @@ __device__ void track_job(const Job &a, double *smem) {
       }
       break;
     }
-    // step control (Fig. "Accelerated tracking of one single path")
+    // step control (Fig. 3)
     if (tid == 0) {
       const int ok = s_ok;
       s_st.steps += 1;

@@ -1,8 +1,7 @@
 // track.cu -- ph_track_path: one solution path tracked entirely on the device.
 //
 // The paper keeps the step control on the host and copies the two norms of
-// each Newton iteration back (Section 3.1, Fig. "An accelerated Newton's
-// method", Fig. "Accelerated tracking of one single path").  On GB300 a host
+// each Newton iteration back (Section 3.1, Fig. 2, Fig. 3).  On GB300 a host
 // round trip costs more than a small step's kernels, so here the same
 // decisions run in one-thread kernels on the device and the whole path is a
 // single CUDA graph launch: a conditional WHILE node repeats the body

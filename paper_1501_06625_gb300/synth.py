@@ -232,7 +232,7 @@ def planted_system(rng: Rng, n: int, terms_per_poly: int, vars_per_term: int,
 
 
 def cyclic_system(n: int) -> SystemSpec:
-    """Cyclic n-roots (Section 4.2, Eq. (8)): f_i = sum_j prod_{k=j}^{j+i-1}
+    """Cyclic n-roots (Section 4.2, Eq. (10)): f_i = sum_j prod_{k=j}^{j+i-1}
     x_{k mod n} for i = 1..n-1, and f_n = x_0 x_1 ... x_{n-1} - 1.  Built with
     array operations: n = 352 has about 21.7 million (variable, exponent)
     pairs.  The variables of each term are listed in increasing order."""

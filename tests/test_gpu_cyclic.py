@@ -1,4 +1,4 @@
-"""GPU parity on the cyclic n-roots systems (Section 4.2, Eq. (8)).
+"""GPU parity on the cyclic n-roots systems (Section 4.2, Eq. (10)).
 
 * n = 8, 16, 24: values and Jacobians of f and of the homotopy against the
   oracle at random points, within 1e-28 (DD) / 1e-58 (QD) relative to the sum

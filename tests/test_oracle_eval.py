@@ -9,7 +9,7 @@ and its Jacobian (Section 2, Eq. (1)).
   evaluation to far below the DD/QD tolerances (relative to sum |terms|).
 * Central differences in QD on DD points pin the Jacobian against the values
   (both real and imaginary directions, which catches a conjugation).
-* Closed forms: cyclic n-roots (Section 4.2, Eq. (8)) at the all-ones point
+* Closed forms: cyclic n-roots (Section 4.2, Eq. (10)) at the all-ones point
   and at its root (1, w, w^2, ...), and the start system x_i^{d_i} - 1 at
   roots of unity.
 """

@@ -1,8 +1,7 @@
 """Pins of the oracle's predictor, Newton corrector and step-size control.
 
 * Step control: scripted success/failure sequences against traces derived by
-  hand from the path-tracking pseudocode (Fig. "Accelerated tracking of one
-  single path") with the readings in the oracle's header.
+  hand from the path-tracking pseudocode (Fig. 3) with the readings in the oracle's header.
 * Predictor: the extrapolation reproduces any polynomial of degree <= p
   through p+1 points, and for degree p+1 data misses by exactly the
   interpolation remainder c_{p+1} prod (t - t_j) (mpmath).
