@@ -1,6 +1,7 @@
-"""Shared helpers of the GPU parity tests (numpy only: the GPU machine has no
-mpmath).  Tolerances are relative to the sum of the magnitudes of the terms of
-each output, the measure the accuracy targets are stated in."""
+"""Shared helpers of the GPU parity tests (numpy only: they must run where
+mpmath is not installed).  Tolerances are relative to the sum of the
+magnitudes of the terms of each output, the measure the accuracy targets are
+stated in."""
 from __future__ import annotations
 
 import numpy as np
