@@ -332,6 +332,57 @@ def precision_leg(libph, synth, ctx, torch, dev, flush, seed, paths):
     return out
 
 
+def precision_path_leg(libph, synth, ctx, torch, dev, flush, seed):
+    """The precision form in the single-path tracker: one precision128 path
+    (n = 128, coefficient moduli over 12 decades per equation) over the same
+    segment of adaptive steps as the many-path comparison, plain (lin_prec 0,
+    every Newton system in DD/QD) against lin_prec 1 (Newton systems in
+    double, residual and update in DD/QD; in QD also with one Newton iteration
+    more).  Each run is timed with CUDA events around one ph_track_path call
+    after an untimed call that builds its step graph; the end points of the
+    two forms are compared (their corrector tolerances are the same)."""
+    out = {}
+    cases = [("dd", 6, 5, ((0, 0), (1, 0))), ("qd", 3, 6, ((0, 0), (1, 0), (1, 1)))]
+    stream = torch.cuda.current_stream(dev)
+    for prec, seg, mn, runs in cases:
+        wl = synth.precision128(seed, prec)[0]
+        f = ctx.load(wl.f, wl.L)
+        x0 = torch.tensor(batch_starts(wl, 1)[0], dtype=torch.float64, device=dev)
+        gam = torch.tensor(wl.gamma_soa(), dtype=torch.float64, device=dev)
+        row = {"segment_steps": seg, "max_dt": 1e-3, "max_newton": mn}
+        base = None
+        for lin, extra in runs:
+            params = dict(wl.params, max_steps=seg - 1, max_dt=1e-3, max_newton=mn + extra,
+                          lin_prec=lin)
+            xo = torch.empty_like(x0)
+            libph.ph_track_path(ctx.h, f, None, gam, x0, params, xo)      # builds the graph
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st, sd, _ = libph.ph_track_path(ctx.h, f, None, gam, x0, params, xo)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            r = {"status": int(st), "ms": ms, "accepted_steps": sd["accepted"],
+                 "newton_iters": sd["newton_iters"], "solves_f64": sd["solves_f64"],
+                 "escalated": sd["escalated"],
+                 "ms_per_accepted_step": ms / max(1, sd["accepted"])}
+            if lin:
+                r["cond_estimate"] = sd["cond"]
+            x = xo.cpu().numpy()
+            if base is None:
+                base, xb = r, x
+            else:
+                r["accepted_steps_vs_plain"] = (base["ms_per_accepted_step"]
+                                                / r["ms_per_accepted_step"])
+                d = np.abs((x[0, 0] - xb[0, 0]) + 1j * (x[0, 1] - xb[0, 1])).max()
+                r["end_point_diff_vs_plain"] = float(d)
+            row[f"lin{lin}" + (f"_newton+{extra}" if extra else "")] = r
+        out[f"precision128_{prec}_single_path"] = row
+    return out
+
+
 # The paper's summation-kernel times on its K20C (Section 3.3, the tables for
 # cyclic 128- and 352-roots, ms per evaluation at the best number of threads
 # per sum): context, not targets.
@@ -623,6 +674,7 @@ def main():
     if args.precision_paths > 0 and rank == 0:
         precision = precision_leg(libph, synth, ctx, torch, dev, flush, args.seed,
                                   args.precision_paths)
+        precision.update(precision_path_leg(libph, synth, ctx, torch, dev, flush, args.seed))
 
     # end to end through the same call with host buffers
     e2e_v, h2d, d2h = e2e_leg(libph, ctx, f, wl, max(2, args.steps // 2), torch)

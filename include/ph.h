@@ -152,7 +152,9 @@ typedef struct {
    * working-precision iterates to kappa u_low, and so does their failure.
    * Steps to t >= endgame_t run in working precision throughout (the end
    * game).
-   * Only ph_track_paths and the serving loop take lin_prec != 0. */
+   * ph_track_paths and the serving loop take 0..3; ph_track_path takes 0 and
+   * 1 (its step graph holds both kernel sets, one of them gated off per
+   * iteration). */
   int32_t lin_prec;
   int32_t reserved;   /* 0                                                        */
   double endgame_t;   /* <= 0: 1.0 (only the step that lands on t = 1)           */
@@ -200,6 +202,9 @@ typedef struct {
  * With params->control = 0 the whole loop runs on the device (one CUDA graph
  * launch per path) and the host reads the result once at the end; with 1 the
  * host launches one step (one graph) at a time, as in the paper.
+ * params->lin_prec is 0 or 1 here (PH_EINVAL otherwise): with 1 each step's
+ * Newton systems below endgame_t are evaluated and solved in IEEE double
+ * (see ph_track_params), the rest as with 0.
  *   f, g, gamma  as in ph_eval_jac (gamma is required here);
  *   x0           start solution [L][2][n];
  *   x_out        end point [L][2][n] (the last accepted point);

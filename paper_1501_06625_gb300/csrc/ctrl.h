@@ -62,3 +62,9 @@ PH_HD void ctrl_report(ph_ctrl_state *c, const ph_track_params *p, double t_new,
   }
   c->nsteps += 1;
 }
+
+// The precision form (lin_prec != 0): a failed step is corrected again in
+// working precision only if one of its double-precision solves had kappa
+// u_double above this: below it the double corrector contracts like the
+// working-precision one.
+constexpr double kEscalateRho = 1e-6;

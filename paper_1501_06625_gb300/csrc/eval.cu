@@ -51,6 +51,22 @@ __global__ void __launch_bounds__(128) k_ad(int M, int Mp, const int32_t *__rest
   ad_term<P>(s, Mp, nv, vidx, vexp, coeff, ptab, n, maxv, slots, nslots);
 }
 
+// The value c x^a of term s alone (no derivatives): the residual of the
+// precision form, where the Jacobian is evaluated in a lower precision.
+template <class P>
+__global__ void __launch_bounds__(128) k_val(int M, int Mp, const int32_t *__restrict__ nv,
+                                             const int32_t *__restrict__ vidx,
+                                             const int32_t *__restrict__ vexp,
+                                             const double *__restrict__ coeff,
+                                             const double *__restrict__ ptab, int n, int emax,
+                                             int maxv, double *__restrict__ slots, long nslots,
+                                             const int *__restrict__ skip) {
+  if (skip && *skip) return;
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= M) return;
+  val_term<P>(s, Mp, nv, vidx, vexp, coeff, ptab, n, emax, maxv, slots, nslots);
+}
+
 template <class P>
 PHD cx<P> shfl_up_c(const cx<P> &a, int d, int width) {
   cx<P> z;
@@ -159,10 +175,10 @@ __global__ void __launch_bounds__(256) k_sum(
     const double *__restrict__ spow, const double *__restrict__ scal, int homotopy,
     double *__restrict__ J, long ldJ, long Jplane, double *__restrict__ h,
     double *__restrict__ rhs, long rhs_plane, unsigned long long *__restrict__ res_bits,
-    const int *__restrict__ skip) {
+    const int *__restrict__ skip, int o0, int lead_rhs) {
   if (skip && *skip) return;
   long gt = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  int o = (int)(gt / G);
+  int o = o0 + (int)(gt / G);
   int lane = (int)(gt % G);
   bool active = o < nout;
   cx<P> val = sum_output<P, G>(active, o, lane, N, n, optr, oslot, slots, nslots, goptr, goslot,
@@ -175,7 +191,12 @@ __global__ void __launch_bounds__(256) k_sum(
   } else {
     int i = o - nN;
     if (h) c_store<P>(h, N, i, val);
-    if (rhs) c_store<P>(rhs, rhs_plane, i, c_neg<P>(val));
+    if (rhs && lead_rhs) {                     // the leading limbs of -h, [re|im]
+      rhs[i] = -P::lead(val.re);
+      rhs[rhs_plane + i] = -P::lead(val.im);
+    } else if (rhs) {
+      c_store<P>(rhs, rhs_plane, i, c_neg<P>(val));
+    }
     if (res_bits) atomicMax(res_bits, (unsigned long long)__double_as_longlong(c_mag_lead<P>(val)));
   }
 }
@@ -212,12 +233,13 @@ template <class P, int G>
 void sum_launch_g(const ph_system *f, const ph_system *g, int N, int n, const double *fslots,
                   long fs, const double *gslots, long gs, const double *spow, const double *scal,
                   int homotopy, double *J, long ldJ, long Jplane, double *h, double *rhs,
-                  long rhs_plane, unsigned long long *res_bits, const int *skip, cudaStream_t st) {
-  const long threads = (long)f->nout * G;
+                  long rhs_plane, unsigned long long *res_bits, const int *skip, cudaStream_t st,
+                  int o0, int lead_rhs) {
+  const long threads = (long)(f->nout - o0) * G;
   k_sum<P, G><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
       N, n, f->nout, f->out_ptr.as<int32_t>(), f->out_slot.as<int32_t>(), fslots, fs,
       g ? g->out_ptr.as<int32_t>() : nullptr, g ? g->out_slot.as<int32_t>() : nullptr, gslots, gs,
-      spow, scal, homotopy, J, ldJ, Jplane, h, rhs, rhs_plane, res_bits, skip);
+      spow, scal, homotopy, J, ldJ, Jplane, h, rhs, rhs_plane, res_bits, skip, o0, lead_rhs);
 }
 
 constexpr int kSumLanes[6] = {1, 2, 4, 8, 16, 32};
@@ -226,11 +248,12 @@ template <class P>
 void sum_launch(int G, const ph_system *f, const ph_system *g, int N, int n, const double *fslots,
                 long fs, const double *gslots, long gs, const double *spow, const double *scal,
                 int homotopy, double *J, long ldJ, long Jplane, double *h, double *rhs,
-                long rhs_plane, unsigned long long *res_bits, const int *skip, cudaStream_t st) {
+                long rhs_plane, unsigned long long *res_bits, const int *skip, cudaStream_t st,
+                int o0 = 0, int lead_rhs = 0) {
 #define PH_SUM_CASE(g_)                                                                          \
   case g_:                                                                                       \
     sum_launch_g<P, g_>(f, g, N, n, fslots, fs, gslots, gs, spow, scal, homotopy, J, ldJ,        \
-                        Jplane, h, rhs, rhs_plane, res_bits, skip, st);                           \
+                        Jplane, h, rhs, rhs_plane, res_bits, skip, st, o0, lead_rhs);             \
     break;
   switch (G) {
     PH_SUM_CASE(1)
@@ -240,7 +263,7 @@ void sum_launch(int G, const ph_system *f, const ph_system *g, int N, int n, con
     PH_SUM_CASE(32)
     default:
       sum_launch_g<P, 8>(f, g, N, n, fslots, fs, gslots, gs, spow, scal, homotopy, J, ldJ, Jplane,
-                         h, rhs, rhs_plane, res_bits, skip, st);
+                         h, rhs, rhs_plane, res_bits, skip, st, o0, lead_rhs);
   }
 #undef PH_SUM_CASE
 }
@@ -335,7 +358,71 @@ cudaError_t eval_impl(ph_ctx *ctx, const ph_system *f, const ph_system *g, const
   return cudaGetLastError();
 }
 
+// h(x, t) alone in the working precision: the power table and the factors,
+// the value of every term, and the summation of the N outputs of h only; the
+// leading limbs of -h go to rhs ([re|im], planes rhs_plane apart) and
+// max_i |h_i| to *res_bits.
+template <class P>
+cudaError_t eval_values_impl(ph_ctx *ctx, const ph_system *f, const ph_system *g,
+                             const double *gamma, int k, const double *t, const double *x,
+                             double *rhs, long rhs_plane, const int *skip,
+                             unsigned long long *res_bits) {
+  const int L = P::L, n = f->n, N = f->N;
+  int emax = f->emax;
+  if (g && g->emax > emax) emax = g->emax;
+  const int ntab = emax > 2 ? emax - 1 : 1;
+  cudaError_t e;
+  if ((e = ctx->ptab.ensure(sizeof(double) * 2 * L * (size_t)n * ntab)) != cudaSuccess) return e;
+  if ((e = ctx->scal.ensure(sizeof(double) * 3 * L)) != cudaSuccess) return e;
+  if ((e = ctx->spow.ensure(sizeof(double) * 4 * L * (size_t)n)) != cudaSuccess) return e;
+  double *spow = (gamma && !g) ? ctx->spow.as<double>() : nullptr;
+  const long fs = (long)(f->maxv + 1) * f->Mp;
+  const long gs = g ? (long)(g->maxv + 1) * g->Mp : 0;
+  if ((e = ctx->slots.ensure(sizeof(double) * 2 * L * (size_t)(fs + gs + 1))) != cudaSuccess) return e;
+  double *ptab = ctx->ptab.as<double>(), *scal = ctx->scal.as<double>();
+  double *fslots = ctx->slots.as<double>(), *gslots = fslots + 2 * L * fs;
+  cudaStream_t st = ctx->stream;
+  k_prep<P><<<(n + 127) / 128, 128, 0, st>>>(x, n, emax, ptab, f->deg.as<int32_t>(), spow, t,
+                                             gamma, k, scal, skip);
+  if (f->M > 0)
+    k_val<P><<<(f->M + 127) / 128, 128, 0, st>>>(f->M, f->Mp, f->nv.as<int32_t>(),
+                                                 f->vidx.as<int32_t>(), f->vexp.as<int32_t>(),
+                                                 f->coeff.as<double>(), ptab, n, emax, f->maxv,
+                                                 fslots, fs, skip);
+  if (g && g->M > 0)
+    k_val<P><<<(g->M + 127) / 128, 128, 0, st>>>(g->M, g->Mp, g->nv.as<int32_t>(),
+                                                 g->vidx.as<int32_t>(), g->vexp.as<int32_t>(),
+                                                 g->coeff.as<double>(), ptab, n, emax, g->maxv,
+                                                 gslots, gs, skip);
+  tune_sum<P>(ctx, f, g);
+  sum_launch<P>(f->sum_lanes > 0 ? f->sum_lanes : 8, f, g, N, n, fslots, fs, gslots, gs, spow,
+                scal, gamma != nullptr, nullptr, 0, 0, nullptr, rhs, rhs_plane, res_bits, skip, st,
+                n * N, 1);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t ph_eval_values_launch(ph_ctx *ctx, const ph_system *f, const ph_system *g,
+                                  const double *gamma, int k, const double *t, const double *x,
+                                  double *rhs, long rhs_plane, const int *skip,
+                                  unsigned long long *res_bits) {
+  if (f->L == 1)
+    return eval_values_impl<F64>(ctx, f, g, gamma, k, t, x, rhs, rhs_plane, skip, res_bits);
+  if (f->L == 2)
+    return eval_values_impl<DD>(ctx, f, g, gamma, k, t, x, rhs, rhs_plane, skip, res_bits);
+  return eval_values_impl<QD>(ctx, f, g, gamma, k, t, x, rhs, rhs_plane, skip, res_bits);
+}
+
+// The evaluation in IEEE double of a system loaded with more limbs: every
+// array is read through its leading limb (the limb-major layouts put limb 0
+// first), the results are written in the one-limb layout.
+cudaError_t ph_eval_launch_f64(ph_ctx *ctx, const ph_system *f, const ph_system *g,
+                               const double *gamma, int k, const double *t, const double *x,
+                               double *J, long ldJ, long Jplane, const int *skip) {
+  return eval_impl<F64>(ctx, f, g, gamma, k, t, x, nullptr, J, ldJ, Jplane, nullptr, 0, skip,
+                        nullptr, 7);
+}
 
 cudaError_t ph_eval_launch_part(ph_ctx *ctx, const ph_system *f, const ph_system *g,
                                 const double *gamma, int k, const double *t, const double *x,

@@ -58,6 +58,13 @@ struct PathState {
   int32_t skip_step, skip_nt;
   double t_dev[4];              // t of the step, L limbs
   double hist_t[16];            // t of the accepted points in the history ring
+  // the precision form (lin_prec 1): the precision of the current solve (0
+  // working, 1 double), the scale exponent of the right-hand side, the
+  // escalation state of the step, and the gates of the two kernel sets
+  int32_t lin, scale_e, force, escalate, onpath, retry, pass;
+  int32_t gate_wp, gate_lp;
+  int32_t solves_f64, escalated;
+  double cond;
 };
 
 struct ph_ctx {
@@ -129,13 +136,27 @@ cudaError_t ph_eval_launch_part(ph_ctx *ctx, const ph_system *f, const ph_system
                                 long rhs_plane, const int *skip, unsigned long long *res_bits,
                                 int parts);
 
+// eval.cu: h alone in the working precision (no derivatives): -h's leading
+// limbs to rhs ([re|im], planes rhs_plane apart), max |h_i| to *res_bits.
+cudaError_t ph_eval_values_launch(ph_ctx *ctx, const ph_system *f, const ph_system *g,
+                                  const double *gamma, int k, const double *t, const double *x,
+                                  double *rhs, long rhs_plane, const int *skip,
+                                  unsigned long long *res_bits);
+
+// eval.cu: the Jacobian alone in IEEE double from the leading limbs of every
+// input (x, t, gamma, the coefficients), in the one-limb layout.
+cudaError_t ph_eval_launch_f64(ph_ctx *ctx, const ph_system *f, const ph_system *g,
+                               const double *gamma, int k, const double *t, const double *x,
+                               double *J, long ldJ, long Jplane, const int *skip);
+
 // eval.cu: the summation kernel's lanes per output for f (and g), measured
 // on the first evaluation outside a stream capture (called before a capture).
 void ph_sum_tune(ph_ctx *ctx, const ph_system *f, const ph_system *g);
 
 // mgs.cu: least squares on the augmented matrix A = [J | rhs] held in
 //   A (plane stride (n+1)*ldA, leading dim ldA); dx [2L][n] out;
-//   st->dx_bits: max |dx_i| accumulated; resid: ||residual||_2 (may be null).
+//   st->dx_bits: max |dx_i| accumulated; resid: ||residual||_2 (may be null);
+//   ctx->nrm2[k] (k < n) ends as the leading limb of r_kk^2 with either variant.
 //   The pivot flags (ctx->flags, n+1 ints) must be zero when the state's
 //   mgs_epoch is zero: zero both at the start of every call.
 cudaError_t ph_mgs_launch(ph_ctx *ctx, int L, int N, int n, double *A, long ldA, double *dx,
@@ -154,4 +175,4 @@ int ph_mgs_tune(ph_ctx *ctx, int L, int N, int n);
 int ph_mgs_cluster_size(int L, int N, int n);
 cudaError_t ph_mgs_cluster_launch(cudaStream_t stream, int C, int L, int N, int n, const double *A,
                                   long ldA, double *W, double *dx, PathState *st, const int *skip,
-                                  double *resid);
+                                  double *resid, double *nrm_out);   // nrm_out: r_kk^2 (may be null)

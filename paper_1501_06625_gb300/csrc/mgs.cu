@@ -463,7 +463,7 @@ int ph_mgs_tune(ph_ctx *ctx, int L, int N, int n) {
                                              nullptr)
                      : ph_mgs_cluster_launch(ctx->stream, C, L, N, n, A, ldA,
                                              ctx->tuneW.as<double>(), ctx->tuneX.as<double>(), st,
-                                             nullptr, nullptr);
+                                             nullptr, nullptr, nullptr);
         if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float ms = 0.0f;
@@ -490,7 +490,8 @@ cudaError_t ph_mgs_launch(ph_ctx *ctx, int L, int N, int n, double *A, long ldA,
   if ((e = ctx->flags.ensure(sizeof(int) * (size_t)nc)) != cudaSuccess) return e;
   double *W = ctx->R.as<double>(), *nrm2 = ctx->nrm2.as<double>();
   const int C = ph_mgs_tune(ctx, L, N, n);
-  if (C > 0) return ph_mgs_cluster_launch(ctx->stream, C, L, N, n, A, ldA, W, dx, st, skip, resid);
+  if (C > 0)
+    return ph_mgs_cluster_launch(ctx->stream, C, L, N, n, A, ldA, W, dx, st, skip, resid, nrm2);
   if (L == 1)
     return launch_p<F64>(ctx->sm_count, ctx->stream, N, n, A, ldA, W, nrm2, dx,
                          ctx->flags.as<int>(), st, skip, resid);

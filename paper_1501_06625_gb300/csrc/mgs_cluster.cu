@@ -99,7 +99,8 @@ __global__ void __launch_bounds__(kCT) k_mgs_cl(int N, int n, const double *__re
                                                 long ldA, double *__restrict__ W,
                                                 double *__restrict__ dx, PathState *st,
                                                 const int *__restrict__ skip,
-                                                double *__restrict__ resid) {
+                                                double *__restrict__ resid,
+                                                double *__restrict__ nrm_out) {
   if (skip && *skip) return;                       // the same value in every CTA
   typedef typename P::real real;
   typedef Part<P> PO;
@@ -171,6 +172,8 @@ __global__ void __launch_bounds__(kCT) k_mgs_cl(int N, int n, const double *__re
         // pair holding column n always does)
         if (part == 0 && lane == 0 && (!(P::lead(r2) > 0.0) || !isfinite(P::lead(r2))))
           atomicExch(&st->mgs_status, PH_NONFINITE);
+        // ||a_k||^2 = r_kk^2 (leading limb), by the pair that holds column k+1
+        if (nrm_out && j == k + 1 && part == 0 && lane == 0) nrm_out[k] = P::lead(r2);
       }
       pair_sync(pair);
       first = false;
@@ -239,7 +242,8 @@ __global__ void __launch_bounds__(kCT) k_mgs_cl(int N, int n, const double *__re
 
 template <class P>
 cudaError_t launch_cl(cudaStream_t stream, int C, int N, int n, const double *A, long ldA,
-                      double *W, double *dx, PathState *st, const int *skip, double *resid) {
+                      double *W, double *dx, PathState *st, const int *skip, double *resid,
+                      double *nrm_out) {
   const size_t smem = sizeof(double) * (size_t)cl_layout(P::L, N, n, C).total;
   cudaError_t e = cudaFuncSetAttribute(k_mgs_cl<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
@@ -260,7 +264,7 @@ cudaError_t launch_cl(cudaStream_t stream, int C, int N, int n, const double *A,
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_mgs_cl<P>, N, n, A, ldA, W, dx, st, skip, resid);
+  return cudaLaunchKernelEx(&cfg, k_mgs_cl<P>, N, n, A, ldA, W, dx, st, skip, resid, nrm_out);
 }
 
 template <class P>
@@ -306,8 +310,8 @@ int ph_mgs_cluster_size(int L, int N, int n) {
 
 cudaError_t ph_mgs_cluster_launch(cudaStream_t stream, int C, int L, int N, int n, const double *A,
                                   long ldA, double *W, double *dx, PathState *st, const int *skip,
-                                  double *resid) {
-  if (L == 1) return launch_cl<F64>(stream, C, N, n, A, ldA, W, dx, st, skip, resid);
-  if (L == 2) return launch_cl<DD>(stream, C, N, n, A, ldA, W, dx, st, skip, resid);
-  return launch_cl<QD>(stream, C, N, n, A, ldA, W, dx, st, skip, resid);
+                                  double *resid, double *nrm_out) {
+  if (L == 1) return launch_cl<F64>(stream, C, N, n, A, ldA, W, dx, st, skip, resid, nrm_out);
+  if (L == 2) return launch_cl<DD>(stream, C, N, n, A, ldA, W, dx, st, skip, resid, nrm_out);
+  return launch_cl<QD>(stream, C, N, n, A, ldA, W, dx, st, skip, resid, nrm_out);
 }

@@ -21,10 +21,6 @@ constexpr int kBT = 256;          // threads per block: 8 warps, 2 per SM sub-pa
 constexpr int kNW = kBT / 32;
 constexpr int kHistB = 16;        // accepted points kept for the predictor
 constexpr int kSG = 4;            // lanes per output in the summation
-// A failed step is corrected again in working precision only if one of its
-// double-precision solves had kappa u_double above this: below it the double
-// corrector contracts like the working-precision one.
-constexpr double kEscalateRho = 1e-6;
 
 struct Job {
   int L, N, n, Mf, Mpf, maxvf, Mg, Mpg, maxvg, emax, nout;

@@ -17,6 +17,16 @@
 // until step_end clears the condition.  Kernels gate themselves on flags in
 // PathState, so a corrector that finished early costs only empty launches.
 // The host reads the state once, after the path.
+//
+// The precision form (lin_prec 1) records a second kernel set beside each
+// iteration's: h alone in working precision (its leading limbs scaled by 2^-e,
+// e the exponent of max |h_i|), the Jacobian in IEEE double from the leading
+// limbs, MGS in double, and x += 2^e dx in working precision.  The control
+// kernels choose the set per step through two gates: double while t is below
+// the end game, working precision at t = 1 and when a failed step is corrected
+// again (the retry runs the step body once more at the same t, in working
+// precision).  The rules (one extra iteration, escalation) are those of the
+// many-path form.
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -35,6 +45,14 @@ namespace {
 
 constexpr int kHist = 16;          // ring of accepted points (pred_order <= 8)
 
+// The gates of the precision form's two kernel sets: the working-precision set
+// runs while the corrector runs and solves in working precision, the double
+// set while it runs and solves in double.
+__device__ __forceinline__ void set_gates(PathState *st) {
+  st->gate_wp = st->skip_nt || st->lin != 0;
+  st->gate_lp = st->skip_nt || st->lin == 0;
+}
+
 __global__ void k_step_begin(PathState *st, ph_track_params p, int L) {
   st->iterations += 1;
   if (st->timeout && !st->ctrl.done) {     // a bounded wait ran out: stop the path
@@ -44,13 +62,24 @@ __global__ void k_step_begin(PathState *st, ph_track_params p, int L) {
   if (st->ctrl.done) {
     st->skip_step = 1;
     st->skip_nt = 1;
+    set_gates(st);
     return;
   }
-  double tn = ctrl_next_t(&st->ctrl, &p);
-  if (tn < 0.0) {
-    st->skip_step = 1;
-    st->skip_nt = 1;
-    return;
+  double tn;
+  if (st->retry) {                         // the failed step again, in working precision
+    st->retry = 0;
+    st->pass = 1;
+    tn = st->t_new;
+  } else {
+    tn = ctrl_next_t(&st->ctrl, &p);
+    if (tn < 0.0) {
+      st->skip_step = 1;
+      st->skip_nt = 1;
+      set_gates(st);
+      return;
+    }
+    st->pass = 0;
+    st->force = 0;
   }
   st->t_new = tn;
   st->t_dev[0] = tn;
@@ -65,6 +94,11 @@ __global__ void k_step_begin(PathState *st, ph_track_params p, int L) {
   st->mgs_status = 0;
   st->skip_step = 0;
   st->skip_nt = 0;
+  st->escalate = 0;
+  st->onpath = 0;
+  const double endgame = p.endgame_t > 0.0 ? p.endgame_t : 1.0;
+  st->lin = (p.lin_prec == 1 && !(tn >= endgame) && st->force != 2) ? 1 : 0;
+  set_gates(st);
 }
 
 // x(t_new) = sum_j w_j x(t_j) over the last m accepted points, with the
@@ -119,41 +153,108 @@ __global__ void k_check_res(PathState *st, ph_track_params p) {
   st->res_last = r;
   st->dx_bits = 0;
   st->mgs_status = 0;
-  if (p.fixed_steps > 0) return;
-  if (!(r <= st->last_res) || !isfinite(r)) {       // residual grew (or NaN): fail
-    st->nt_done = 1;
-    st->nt_success = 0;
-    st->skip_nt = 1;
-  } else if (r < p.tol_res) {
-    st->nt_done = 1;
-    st->nt_success = 1;
-    st->skip_nt = 1;
+  // the exponent by which the double solve's right-hand side is scaled
+  st->scale_e = (r > 0.0 && isfinite(r)) ? ilogb(r) : 0;
+  if (p.fixed_steps <= 0) {
+    if (!(r <= st->last_res) || !isfinite(r)) {     // residual grew (or NaN): fail
+      st->nt_done = 1;
+      st->nt_success = 0;
+      st->skip_nt = 1;
+    } else if (r < p.tol_res) {
+      st->nt_done = 1;
+      st->nt_success = 1;
+      st->skip_nt = 1;
+    }
+  }
+  set_gates(st);
+}
+
+// The double solve's right-hand side: -h's leading limbs times 2^-e, so that
+// neither it nor the update underflows however small the residual.
+__global__ void k_rhs_scale(const PathState *st, double *__restrict__ rhs, long plane, int N) {
+  if (st->gate_lp) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) {
+    const int e = st->scale_e;
+    rhs[i] = ldexp(rhs[i], -e);
+    rhs[plane + i] = ldexp(rhs[plane + i], -e);
   }
 }
 
+// x += dx: from the working-precision solve (lowp 0, dx in the L-limb layout)
+// or from the double solve (lowp 1, dx [re|im][n] scaled back by 2^e).
 template <class P>
 __global__ void k_update(PathState *st, double *__restrict__ xw, const double *__restrict__ dx,
-                         int n, int fixed) {
-  if (st->skip_nt) return;
+                         int n, int fixed, int lowp) {
+  if (st->skip_nt || st->lin != lowp) return;
   const bool bad = st->mgs_status != 0;
   if (bad && !fixed) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) {
-    cx<P> d = bad ? c_from<P>(NAN, NAN) : c_load<P>(dx, n, i);
+    cx<P> d;
+    if (bad) {
+      d = c_from<P>(NAN, NAN);
+    } else if (lowp) {
+      const int e = st->scale_e;
+      d = c_from<P>(ldexp(dx[i], e), ldexp(dx[n + i], e));
+    } else {
+      d = c_load<P>(dx, n, i);
+    }
     c_store<P>(xw, n, i, c_add<P>(c_load<P>(xw, n, i), d));
   }
 }
 
-__global__ void k_check_dx(PathState *st, ph_track_params p) {
+// The update test.  After a double solve, also the condition estimate
+// max r_kk / min r_kk from the solve's pivot norms (nrm2[k] = r_kk^2, k < n),
+// the escalation rule, and one iteration beyond max_newton when the previous
+// update was below sqrt(tol_dx) (the working-precision corrector would have
+// squared it below tol_dx by now; the double one contracts by kappa u_double).
+__global__ void k_check_dx(PathState *st, ph_track_params p, const double *__restrict__ nrm2,
+                           int n) {
   if (st->skip_nt) return;
+  __shared__ double s_mx[32], s_mn[32];
+  const int lin = st->lin, tid = threadIdx.x;
+  double mx = 0.0, mn = INFINITY;
+  if (lin) {
+    for (int k = tid; k < n; k += blockDim.x) {
+      const double v = nrm2[k];
+      mx = fmax(mx, v);
+      mn = fmin(mn, v);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+      mn = fmin(mn, __shfl_down_sync(0xffffffffu, mn, o));
+    }
+    if ((tid & 31) == 0) {
+      s_mx[tid >> 5] = mx;
+      s_mn[tid >> 5] = mn;
+    }
+    __syncthreads();
+    if (tid == 0)
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+        mx = fmax(mx, s_mx[w]);
+        mn = fmin(mn, s_mn[w]);
+      }
+  }
+  if (tid != 0) return;
   const bool fixed = p.fixed_steps > 0;
+  if (lin) {
+    const double c = st->mgs_status == 0 ? sqrt(mx / mn) : INFINITY;
+    st->solves_f64 += 1;
+    st->cond = c;
+    if (!(c * 0x1p-53 <= kEscalateRho)) st->escalate = 2;
+  }
   if (st->mgs_status != 0 && !fixed) {               // singular Jacobian: fail
     st->nt_done = 1;
     st->nt_success = 0;
     st->skip_nt = 1;
+    set_gates(st);
     return;
   }
   double d = st->mgs_status != 0 ? NAN : __longlong_as_double((long long)st->dx_bits);
+  if (lin) d = ldexp(d, st->scale_e);
+  const bool prev_on_path = lin && st->nt_updates >= 1 && st->dxn <= sqrt(p.tol_dx);
+  if (prev_on_path) st->onpath = 1;
   st->dxn = d;
   st->dx_last = d;
   st->nt_updates += 1;
@@ -164,33 +265,54 @@ __global__ void k_check_dx(PathState *st, ph_track_params p) {
       st->nt_done = 1;
       st->nt_success = 0;
       st->skip_nt = 1;
+      set_gates(st);
       return;
     }
     if (d < p.tol_dx) {
       st->nt_done = 1;
       st->nt_success = 1;
       st->skip_nt = 1;
+      set_gates(st);
       return;
     }
     st->last_res = st->res;
   }
-  if (st->nt_iters >= p.max_newton) {                // out of iterations
-    st->nt_done = 1;
+  const int max_it = fixed ? p.max_newton : p.max_newton + 1;
+  if (st->nt_iters >= p.max_newton && !(prev_on_path && st->nt_iters < max_it)) {
+    st->nt_done = 1;                                 // out of iterations
     st->nt_success = fixed ? 1 : 0;
     st->skip_nt = 1;
   }
+  set_gates(st);
 }
 
 template <class P>
 __global__ void k_step_end(PathState *st, ph_track_params p, double *__restrict__ hist,
                            const double *__restrict__ xw, int n, ph_step_record *log, int log_cap,
                            cudaGraphConditionalHandle cond, int use_cond) {
-  __shared__ int s_ok, s_slot;
+  __shared__ int s_ok, s_slot, s_retry;
   __shared__ double s_max;
   if (st->skip_step) {
     if (use_cond && threadIdx.x == 0 && st->ctrl.done) cudaGraphSetConditional(cond, 0);
     return;
   }
+  if (threadIdx.x == 0) {
+    // the precision form: a failed step whose corrector must not be trusted is
+    // corrected once more at the same t, in working precision (k_step_begin)
+    int ok = st->nt_success;
+    s_retry = 0;
+    if (p.lin_prec != 0 && !ok) {
+      if (st->onpath) st->escalate = 2;
+      if (st->pass == 0 && st->escalate && p.fixed_steps <= 0) {
+        st->force = st->escalate;
+        st->escalated += 1;
+        st->retry = 1;
+        s_retry = 1;
+      }
+    }
+  }
+  __syncthreads();
+  if (s_retry) return;
   if (threadIdx.x == 0) {
     int ok = st->nt_success;
     st->steps += 1;
@@ -312,17 +434,35 @@ static cudaError_t record_step(ph_ctx *ctx, cudaStream_t s, const ph_system *f,
   if (L == 1) k_predict<F64><<<pg, pb, 0, s>>>(st, hist, xw, n, p.pred_order);
   else if (L == 2) k_predict<DD><<<pg, pb, 0, s>>>(st, hist, xw, n, p.pred_order);
   else k_predict<QD><<<pg, pb, 0, s>>>(st, hist, xw, n, p.pred_order);
-  for (int it = 0; it < p.max_newton && e == cudaSuccess; ++it) {
-    e = ph_eval_launch(ctx, f, g, gamma, p.relax_k, st->t_dev, xw, nullptr, A, ldA, Ap,
-                       A + (long)n * ldA, Ap, &st->skip_nt, &st->res_bits);
+  // the precision form: both kernel sets, and one iteration more (k_check_dx)
+  const bool mixed = p.lin_prec == 1;
+  const int n_it = mixed && p.fixed_steps <= 0 ? p.max_newton + 1 : p.max_newton;
+  const int *gwp = mixed ? &st->gate_wp : &st->skip_nt;
+  double *rhs = A + (long)n * ldA;
+  const int fx = p.fixed_steps > 0;
+  const unsigned ub = (unsigned)((n + 127) / 128);
+  for (int it = 0; it < n_it && e == cudaSuccess; ++it) {
+    e = ph_eval_launch(ctx, f, g, gamma, p.relax_k, st->t_dev, xw, nullptr, A, ldA, Ap, rhs, Ap,
+                       gwp, &st->res_bits);
+    if (e == cudaSuccess && mixed)
+      e = ph_eval_values_launch(ctx, f, g, gamma, p.relax_k, st->t_dev, xw, rhs, Ap, &st->gate_lp,
+                                &st->res_bits);
     if (e != cudaSuccess) break;
     k_check_res<<<1, 1, 0, s>>>(st, p);
-    e = ph_mgs_launch(ctx, L, N, n, A, ldA, dx, st, &st->skip_nt, nullptr);
+    if (mixed) {
+      k_rhs_scale<<<(N + 127) / 128, 128, 0, s>>>(st, rhs, Ap, N);
+      e = ph_eval_launch_f64(ctx, f, g, gamma, p.relax_k, st->t_dev, xw, A, ldA, Ap, &st->gate_lp);
+      if (e != cudaSuccess) break;
+    }
+    e = ph_mgs_launch(ctx, L, N, n, A, ldA, dx, st, gwp, nullptr);
+    if (e == cudaSuccess && mixed) e = ph_mgs_launch(ctx, 1, N, n, A, ldA, dx, st, &st->gate_lp, nullptr);
     if (e != cudaSuccess) break;
-    if (L == 1) k_update<F64><<<(n + 127) / 128, 128, 0, s>>>(st, xw, dx, n, p.fixed_steps > 0);
-    else if (L == 2) k_update<DD><<<(n + 127) / 128, 128, 0, s>>>(st, xw, dx, n, p.fixed_steps > 0);
-    else k_update<QD><<<(n + 127) / 128, 128, 0, s>>>(st, xw, dx, n, p.fixed_steps > 0);
-    k_check_dx<<<1, 1, 0, s>>>(st, p);
+    for (int lowp = 0; lowp <= (mixed ? 1 : 0); ++lowp) {
+      if (L == 1) k_update<F64><<<ub, 128, 0, s>>>(st, xw, dx, n, fx, lowp);
+      else if (L == 2) k_update<DD><<<ub, 128, 0, s>>>(st, xw, dx, n, fx, lowp);
+      else k_update<QD><<<ub, 128, 0, s>>>(st, xw, dx, n, fx, lowp);
+    }
+    k_check_dx<<<1, 128, 0, s>>>(st, p, ctx->nrm2.as<double>(), n);
   }
   if (e == cudaSuccess) {
     int eb = n < 256 ? 128 : 256;
@@ -343,6 +483,7 @@ static ph_status build_graph(ph_ctx *ctx, TrackCache *c, const ph_system *f, con
                              ph_step_record *log, int log_cap) {
   drop_graph(c->tg);
   ph_mgs_tune(ctx, f->L, f->N, f->n);                // measured now: the capture cannot
+  if (p.lin_prec == 1) ph_mgs_tune(ctx, 1, f->N, f->n);
   ph_sum_tune(ctx, f, g);
   if (!c->cap) PH_CUDA(ctx, cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
   TrackGraph &tg = c->tg;
@@ -397,8 +538,9 @@ extern "C" ph_status ph_track_path(ph_ctx *ctx, const ph_system *f, const ph_sys
       p.relax_k < 1 || p.relax_k > 64 || p.control < 0 || p.control > 1 || p.max_steps < 0 ||
       (p.fixed_steps <= 0 && !(p.max_dt > 0.0 && p.min_dt > 0.0 && p.min_dt <= p.max_dt)))
     return ph_fail(ctx, PH_EINVAL, "ph_track_path: invalid parameters");
-  if (p.lin_prec != 0)
-    return ph_fail(ctx, PH_EINVAL, "ph_track_path: lin_prec != 0 is taken by ph_track_paths and the serving loop");
+  if (p.lin_prec != 0 && p.lin_prec != 1)
+    return ph_fail(ctx, PH_EINVAL,
+                   "ph_track_path: lin_prec 2 and 3 are taken by ph_track_paths and the serving loop");
   if (!g) {
     if (f->N != f->n) return ph_fail(ctx, PH_EINVAL, "ph_track_path: the total-degree start system needs N == n");
     for (int d : f->h_deg)
@@ -513,6 +655,11 @@ extern "C" ph_status ph_track_path(ph_ctx *ctx, const ph_system *f, const ph_sys
     stats->res = hs.res_last;
     stats->dx = hs.dx_last;
     stats->launches = (int64_t)hs.iterations * c->tg.kernels_per_step;
+    stats->solves_f64 = hs.solves_f64;
+    stats->solves_f32 = 0;
+    stats->escalated = hs.escalated;
+    stats->reserved = 0;
+    stats->cond = hs.cond;
   }
   if (status == PH_TIMEOUT) return ph_fail(ctx, PH_TIMEOUT, "ph_track_path: a grid barrier timed out");
   return status;
