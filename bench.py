@@ -432,6 +432,68 @@ def cyclic_leg(libph, synth, ctx, torch, dev, peak):
     return out
 
 
+# The paper's Table 8: one monodromy path of cyclic n-roots on its Tesla K20C,
+# per (n, limbs): success (1) or failure (0), predictor-corrector steps m, CPU
+# and GPU seconds.  Context, not targets.
+PAPER_CYCLIC_PATH = {(16, 1): (1, 32, 0.00, 0.03), (16, 2): (1, 20, 0.04, 0.06),
+                     (16, 4): (1, 32, 0.48, 0.52), (64, 1): (0, 987, 4.48, 4.15),
+                     (64, 2): (1, 225, 22.94, 2.57), (64, 4): (1, 987, 229.99, 17.93),
+                     (144, 1): (0, 214, 12.58, 2.67), (144, 2): (0, 1500, 1487.86, 61.59),
+                     (144, 4): (1, 214, 15898.67, 479.18)}
+
+
+def monodromy_leg(libph, synth, ctx, torch, dev, seed, segment):
+    """One monodromy path on cyclic n-roots, n = m^2 = 16, 64, 144 (Section
+    4.2; the paper's runs of Table 8): the (m-1)-dimensional solution set cut
+    by m - 1 random hyperplanes that move to m - 1 others, N = n + m - 1
+    equations corrected by least squares, from a start point of Backelin's
+    family (synth.cyclic_monodromy).  D, DD and QD with 3 / 5 / 6 Newton
+    iterations per step and the library's default tolerances.  Whole paths
+    where they take seconds; elsewhere the first `segment` steps.  Each run is
+    timed with CUDA events around one ph_track_path call, after an untimed
+    call that builds its step graph.  The comparison with the paper is per
+    predictor-corrector step: the paper's tolerances and Newton budget are not
+    stated, so the step counts of whole paths differ."""
+    out = {}
+    newton = {1: 3, 2: 5, 4: 6}
+    stream = torch.cuda.current_stream(dev)
+    for n in (16, 64, 144):
+        F, G, gam, x0 = synth.cyclic_monodromy(seed, n)
+        for L, name in ((1, "d"), (2, "dd"), (4, "qd")):
+            whole = n == 16 or (n == 64 and L < 4)
+            params = synth.default_params(L, max_newton=newton[L],
+                                          max_steps=5000 if whole else segment - 1)
+            f, g = ctx.load(F, L), ctx.load(G, L)
+            xs = np.zeros((L, 2, n))
+            xs[0, 0], xs[0, 1] = x0.real, x0.imag
+            gs = np.zeros((L, 2))
+            gs[0] = [gam.real, gam.imag]
+            dx0 = torch.tensor(xs, dtype=torch.float64, device=dev)
+            dg = torch.tensor(gs, dtype=torch.float64, device=dev)
+            xo = torch.empty_like(dx0)
+            libph.ph_track_path(ctx.h, f, g, dg, dx0, params, xo)        # builds the graph
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st, sd, _ = libph.ph_track_path(ctx.h, f, g, dg, dx0, params, xo)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            ps, pm, pcpu, pgpu = PAPER_CYCLIC_PATH[(n, L)]
+            per_step = ms / max(1, sd["steps"])
+            out[f"cyclic{n}_{name}"] = {
+                "N": F.N, "n": n, "whole_path": whole, "status": int(st),
+                "t_final": sd["t_final"], "steps": sd["steps"], "accepted": sd["accepted"],
+                "newton_iters": sd["newton_iters"], "ms": ms, "ms_per_step": per_step,
+                "ms_per_newton_iter": ms / max(1, sd["newton_iters"]),
+                "paper_k20c": {"success": ps, "steps": pm, "gpu_s": pgpu, "cpu_s": pcpu,
+                               "ms_per_step": 1e3 * pgpu / pm},
+                "per_step_vs_paper": (1e3 * pgpu / pm) / per_step}
+            ctx.free(f)
+            ctx.free(g)
+    return out
+
+
 def serve_leg(libph, synth, ctx, nreq, seed, lin=0, seq_rate=None):
     """A stream of path-tracking requests through the continuous-batching loop
     (ph_server_*).  A pool of 16 systems per (recipe, precision): n =
@@ -568,7 +630,9 @@ def main():
                     help="paths of the precision-form leg (0 skips it)")
     ap.add_argument("--serve-requests", type=int, default=384,
                     help="requests of the serving leg (0 skips it)")
-    ap.add_argument("--no-cyclic", action="store_true", help="skip the cyclic n-roots leg")
+    ap.add_argument("--no-cyclic", action="store_true", help="skip the cyclic n-roots legs")
+    ap.add_argument("--monodromy-segment", type=int, default=40,
+                    help="steps of the cyclic monodromy paths not tracked whole")
     ap.add_argument("--no-sparse", action="store_true",
                     help="skip the n=512 QD solver roofline measurement")
     args = ap.parse_args()
@@ -667,9 +731,11 @@ def main():
         serve_mixed = serve_leg(libph, synth, ctx, args.serve_requests, args.seed, lin=3,
                                 seq_rate=serve["sequential_single_path"]["paths_per_s"])
 
-    cyclic = None
+    cyclic = monodromy = None
     if not args.no_cyclic and rank == 0:
         cyclic = cyclic_leg(libph, synth, ctx, torch, dev, peak)
+        monodromy = monodromy_leg(libph, synth, ctx, torch, dev, args.seed,
+                                  args.monodromy_segment)
 
     precision = None
     if args.precision_paths > 0 and rank == 0:
@@ -738,6 +804,7 @@ def main():
             "p50_segment_ms": s["p50_segment_ms"], "p99_segment_ms": s["p99_segment_ms"],
             "path": s["path"], "qd": qd, "batched": batch, "serving": serve,
             "serving_mixed": serve_mixed, "precision": precision, "cyclic": cyclic,
+            "cyclic_monodromy_path": monodromy,
             "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": s["launches"], "roofline": roof, "roofline_sparse512_mgs": roof512,

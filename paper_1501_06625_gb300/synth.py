@@ -262,6 +262,82 @@ def cyclic_system(n: int) -> SystemSpec:
                       np.ones(var_idx.size, dtype=np.int32), coeff)
 
 
+def backelin_point(m: int, v: np.ndarray) -> np.ndarray:
+    """A point of the (m-1)-dimensional solution set of cyclic n-roots,
+    n = m^2, that Backelin's lemma asserts (Section 4.2).  Writing
+    x_k = z_{k+1} / z_k (indices mod n) turns f_i = 0 (i < n) into the vanishing
+    of the periodic correlations sum_j z_{j+i} / z_j, and makes f_n = 0 read
+    prod x_k = 1, which then holds.  The sequence z_{am+b} = w^{ab} u_b
+    (0 <= a, b < m, w = e^{2 pi i/m}, u_b free) has every correlation zero: the
+    sum over a kills each shift that is not a multiple of m, the sum over b
+    each that is.  In x this is x_{am+b} = w^a v_b with v_b = u_{b+1} / u_b, that
+    is, any v with prod_b v_b = 1: v gives the m - 1 free parameters.
+    v: m complex numbers; v[m-1] is replaced by 1 / prod(v[:m-1])."""
+    v = np.asarray(v, dtype=np.complex128).copy()
+    v[m - 1] = 1.0 / np.prod(v[:m - 1])
+    a = np.arange(m)
+    w = np.exp(2j * np.pi * a / m)
+    return (w[:, None] * v[None, :]).ravel()              # index a m + b
+
+
+def _with_linear_rows(spec: SystemSpec, coef: np.ndarray, const: np.ndarray,
+                      const_lo: np.ndarray) -> SystemSpec:
+    """spec followed by the rows sum_k coef[r, k] x_k + const[r] (+ const_lo[r],
+    a second limb)."""
+    r, n = coef.shape
+    M0 = spec.M
+    term_ptr = np.concatenate([spec.term_ptr.astype(np.int64),
+                               M0 + (n + 1) * np.arange(1, r + 1)])
+    lens = np.tile(np.append(np.ones(n, dtype=np.int64), 0), r)
+    var_ptr = np.concatenate([spec.var_ptr.astype(np.int64),
+                              spec.var_ptr[-1] + np.cumsum(lens)])
+    var_idx = np.concatenate([spec.var_idx, np.tile(np.arange(n, dtype=np.int32), r)])
+    var_exp = np.concatenate([spec.var_exp, np.ones(n * r, dtype=np.int32)])
+    coeff = np.concatenate([spec.coeff, np.hstack([coef, const[:, None]]).ravel()])
+    lo0 = spec.coeff_lo if spec.coeff_lo is not None else np.zeros(M0, dtype=np.complex128)
+    lo = np.concatenate([lo0, np.hstack([np.zeros((r, n)), const_lo[:, None]]).ravel()])
+    return SystemSpec(spec.N + r, spec.n, term_ptr.astype(np.int32), var_ptr.astype(np.int32),
+                      var_idx.astype(np.int32), var_exp.astype(np.int32), coeff,
+                      lo.astype(np.complex128))
+
+
+def cyclic_monodromy(seed: int, n: int):
+    """One monodromy path on cyclic n-roots, n = m^2 (Section 4.2): the
+    solution set of dimension m - 1 cut by m - 1 random hyperplanes L, moved to
+    m - 1 other random hyperplanes K.  The paper's homotopy {f = 0,
+    alpha (1-t) L + t K = 0} has the zero set of gamma (1-t) G + t F with
+    G = [f; L], F = [f; K] and gamma = alpha (its first block is f times
+    gamma (1-t) + t, which does not vanish for t in [0, 1]): N = n + m - 1
+    equations in n unknowns, corrected by least squares.  The start point is
+    backelin_point with v of unit modulus (random angles); L's constant terms
+    are -sum_k c_k x0_k, summed exactly in rationals from the double x0 and
+    stored as two limbs.  Returns (F, G, gamma, x0)."""
+    from fractions import Fraction
+    m = int(round(np.sqrt(n)))
+    if m * m != n or m < 2:
+        raise ValueError("the monodromy workload needs n = m^2, m >= 2")
+    rng = Rng(seed * 1000003 + n)
+    v = np.array([rng.unit_complex() for _ in range(m)])
+    x0 = backelin_point(m, v)
+    r = m - 1
+    cL = np.array([[rng.unit_complex() for _ in range(n)] for _ in range(r)])
+    cK = np.array([[rng.unit_complex() for _ in range(n)] for _ in range(r)])
+    kK = np.array([rng.unit_complex() for _ in range(r)])
+    hi, lo = np.zeros(r, dtype=np.complex128), np.zeros(r, dtype=np.complex128)
+    for q in range(r):
+        sr, si = Fraction(0), Fraction(0)
+        for c, x in zip(cL[q], x0):
+            sr -= Fraction(c.real) * Fraction(x.real) - Fraction(c.imag) * Fraction(x.imag)
+            si -= Fraction(c.real) * Fraction(x.imag) + Fraction(c.imag) * Fraction(x.real)
+        hr, him = float(sr), float(si)
+        hi[q] = complex(hr, him)
+        lo[q] = complex(float(sr - Fraction(hr)), float(si - Fraction(him)))
+    f = cyclic_system(n)
+    F = _with_linear_rows(f, cK, kK, np.zeros(r, dtype=np.complex128))
+    G = _with_linear_rows(f, cL, hi, lo)
+    return F, G, rng.unit_complex(), x0
+
+
 def default_params(L: int, **over) -> dict:
     """Path-tracking parameters (the paper leaves them open).  Newton's
     method roughly squares the error per iteration, so from a predictor error

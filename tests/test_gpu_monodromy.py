@@ -1,0 +1,84 @@
+"""One monodromy path on cyclic 16-roots (Section 4.2, the paper's runs of
+Table 8): the solution set of dimension 3 (m = 4) cut by three random
+hyperplanes L, which move to three others K, a least-squares path (N = 19
+equations in n = 16 unknowns) from a start point of Backelin's family.
+
+* complex double: the whole adaptive path, and the oracle's replay of its
+  schedule ends at the same point;
+* DD and QD: segments of the adaptive path replayed by the oracle (a whole
+  path would take the oracle minutes), and whole paths that end on the same
+  component (x_{4a+b} = i^a x_b, exact in every limb) and on the target
+  slices.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_common import TOL_END, U, cabs_diff, lead_complex, soa_from_complex
+from paper_1501_06625_gb300 import libph, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1501_06625_gb300 import build
+    build.build()
+    oracle.build()
+    c = libph.Context(0)
+    yield c
+    c.close()
+
+
+def _mono(L, **over):
+    F, G, gam, x0 = synth.cyclic_monodromy(1, 16)
+    xs = soa_from_complex(x0, L)
+    gs = soa_from_complex([gam], L).reshape(L, 2)
+    return F, G, gs, xs, synth.default_params(L, **over)
+
+
+def _family_gap(x, L):
+    """max |x_{4a+b} - i^a x_b| over the limbs (exact for m = 4: multiplying by
+    i^a swaps or negates parts), relative to max |x|: zero on the component."""
+    z = x[:, 0] + 1j * x[:, 1]                  # [L][n]
+    w = np.array([1, 1j, -1, -1j])
+    d = z.reshape(L, 4, 4) - w[None, :, None] * z.reshape(L, 4, 4)[:, :1, :]
+    tot = d[::-1].sum(axis=0)                   # limbs summed from the smallest
+    return np.abs(tot).max() / np.abs(z[0]).max()
+
+
+def test_monodromy_path_double_replay(ctx):
+    L = 1
+    F, G, gs, xs, params = _mono(L, max_steps=3000)
+    f, g = ctx.load(F, L), ctx.load(G, L)
+    x = np.zeros_like(xs)
+    st, stats, log = libph.ph_track_path(ctx.h, f, g, gs, xs, params, x, log_cap=3100)
+    assert st == libph.PH_OK and stats["t_final"] == 1.0 and len(log) == stats["steps"]
+    xo = oracle.replay(oracle.System(F, L), xs, gs, params, log, g=oracle.System(G, L))
+    assert cabs_diff(x, xo).max() <= TOL_END[L] * np.abs(lead_complex(xo)).max()
+    assert _family_gap(x, L) < 1e-13
+
+
+@pytest.mark.parametrize("L,steps,newton", [(2, 40, 5), (4, 8, 6)])
+def test_monodromy_segment_replay(ctx, L, steps, newton):
+    F, G, gs, xs, params = _mono(L, max_steps=steps - 1, max_newton=newton)
+    f, g = ctx.load(F, L), ctx.load(G, L)
+    x = np.zeros_like(xs)
+    st, stats, log = libph.ph_track_path(ctx.h, f, g, gs, xs, params, x, log_cap=steps)
+    assert stats["steps"] == steps and stats["accepted"] >= 1
+    xo = oracle.replay(oracle.System(F, L), xs, gs, params, log, g=oracle.System(G, L))
+    assert cabs_diff(x, xo).max() <= TOL_END[L]
+
+
+@pytest.mark.parametrize("L,newton", [(2, 5), (4, 6)])
+def test_monodromy_path_ends_on_the_component(ctx, L, newton):
+    """The whole path in DD / QD: it reaches t = 1 on the same component
+    (x_{4a+b} = i^a x_b to working precision) and on the target slices."""
+    F, G, gs, xs, params = _mono(L, max_steps=3000, max_newton=newton)
+    f, g = ctx.load(F, L), ctx.load(G, L)
+    x = np.zeros_like(xs)
+    st, stats, _ = libph.ph_track_path(ctx.h, f, g, gs, xs, params, x)
+    assert st == libph.PH_OK and stats["t_final"] == 1.0, stats
+    assert _family_gap(x, L) < 1e3 * U[L]
+    h, _ = oracle.eval_h(oracle.System(F, L), x)
+    assert np.abs(lead_complex(h)).max() < 1e3 * params["tol_res"]

@@ -1,0 +1,86 @@
+"""The monodromy workload on cyclic n-roots (Section 4.2), n = m^2: its start
+point must lie on the (m-1)-dimensional solution set that Backelin's lemma
+gives, and the start slices must pass through it.
+
+* the cyclic equations (Eq. (10)), evaluated in 60-digit arithmetic at the
+  double start point, vanish to the rounding of that point;
+* the Jacobian of the cyclic equations there has exactly m - 1 singular
+  values at rounding level: the solution set has dimension m - 1 at x0, as
+  many as there are slices;
+* the oracle's evaluation of the start system [f; L] at x0 in double-double:
+  the slice rows vanish to DD rounding (their constant terms are the exact
+  sums stored as two limbs), the cyclic rows to the rounding of x0.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1501_06625_gb300 import synth
+
+mpmath = pytest.importorskip("mpmath")
+
+
+def _cyclic_mp(x):
+    mp = mpmath.mp
+    n = len(x)
+    out = []
+    for i in range(1, n):
+        s = mp.mpc(0)
+        for j in range(n):
+            p = mp.mpc(1)
+            for k in range(j, j + i):
+                p *= x[k % n]
+            s += p
+        out.append(s)
+    p = mp.mpc(1)
+    for v in x:
+        p *= v
+    out.append(p - 1)
+    return out
+
+
+@pytest.mark.parametrize("n", [4, 9, 16])
+def test_start_point_on_backelin_set(n):
+    mpmath.mp.prec = 200
+    F, G, gam, x0 = synth.cyclic_monodromy(3, n)
+    xm = [mpmath.mpc(float(z.real), float(z.imag)) for z in x0]
+    res = max(abs(v) for v in _cyclic_mp(xm))
+    assert float(res) < 50 * n * 2.0 ** -53, float(res)
+
+
+def _cyclic_jacobian(x):
+    n = len(x)
+    J = np.zeros((n, n), dtype=np.complex128)
+    for i in range(1, n):                       # f_i: windows of length i
+        for j in range(n):
+            idx = [(j + k) % n for k in range(i)]
+            for q in idx:
+                J[i - 1, q] += np.prod([x[r] for r in idx if r != q])
+    for q in range(n):
+        J[n - 1, q] = np.prod([x[r] for r in range(n) if r != q])
+    return J
+
+
+@pytest.mark.parametrize("m", [2, 3, 4])
+def test_solution_set_dimension(m):
+    n = m * m
+    _, _, _, x0 = synth.cyclic_monodromy(5, n)
+    s = np.linalg.svd(_cyclic_jacobian(x0), compute_uv=False)
+    assert np.all(s[-(m - 1):] < 1e-11 * s[0]), s
+    assert s[-m] > 1e-4 * s[0], s
+
+
+@pytest.mark.parametrize("L", [2, 4])
+def test_start_slices_pass_through_x0(L):
+    n, m = 16, 4
+    F, G, gam, x0 = synth.cyclic_monodromy(1, n)
+    assert (F.N, F.n, G.N) == (n + m - 1, n, n + m - 1)
+    xs = np.zeros((L, 2, n))
+    xs[0, 0], xs[0, 1] = x0.real, x0.imag
+    h, _ = oracle.eval_h(oracle.System(G, L), xs)
+    hv = h[0, 0] + 1j * h[0, 1]
+    assert np.abs(hv[:n]).max() < 50 * n * 2.0 ** -53
+    # the slice rows: DD/QD evaluation of an exact sum: rounding of DD only
+    assert np.abs(hv[n:]).max() < 1e-28
+    h, _ = oracle.eval_h(oracle.System(F, L), xs)
+    assert np.abs(h[0, 0, n:] + 1j * h[0, 1, n:]).min() > 1e-3     # K does not
