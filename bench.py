@@ -212,7 +212,7 @@ CONTROL = {"control": 0}       # 1: host-side step control (for profiling runs)
 # DRAM bytes (read + write) of one k_mgs<DD> launch on the dense64 DD system,
 # from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # current kernel: the 64 x 65 matrix and the projection coefficients, read once.
-MGS_DENSE64_DD_TRAFFIC = 266240
+MGS_DENSE64_DD_TRAFFIC = 269568
 
 
 def seg_params(wl):
@@ -479,6 +479,10 @@ def monodromy_leg(libph, synth, ctx, torch, dev, seed, segment):
             e1.record(stream)
             e1.synchronize()
             ms = e0.elapsed_time(e1)
+            # one corrector iteration's kernels at the path's end point
+            tl = torch.zeros(L, dtype=torch.float64, device=dev)
+            tl[0] = sd["t_final"]
+            kms = libph.ph_profile_newton(ctx.h, f, g, dg, 1, tl, xo, 3)
             ps, pm, pcpu, pgpu = PAPER_CYCLIC_PATH[(n, L)]
             per_step = ms / max(1, sd["steps"])
             out[f"cyclic{n}_{name}"] = {
@@ -486,6 +490,7 @@ def monodromy_leg(libph, synth, ctx, torch, dev, seed, segment):
                 "t_final": sd["t_final"], "steps": sd["steps"], "accepted": sd["accepted"],
                 "newton_iters": sd["newton_iters"], "ms": ms, "ms_per_step": per_step,
                 "ms_per_newton_iter": ms / max(1, sd["newton_iters"]),
+                "kernel_ms": dict(zip(["prep", "monomial_ad", "summation", "mgs"], kms)),
                 "paper_k20c": {"success": ps, "steps": pm, "gpu_s": pgpu, "cpu_s": pcpu,
                                "ms_per_step": 1e3 * pgpu / pm},
                 "per_step_vs_paper": (1e3 * pgpu / pm) / per_step}
@@ -608,6 +613,32 @@ def summarize(ms, stats):
     }
 
 
+def mgs_case(spec: str) -> None:
+    """--only-mgs L,N,n,reps: `reps` least-squares solves (ph_mgs_solve, host
+    buffers) of one seeded N x n complex matrix with L limbs, then one JSON
+    line with the variant the library chose and both variants' measured times.
+    A fixed, small launch sequence for kernel profiles: the first solve of a
+    shape times 4 launches of each variant, then every solve is one launch."""
+    from paper_1501_06625_gb300 import libph
+    L, N, n, reps = (int(v) for v in spec.split(","))
+    rng = np.random.default_rng(N * 7919 + n)
+    A = rng.standard_normal((N, n)) + 1j * rng.standard_normal((N, n)) + 2 * np.eye(N, n)
+    b = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    J = np.zeros((L, 2, n, N))
+    J[0, 0], J[0, 1] = A.T.real, A.T.imag
+    rhs = np.zeros((L, 2, N))
+    rhs[0, 0], rhs[0, 1] = b.real, b.imag
+    dx = np.zeros((L, 2, n))
+    ctx = libph.Context(0)
+    for _ in range(reps):
+        libph.ph_mgs_solve(ctx.h, L, N, n, J, rhs, dx)
+    cl, ms_grid, ms_cluster = libph.ph_mgs_variant(ctx.h, L, N, n)
+    ctx.close()
+    print(json.dumps({"mgs_case": {"L": L, "N": N, "n": n, "solves": reps,
+                                   "cluster": cl, "ms_grid": ms_grid,
+                                   "ms_cluster": ms_cluster}}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -631,6 +662,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=384,
                     help="requests of the serving leg (0 skips it)")
     ap.add_argument("--no-cyclic", action="store_true", help="skip the cyclic n-roots legs")
+    ap.add_argument("--only-mgs", default=None, metavar="L,N,n,reps",
+                    help="only time least-squares solves of one shape (for kernel profiles)")
     ap.add_argument("--monodromy-segment", type=int, default=40,
                     help="steps of the cyclic monodromy paths not tracked whole")
     ap.add_argument("--no-sparse", action="store_true",
@@ -640,6 +673,10 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.only_mgs:
+        from paper_1501_06625_gb300 import build
+        build.build()
+        return mgs_case(args.only_mgs)
     CONTROL["control"] = 1 if args.control == "host" else 0
 
     import torch
