@@ -499,6 +499,52 @@ def monodromy_leg(libph, synth, ctx, torch, dev, seed, segment):
     return out
 
 
+def monodromy_loops_leg(libph, synth, ctx, seed, loops, single):
+    """Many monodromy loops at once, the form the paper's degree computation
+    needs (each loop a path with its own random slices and constant): `loops`
+    independent cyclic n-roots monodromy paths (synth.cyclic_monodromy with
+    seeds seed*1000 + i, each its own pair of loaded systems), submitted at once
+    to the serving loop (one persistent block per path, ph_server_*), whole
+    paths, the same Newton budget and tolerances as the single-path leg.
+    Against `single`, the single-path form's ms per path of the first loop."""
+    out = {}
+    newton = {2: 5, 4: 6}
+    for n, L, name in ((16, 4, "qd"), (16, 2, "dd")):
+        key = f"cyclic{n}_{name}"
+        if single is None or key not in single:
+            continue
+        params = synth.default_params(L, max_newton=newton[L], max_steps=5000)
+        jobs = []
+        for i in range(loops):
+            F, G, gam, x0 = synth.cyclic_monodromy(seed * 1000 + i, n)
+            f, g = ctx.load(F, L), ctx.load(G, L)
+            xs = np.zeros((L, 2, n))
+            xs[0, 0], xs[0, 1] = x0.real, x0.imag
+            gs = np.zeros((L, 2))
+            gs[0] = [gam.real, gam.imag]
+            jobs.append((f, g, gs, xs))
+        srv = libph.ph_server_create(ctx.h, max_n=n, pool_bytes=8 << 30, queue_cap=2 * loops)
+        try:
+            t0 = time.perf_counter()
+            ids = [libph.ph_server_submit(ctx.h, srv, f, g, gs, xs, params)
+                   for f, g, gs, xs in jobs]
+            stats = [libph.ph_server_wait(ctx.h, srv, j, 600000)[0] for j in ids]
+            wall = time.perf_counter() - t0
+        finally:
+            libph.ph_server_destroy(srv)
+        for f, g, _, _ in jobs:
+            ctx.free(f)
+            ctx.free(g)
+        ok = sum(1 for x in stats if x["status"] == libph.PH_OK)
+        rate = loops / wall
+        one = 1e3 / single[key]["ms"]
+        out[key] = {"loops": loops, "wall_s": wall, "paths_per_s": rate, "succeeded": ok,
+                    "steps": sum(x["steps"] for x in stats),
+                    "newton_iters": sum(x["newton_iters"] for x in stats),
+                    "single_path_per_s": one, "vs_single_path": rate / one}
+    return out
+
+
 def serve_leg(libph, synth, ctx, nreq, seed, lin=0, seq_rate=None):
     """A stream of path-tracking requests through the continuous-batching loop
     (ph_server_*).  A pool of 16 systems per (recipe, precision): n =
@@ -666,6 +712,8 @@ def main():
                     help="only time least-squares solves of one shape (for kernel profiles)")
     ap.add_argument("--monodromy-segment", type=int, default=40,
                     help="steps of the cyclic monodromy paths not tracked whole")
+    ap.add_argument("--monodromy-loops", type=int, default=152,
+                    help="monodromy loops tracked at once through the serving loop (0 skips)")
     ap.add_argument("--no-sparse", action="store_true",
                     help="skip the n=512 QD solver roofline measurement")
     args = ap.parse_args()
@@ -773,6 +821,9 @@ def main():
         cyclic = cyclic_leg(libph, synth, ctx, torch, dev, peak)
         monodromy = monodromy_leg(libph, synth, ctx, torch, dev, args.seed,
                                   args.monodromy_segment)
+        if args.monodromy_loops > 0:
+            monodromy["loops_in_flight"] = monodromy_loops_leg(
+                libph, synth, ctx, args.seed, args.monodromy_loops, monodromy)
 
     precision = None
     if args.precision_paths > 0 and rank == 0:

@@ -82,3 +82,23 @@ def test_monodromy_path_ends_on_the_component(ctx, L, newton):
     assert _family_gap(x, L) < 1e3 * U[L]
     h, _ = oracle.eval_h(oracle.System(F, L), x)
     assert np.abs(lead_complex(h)).max() < 1e3 * params["tol_res"]
+
+
+def test_monodromy_loop_through_the_serving_loop(ctx):
+    """The same loop as a serving job (one block, per-block MGS on the 19 x 16
+    least-squares systems): it ends where the single-path form ends."""
+    L = 2
+    F, G, gs, xs, params = _mono(L, max_steps=3000, max_newton=5)
+    f, g = ctx.load(F, L), ctx.load(G, L)
+    x1 = np.zeros_like(xs)
+    st, s1, _ = libph.ph_track_path(ctx.h, f, g, gs, xs, params, x1)
+    assert st == libph.PH_OK
+    srv = libph.ph_server_create(ctx.h, max_n=16, pool_bytes=1 << 26, queue_cap=4)
+    try:
+        jid = libph.ph_server_submit(ctx.h, srv, f, g, gs, xs, params)
+        x2 = np.zeros_like(xs)
+        s2, _ = libph.ph_server_wait(ctx.h, srv, jid, 60000, x2)
+    finally:
+        libph.ph_server_destroy(srv)
+    assert s2["status"] == libph.PH_OK and s2["t_final"] == 1.0
+    assert cabs_diff(x1, x2).max() <= 1e3 * params["tol_dx"]
