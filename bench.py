@@ -449,18 +449,24 @@ def monodromy_leg(libph, synth, ctx, torch, dev, seed, segment):
     equations corrected by least squares, from a start point of Backelin's
     family (synth.cyclic_monodromy).  D, DD and QD with 3 / 5 / 6 Newton
     iterations per step and the library's default tolerances.  Whole paths
-    where they take seconds; elsewhere the first `segment` steps.  Each run is
-    timed with CUDA events around one ph_track_path call, after an untimed
-    call that builds its step graph.  The comparison with the paper is per
-    predictor-corrector step: the paper's tolerances and Newton budget are not
-    stated, so the step counts of whole paths differ."""
+    for n <= 64; at n = 144 the first `segment` steps.  Each run is timed with
+    CUDA events around one ph_track_path call, after an untimed call that
+    builds its step graph (except the n = 64 QD path, timed in one call).
+    Compared with the paper per predictor-corrector step and, for whole paths,
+    per path: the paper's tolerances and Newton budget are not stated, so the
+    step counts differ.  F and G both hold the cyclic equations, so each
+    iteration evaluates them twice; the paper's homotopy evaluates them once."""
     out = {}
     newton = {1: 3, 2: 5, 4: 6}
     stream = torch.cuda.current_stream(dev)
     for n in (16, 64, 144):
         F, G, gam, x0 = synth.cyclic_monodromy(seed, n)
         for L, name in ((1, "d"), (2, "dd"), (4, "qd")):
-            whole = n == 16 or (n == 64 and L < 4)
+            whole = n <= 64
+            # a warm-up call (same parameters: it builds the step graph) where
+            # it is cheap; the QD path at n = 64 is timed in one call, the
+            # graph's construction (tens of ms) inside its seconds
+            warm = not (n == 64 and L == 4)
             params = synth.default_params(L, max_newton=newton[L],
                                           max_steps=5000 if whole else segment - 1)
             f, g = ctx.load(F, L), ctx.load(G, L)
@@ -471,7 +477,8 @@ def monodromy_leg(libph, synth, ctx, torch, dev, seed, segment):
             dx0 = torch.tensor(xs, dtype=torch.float64, device=dev)
             dg = torch.tensor(gs, dtype=torch.float64, device=dev)
             xo = torch.empty_like(dx0)
-            libph.ph_track_path(ctx.h, f, g, dg, dx0, params, xo)        # builds the graph
+            if warm:
+                libph.ph_track_path(ctx.h, f, g, dg, dx0, params, xo)    # builds the graph
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -486,7 +493,8 @@ def monodromy_leg(libph, synth, ctx, torch, dev, seed, segment):
             ps, pm, pcpu, pgpu = PAPER_CYCLIC_PATH[(n, L)]
             per_step = ms / max(1, sd["steps"])
             out[f"cyclic{n}_{name}"] = {
-                "N": F.N, "n": n, "whole_path": whole, "status": int(st),
+                "N": F.N, "n": n, "whole_path": whole, "graph_built_in_timing": not warm,
+                "status": int(st),
                 "t_final": sd["t_final"], "steps": sd["steps"], "accepted": sd["accepted"],
                 "newton_iters": sd["newton_iters"], "ms": ms, "ms_per_step": per_step,
                 "ms_per_newton_iter": ms / max(1, sd["newton_iters"]),
@@ -494,6 +502,8 @@ def monodromy_leg(libph, synth, ctx, torch, dev, seed, segment):
                 "paper_k20c": {"success": ps, "steps": pm, "gpu_s": pgpu, "cpu_s": pcpu,
                                "ms_per_step": 1e3 * pgpu / pm},
                 "per_step_vs_paper": (1e3 * pgpu / pm) / per_step}
+            if whole and st == libph.PH_OK:
+                out[f"cyclic{n}_{name}"]["per_path_vs_paper"] = 1e3 * pgpu / ms
             ctx.free(f)
             ctx.free(g)
     return out
@@ -540,6 +550,7 @@ def monodromy_loops_leg(libph, synth, ctx, seed, loops, single):
         one = 1e3 / single[key]["ms"]
         out[key] = {"loops": loops, "wall_s": wall, "paths_per_s": rate, "succeeded": ok,
                     "steps": sum(x["steps"] for x in stats),
+                    "longest_path_steps": max(x["steps"] for x in stats),
                     "newton_iters": sum(x["newton_iters"] for x in stats),
                     "single_path_per_s": one, "vs_single_path": rate / one}
     return out
@@ -685,6 +696,44 @@ def mgs_case(spec: str) -> None:
                                    "ms_cluster": ms_cluster}}))
 
 
+def monodromy_paths_case(spec: str) -> None:
+    """--only-monodromy-paths n,L,paths,steps: one ph_track_paths call (one
+    kernel launch) over `paths` copies of the first cyclic n-roots monodromy
+    loop, `steps` predictor-corrector steps each, twice; one JSON line with the
+    event-timed ms of the second call.  A single long launch for profiles of
+    the per-block path kernel on a system with long terms and N > n."""
+    import torch
+    from paper_1501_06625_gb300 import libph, synth
+    n, L, paths, steps = (int(v) for v in spec.split(","))
+    F, G, gam, x0 = synth.cyclic_monodromy(1, n)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    ctx = libph.Context(0, stream=stream)
+    f, g = ctx.load(F, L), ctx.load(G, L)
+    xs = np.zeros((paths, L, 2, n))
+    xs[:, 0, 0], xs[:, 0, 1] = x0.real, x0.imag
+    gs = np.zeros((L, 2))
+    gs[0] = [gam.real, gam.imag]
+    bx = torch.tensor(xs, dtype=torch.float64, device=dev)
+    bo = torch.empty_like(bx)
+    bg = torch.tensor(gs, dtype=torch.float64, device=dev)
+    params = synth.default_params(L, max_newton=5 if L == 2 else 6, max_steps=steps - 1)
+    ms = 0.0
+    for _ in range(2):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st, _ = libph.ph_track_paths(ctx.h, f, g, bg, bx, params, bo)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+    it = sum(x["newton_iters"] for x in st)
+    ctx.close()
+    print(json.dumps({"monodromy_paths_case": {"n": n, "L": L, "paths": paths, "steps": steps,
+                                               "ms": ms, "newton_iters": it,
+                                               "ms_per_iter_per_path": ms * paths / max(1, it)}}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -710,6 +759,8 @@ def main():
     ap.add_argument("--no-cyclic", action="store_true", help="skip the cyclic n-roots legs")
     ap.add_argument("--only-mgs", default=None, metavar="L,N,n,reps",
                     help="only time least-squares solves of one shape (for kernel profiles)")
+    ap.add_argument("--only-monodromy-paths", default=None, metavar="n,L,paths,steps",
+                    help="only time one many-path launch on a monodromy loop (for kernel profiles)")
     ap.add_argument("--monodromy-segment", type=int, default=40,
                     help="steps of the cyclic monodromy paths not tracked whole")
     ap.add_argument("--monodromy-loops", type=int, default=152,
@@ -721,10 +772,12 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
-    if args.only_mgs:
+    if args.only_mgs or args.only_monodromy_paths:
         from paper_1501_06625_gb300 import build
         build.build()
-        return mgs_case(args.only_mgs)
+        if args.only_mgs:
+            return mgs_case(args.only_mgs)
+        return monodromy_paths_case(args.only_monodromy_paths)
     CONTROL["control"] = 1 if args.control == "host" else 0
 
     import torch
