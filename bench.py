@@ -454,8 +454,9 @@ def monodromy_leg(libph, synth, ctx, torch, dev, seed, segment):
     builds its step graph (except the n = 64 QD path, timed in one call).
     Compared with the paper per predictor-corrector step and, for whole paths,
     per path: the paper's tolerances and Newton budget are not stated, so the
-    step counts differ.  F and G both hold the cyclic equations, so each
-    iteration evaluates them twice; the paper's homotopy evaluates them once."""
+    step counts differ.  The paper's homotopy {f = 0, alpha (1-t) L + t K = 0}:
+    F = [f; K], G = [0; L] with the cyclic rows held fixed (fixed_rows), so f
+    is evaluated once per iteration."""
     out = {}
     newton = {1: 3, 2: 5, 4: 6}
     stream = torch.cuda.current_stream(dev)
@@ -467,7 +468,7 @@ def monodromy_leg(libph, synth, ctx, torch, dev, seed, segment):
             # it is cheap; the QD path at n = 64 is timed in one call, the
             # graph's construction (tens of ms) inside its seconds
             warm = not (n == 64 and L == 4)
-            params = synth.default_params(L, max_newton=newton[L],
+            params = synth.default_params(L, max_newton=newton[L], fixed_rows=1,
                                           max_steps=5000 if whole else segment - 1)
             f, g = ctx.load(F, L), ctx.load(G, L)
             xs = np.zeros((L, 2, n))
@@ -523,7 +524,7 @@ def monodromy_loops_leg(libph, synth, ctx, seed, loops, single):
         key = f"cyclic{n}_{name}"
         if single is None or key not in single:
             continue
-        params = synth.default_params(L, max_newton=newton[L], max_steps=5000)
+        params = synth.default_params(L, max_newton=newton[L], max_steps=5000, fixed_rows=1)
         jobs = []
         for i in range(loops):
             F, G, gam, x0 = synth.cyclic_monodromy(seed * 1000 + i, n)
@@ -717,7 +718,8 @@ def monodromy_paths_case(spec: str) -> None:
     bx = torch.tensor(xs, dtype=torch.float64, device=dev)
     bo = torch.empty_like(bx)
     bg = torch.tensor(gs, dtype=torch.float64, device=dev)
-    params = synth.default_params(L, max_newton=5 if L == 2 else 6, max_steps=steps - 1)
+    params = synth.default_params(L, max_newton=5 if L == 2 else 6, max_steps=steps - 1,
+                                  fixed_rows=1)
     ms = 0.0
     for _ in range(2):
         e0 = torch.cuda.Event(enable_timing=True)

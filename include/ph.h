@@ -156,7 +156,12 @@ typedef struct {
    * 1 (its step graph holds both kernel sets, one of them gated off per
    * iteration). */
   int32_t lin_prec;
-  int32_t reserved;   /* 0                                                        */
+  /* 1 (with an explicit start system g): every row i where g_i is the zero
+   * polynomial (no terms) is held fixed, h_i = f_i instead of t^k f_i.  This
+   * is the monodromy homotopy of Section 4.2, {f = 0, alpha (1-t) L + t K = 0}:
+   * target [f; K], start [0; L], gamma = alpha; f is evaluated once.  0: every
+   * row moves.  PH_EINVAL with the total-degree start system. */
+  int32_t fixed_rows;
   double endgame_t;   /* <= 0: 1.0 (only the step that lands on t = 1)           */
   double cond_f32;    /* threshold of lin_prec 3; <= 0: 1e3                       */
 } ph_track_params;

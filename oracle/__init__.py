@@ -55,7 +55,7 @@ class Params(C.Structure):
     _fields_ = [("max_dt", C.c_double), ("min_dt", C.c_double), ("tol_res", C.c_double),
                 ("tol_dx", C.c_double), ("max_res", C.c_double), ("max_x", C.c_double),
                 ("max_steps", C.c_int32), ("max_newton", C.c_int32), ("pred_order", C.c_int32),
-                ("relax_k", C.c_int32), ("fixed_steps", C.c_int32), ("reserved", C.c_int32)]
+                ("relax_k", C.c_int32), ("fixed_steps", C.c_int32), ("fixed_rows", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -90,7 +90,8 @@ def lib():
                                          C.POINTER(C.c_void_p)]
             L.orc_system_free.argtypes = [C.c_void_p]
             L.orc_system_degree.argtypes = [C.c_void_p, C.c_int]
-            L.orc_eval.argtypes = [C.c_void_p, C.c_void_p, _dp, C.c_int, _dp, _dp, _dp, _dp]
+            L.orc_eval.argtypes = [C.c_void_p, C.c_void_p, _dp, C.c_int, _dp, _dp, _dp, _dp,
+                                   C.c_int]
             L.orc_mgs_solve.argtypes = [C.c_int, C.c_int, C.c_int, _dp, _dp, _dp, _dp, _dp, _dp]
             L.orc_predict.argtypes = [C.c_int, C.c_int, C.c_int, _dp, _dp, C.c_double, _dp]
             L.orc_newton.argtypes = [C.c_void_p, C.c_void_p, _dp, C.c_int, C.c_double, _dp,
@@ -208,9 +209,11 @@ def _real_limbs(t, L):
     return out
 
 
-def eval_h(f: System, x, t=1.0, gamma=None, k: int = 1, g: System | None = None):
+def eval_h(f: System, x, t=1.0, gamma=None, k: int = 1, g: System | None = None,
+           fixed_rows: int = 0):
     """Values h [L][2][N] and Jacobian J [L][2][n][N] of gamma (1-t)^k g + t^k f
-    (f alone when gamma is None)."""
+    (f alone when gamma is None); with fixed_rows, rows where g has no terms
+    are f's rows unchanged."""
     L = f.L
     x = _f64(x)
     gm = _gamma(gamma, L)
@@ -218,7 +221,7 @@ def eval_h(f: System, x, t=1.0, gamma=None, k: int = 1, g: System | None = None)
     h = np.zeros((L, 2, f.N))
     J = np.zeros((L, 2, f.n, f.N))
     st = lib().orc_eval(f.h, g.h if g else None, _d(gm) if gm is not None else None, k,
-                        _d(tl), _d(x), _d(h), _d(J))
+                        _d(tl), _d(x), _d(h), _d(J), int(fixed_rows))
     if st != OK:
         raise ValueError(f"oracle eval failed: {STATUS_NAMES[st]}")
     return h, J

@@ -144,7 +144,7 @@ int orc_newton_mixed(const orc_system *f, const orc_system *g, const double *gam
   *iters = 0;
   *updates = 0;
   for (int it = 0; it < p->max_newton; it++) {
-    orc_eval(f, g, gamma, k, tl, x, h, J);
+    orc_eval(f, g, gamma, k, tl, x, h, J, p->fixed_rows);
     (*iters)++;
     /* the residual norm from the leading limbs (limb 0 re at [0][0], im at [0][1]) */
     double r = max_mag_lead(h, N);

@@ -78,9 +78,11 @@ void orc_system_free(orc_system *s);
 int  orc_system_degree(const orc_system *s, int i);
 
 /* h(x,t) = gamma (1-t)^k g(x) + t^k f(x) and its Jacobian.  g == NULL means the
-   total-degree start system g_i = x_i^{d_i} - 1.  gamma == NULL evaluates f alone. */
+   total-degree start system g_i = x_i^{d_i} - 1.  gamma == NULL evaluates f alone.
+   fixed != 0 (with g): a row where g has no terms is f's row unchanged (the
+   monodromy homotopy of Section 4.2 holds the cyclic equations fixed). */
 int orc_eval(const orc_system *f, const orc_system *g, const double *gamma, int k,
-             const double *t, const double *x, double *h, double *J);
+             const double *t, const double *x, double *h, double *J, int fixed);
 
 /* ---- modified Gram-Schmidt least squares --------------------------------- */
 /* Textbook MGS on the augmented N x (n+1) matrix [J | rhs]; Q (N x n) and the
@@ -92,7 +94,8 @@ int orc_mgs_solve(int L, int N, int n, const double *J, const double *rhs, doubl
 /* ---- predictor, corrector, path tracker ----------------------------------- */
 typedef struct {
   double max_dt, min_dt, tol_res, tol_dx, max_res, max_x;
-  int32_t max_steps, max_newton, pred_order, relax_k, fixed_steps, reserved;
+  int32_t max_steps, max_newton, pred_order, relax_k, fixed_steps;
+  int32_t fixed_rows;   /* rows where g has no terms are held fixed: h_i = f_i */
 } orc_params;
 
 typedef struct {

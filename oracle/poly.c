@@ -134,7 +134,7 @@ static void eval_total_degree(const orc_system *f, const orc_cplx *x, orc_cplx *
 }
 
 int orc_eval(const orc_system *f, const orc_system *g, const double *gamma, int k,
-             const double *t, const double *x, double *h, double *J) {
+             const double *t, const double *x, double *h, double *J, int fixed) {
   int L = f->L, N = f->N, n = f->n;
   if (k < 0) return ORC_EINVAL;
   if (g && (g->L != L || g->N != N || g->n != n)) return ORC_EINVAL;
@@ -172,12 +172,18 @@ int orc_eval(const orc_system *f, const orc_system *g, const double *gamma, int 
     }
     orc_cplx gam = orc_c_load(L, gamma, 1, 0);
     orc_cplx sg = orc_c_mul_real(L, gam, omtk);
+    /* a row held fixed (g has no terms there): f's row as it is */
     for (int i = 0; i < N; i++) {
-      orc_cplx v = orc_c_add(L, orc_c_mul(L, sg, gv[i]), orc_c_mul_real(L, fv[i], tk));
+      int hold = fixed && g && g->term_ptr[i + 1] == g->term_ptr[i];
+      orc_cplx v = hold ? fv[i]
+                        : orc_c_add(L, orc_c_mul(L, sg, gv[i]), orc_c_mul_real(L, fv[i], tk));
       orc_c_store(L, h, N, i, v);
     }
     for (long e = 0; e < NN; e++) {
-      orc_cplx v = orc_c_add(L, orc_c_mul(L, sg, Jg[e]), orc_c_mul_real(L, Jf[e], tk));
+      int i = (int)(e % N);                     /* J is [column j][row i] */
+      int hold = fixed && g && g->term_ptr[i + 1] == g->term_ptr[i];
+      orc_cplx v = hold ? Jf[e]
+                        : orc_c_add(L, orc_c_mul(L, sg, Jg[e]), orc_c_mul_real(L, Jf[e], tk));
       orc_c_store(L, J, NN, e, v);
     }
   }

@@ -76,7 +76,7 @@ int orc_newton(const orc_system *f, const orc_system *g, const double *gamma, in
   *iters = 0;
   *updates = 0;
   for (int it = 0; it < p->max_newton; it++) {
-    orc_eval(f, g, gamma, k, tl, x, h, J);
+    orc_eval(f, g, gamma, k, tl, x, h, J, p->fixed_rows);
     (*iters)++;
     double r = max_mag(L, h, N);
     *res = r;

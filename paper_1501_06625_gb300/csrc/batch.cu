@@ -93,6 +93,7 @@ void ph_job_fill_system(Job &j, const ph_system *f, const ph_system *g) {
     j.nvg = g->nv.as<int32_t>(); j.vidxg = g->vidx.as<int32_t>(); j.vexpg = g->vexp.as<int32_t>();
     j.optrg = g->out_ptr.as<int32_t>(); j.oslotg = g->out_slot.as<int32_t>();
     j.coeff_g = g->coeff.as<double>();
+    j.zrows_g = g->zero_rows.as<uint8_t>();
     j.nsg = (long)(g->maxv + 1) * g->Mp;
   }
   j.ldA = ph_lda(f->N);
@@ -119,6 +120,7 @@ extern "C" ph_status ph_track_paths(ph_ctx *ctx, const ph_system *f, const ph_sy
   const ph_track_params p = *params;
   if (p.max_newton < 1 || p.max_newton > 64 || p.pred_order < 0 || p.pred_order > 8 ||
       p.relax_k < 1 || p.relax_k > 64 || p.max_steps < 0 || p.lin_prec < 0 || p.lin_prec > 3 ||
+      p.fixed_rows < 0 || p.fixed_rows > 1 || (p.fixed_rows && !g) ||
       (p.fixed_steps <= 0 && !(p.max_dt > 0.0 && p.min_dt > 0.0 && p.min_dt <= p.max_dt)))
     return ph_fail(ctx, PH_EINVAL, "ph_track_paths: invalid parameters");
   if (!g) {

@@ -175,14 +175,14 @@ __global__ void __launch_bounds__(256) k_sum(
     const double *__restrict__ spow, const double *__restrict__ scal, int homotopy,
     double *__restrict__ J, long ldJ, long Jplane, double *__restrict__ h,
     double *__restrict__ rhs, long rhs_plane, unsigned long long *__restrict__ res_bits,
-    const int *__restrict__ skip, int o0, int lead_rhs) {
+    const int *__restrict__ skip, int o0, int lead_rhs, const uint8_t *__restrict__ fixed) {
   if (skip && *skip) return;
   long gt = (long)blockIdx.x * blockDim.x + threadIdx.x;
   int o = o0 + (int)(gt / G);
   int lane = (int)(gt % G);
   bool active = o < nout;
   cx<P> val = sum_output<P, G>(active, o, lane, N, n, optr, oslot, slots, nslots, goptr, goslot,
-                               gslots, gnslots, spow, scal, homotopy);
+                               gslots, gnslots, spow, scal, homotopy, fixed);
   if (!active || lane != 0) return;
   const int nN = n * N;
   if (o < nN) {
@@ -234,12 +234,12 @@ void sum_launch_g(const ph_system *f, const ph_system *g, int N, int n, const do
                   long fs, const double *gslots, long gs, const double *spow, const double *scal,
                   int homotopy, double *J, long ldJ, long Jplane, double *h, double *rhs,
                   long rhs_plane, unsigned long long *res_bits, const int *skip, cudaStream_t st,
-                  int o0, int lead_rhs) {
+                  int o0, int lead_rhs, const uint8_t *fixed) {
   const long threads = (long)(f->nout - o0) * G;
   k_sum<P, G><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
       N, n, f->nout, f->out_ptr.as<int32_t>(), f->out_slot.as<int32_t>(), fslots, fs,
       g ? g->out_ptr.as<int32_t>() : nullptr, g ? g->out_slot.as<int32_t>() : nullptr, gslots, gs,
-      spow, scal, homotopy, J, ldJ, Jplane, h, rhs, rhs_plane, res_bits, skip, o0, lead_rhs);
+      spow, scal, homotopy, J, ldJ, Jplane, h, rhs, rhs_plane, res_bits, skip, o0, lead_rhs, fixed);
 }
 
 constexpr int kSumLanes[6] = {1, 2, 4, 8, 16, 32};
@@ -249,11 +249,11 @@ void sum_launch(int G, const ph_system *f, const ph_system *g, int N, int n, con
                 long fs, const double *gslots, long gs, const double *spow, const double *scal,
                 int homotopy, double *J, long ldJ, long Jplane, double *h, double *rhs,
                 long rhs_plane, unsigned long long *res_bits, const int *skip, cudaStream_t st,
-                int o0 = 0, int lead_rhs = 0) {
+                int o0 = 0, int lead_rhs = 0, const uint8_t *fixed = nullptr) {
 #define PH_SUM_CASE(g_)                                                                          \
   case g_:                                                                                       \
     sum_launch_g<P, g_>(f, g, N, n, fslots, fs, gslots, gs, spow, scal, homotopy, J, ldJ,        \
-                        Jplane, h, rhs, rhs_plane, res_bits, skip, st, o0, lead_rhs);             \
+                        Jplane, h, rhs, rhs_plane, res_bits, skip, st, o0, lead_rhs, fixed);      \
     break;
   switch (G) {
     PH_SUM_CASE(1)
@@ -263,7 +263,7 @@ void sum_launch(int G, const ph_system *f, const ph_system *g, int N, int n, con
     PH_SUM_CASE(32)
     default:
       sum_launch_g<P, 8>(f, g, N, n, fslots, fs, gslots, gs, spow, scal, homotopy, J, ldJ, Jplane,
-                         h, rhs, rhs_plane, res_bits, skip, st, o0, lead_rhs);
+                         h, rhs, rhs_plane, res_bits, skip, st, o0, lead_rhs, fixed);
   }
 #undef PH_SUM_CASE
 }
@@ -325,7 +325,7 @@ template <class P>
 cudaError_t eval_impl(ph_ctx *ctx, const ph_system *f, const ph_system *g, const double *gamma,
                       int k, const double *t, const double *x, double *h, double *J, long ldJ,
                       long Jplane, double *rhs, long rhs_plane, const int *skip,
-                      unsigned long long *res_bits, int parts) {
+                      unsigned long long *res_bits, int parts, const uint8_t *fixed) {
   const int L = P::L, n = f->n, N = f->N;
   int emax = f->emax;
   if (g && g->emax > emax) emax = g->emax;
@@ -353,7 +353,8 @@ cudaError_t eval_impl(ph_ctx *ctx, const ph_system *f, const ph_system *g, const
   if (parts & 4) {
     tune_sum<P>(ctx, f, g);
     sum_launch<P>(f->sum_lanes > 0 ? f->sum_lanes : 8, f, g, N, n, fslots, fs, gslots, gs, spow,
-                  scal, gamma != nullptr, J, ldJ, Jplane, h, rhs, rhs_plane, res_bits, skip, st);
+                  scal, gamma != nullptr, J, ldJ, Jplane, h, rhs, rhs_plane, res_bits, skip, st,
+                  0, 0, fixed);
   }
   return cudaGetLastError();
 }
@@ -366,7 +367,7 @@ template <class P>
 cudaError_t eval_values_impl(ph_ctx *ctx, const ph_system *f, const ph_system *g,
                              const double *gamma, int k, const double *t, const double *x,
                              double *rhs, long rhs_plane, const int *skip,
-                             unsigned long long *res_bits) {
+                             unsigned long long *res_bits, const uint8_t *fixed) {
   const int L = P::L, n = f->n, N = f->N;
   int emax = f->emax;
   if (g && g->emax > emax) emax = g->emax;
@@ -397,7 +398,7 @@ cudaError_t eval_values_impl(ph_ctx *ctx, const ph_system *f, const ph_system *g
   tune_sum<P>(ctx, f, g);
   sum_launch<P>(f->sum_lanes > 0 ? f->sum_lanes : 8, f, g, N, n, fslots, fs, gslots, gs, spow,
                 scal, gamma != nullptr, nullptr, 0, 0, nullptr, rhs, rhs_plane, res_bits, skip, st,
-                n * N, 1);
+                n * N, 1, fixed);
   return cudaGetLastError();
 }
 
@@ -406,12 +407,12 @@ cudaError_t eval_values_impl(ph_ctx *ctx, const ph_system *f, const ph_system *g
 cudaError_t ph_eval_values_launch(ph_ctx *ctx, const ph_system *f, const ph_system *g,
                                   const double *gamma, int k, const double *t, const double *x,
                                   double *rhs, long rhs_plane, const int *skip,
-                                  unsigned long long *res_bits) {
+                                  unsigned long long *res_bits, const uint8_t *fixed) {
   if (f->L == 1)
-    return eval_values_impl<F64>(ctx, f, g, gamma, k, t, x, rhs, rhs_plane, skip, res_bits);
+    return eval_values_impl<F64>(ctx, f, g, gamma, k, t, x, rhs, rhs_plane, skip, res_bits, fixed);
   if (f->L == 2)
-    return eval_values_impl<DD>(ctx, f, g, gamma, k, t, x, rhs, rhs_plane, skip, res_bits);
-  return eval_values_impl<QD>(ctx, f, g, gamma, k, t, x, rhs, rhs_plane, skip, res_bits);
+    return eval_values_impl<DD>(ctx, f, g, gamma, k, t, x, rhs, rhs_plane, skip, res_bits, fixed);
+  return eval_values_impl<QD>(ctx, f, g, gamma, k, t, x, rhs, rhs_plane, skip, res_bits, fixed);
 }
 
 // The evaluation in IEEE double of a system loaded with more limbs: every
@@ -419,24 +420,25 @@ cudaError_t ph_eval_values_launch(ph_ctx *ctx, const ph_system *f, const ph_syst
 // first), the results are written in the one-limb layout.
 cudaError_t ph_eval_launch_f64(ph_ctx *ctx, const ph_system *f, const ph_system *g,
                                const double *gamma, int k, const double *t, const double *x,
-                               double *J, long ldJ, long Jplane, const int *skip) {
+                               double *J, long ldJ, long Jplane, const int *skip,
+                               const uint8_t *fixed) {
   return eval_impl<F64>(ctx, f, g, gamma, k, t, x, nullptr, J, ldJ, Jplane, nullptr, 0, skip,
-                        nullptr, 7);
+                        nullptr, 7, fixed);
 }
 
 cudaError_t ph_eval_launch_part(ph_ctx *ctx, const ph_system *f, const ph_system *g,
                                 const double *gamma, int k, const double *t, const double *x,
                                 double *h, double *J, long ldJ, long Jplane, double *rhs,
                                 long rhs_plane, const int *skip, unsigned long long *res_bits,
-                                int parts) {
+                                int parts, const uint8_t *fixed) {
   if (f->L == 1)
     return eval_impl<F64>(ctx, f, g, gamma, k, t, x, h, J, ldJ, Jplane, rhs, rhs_plane, skip,
-                          res_bits, parts);
+                          res_bits, parts, fixed);
   if (f->L == 2)
     return eval_impl<DD>(ctx, f, g, gamma, k, t, x, h, J, ldJ, Jplane, rhs, rhs_plane, skip,
-                         res_bits, parts);
+                         res_bits, parts, fixed);
   return eval_impl<QD>(ctx, f, g, gamma, k, t, x, h, J, ldJ, Jplane, rhs, rhs_plane, skip,
-                       res_bits, parts);
+                       res_bits, parts, fixed);
 }
 
 void ph_sum_tune(ph_ctx *ctx, const ph_system *f, const ph_system *g) {
@@ -461,7 +463,8 @@ extern "C" ph_status ph_sum_lanes(ph_ctx *ctx, const ph_system *f, const ph_syst
 cudaError_t ph_eval_launch(ph_ctx *ctx, const ph_system *f, const ph_system *g,
                            const double *gamma, int k, const double *t, const double *x,
                            double *h, double *J, long ldJ, long Jplane, double *rhs,
-                           long rhs_plane, const int *skip, unsigned long long *res_bits) {
+                           long rhs_plane, const int *skip, unsigned long long *res_bits,
+                           const uint8_t *fixed) {
   return ph_eval_launch_part(ctx, f, g, gamma, k, t, x, h, J, ldJ, Jplane, rhs, rhs_plane, skip,
-                             res_bits, 7);
+                             res_bits, 7, fixed);
 }

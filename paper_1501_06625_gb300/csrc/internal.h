@@ -92,6 +92,9 @@ struct ph_system {
   int nout = 0;                 // n*N Jacobian entries + N values
   int max_contrib = 0;          // longest summation list
   DevBuf poly, nv, vidx, vexp, coeff, deg, out_ptr, out_slot;
+  // one byte per polynomial: 1 if it has no terms (the rows a start system
+  // leaves to f when the tracker holds them fixed, ph_track_params.fixed_rows)
+  DevBuf zero_rows;
   // sorted terms [s0, s1) differentiated with `lanes` threads per monomial
   struct Bucket { int s0, s1, lanes; };
   std::vector<Bucket> buckets;
@@ -122,11 +125,12 @@ bool ph_is_device_ptr(const void *p);
 //   t: L limbs on the device; gamma: [2L] on the device or null (f alone)
 //   skip: device flag; the kernels do nothing while *skip != 0 (may be null)
 //   res_bits: max |h_i| (leading limbs, double bits) accumulated (may be null)
+//   fixed: one byte per row, rows held fixed (h_i = f_i), or null
 cudaError_t ph_eval_launch(ph_ctx *ctx, const ph_system *f, const ph_system *g,
                            const double *gamma, int k, const double *t, const double *x,
                            double *h, double *J, long ldJ, long Jplane,
                            double *rhs, long rhs_plane, const int *skip,
-                           unsigned long long *res_bits);
+                           unsigned long long *res_bits, const uint8_t *fixed = nullptr);
 
 // the same, launching only the kernels selected by `parts`
 // (1 = power table and factors, 2 = monomial AD, 4 = summation)
@@ -134,20 +138,21 @@ cudaError_t ph_eval_launch_part(ph_ctx *ctx, const ph_system *f, const ph_system
                                 const double *gamma, int k, const double *t, const double *x,
                                 double *h, double *J, long ldJ, long Jplane, double *rhs,
                                 long rhs_plane, const int *skip, unsigned long long *res_bits,
-                                int parts);
+                                int parts, const uint8_t *fixed = nullptr);
 
 // eval.cu: h alone in the working precision (no derivatives): -h's leading
 // limbs to rhs ([re|im], planes rhs_plane apart), max |h_i| to *res_bits.
 cudaError_t ph_eval_values_launch(ph_ctx *ctx, const ph_system *f, const ph_system *g,
                                   const double *gamma, int k, const double *t, const double *x,
                                   double *rhs, long rhs_plane, const int *skip,
-                                  unsigned long long *res_bits);
+                                  unsigned long long *res_bits, const uint8_t *fixed = nullptr);
 
 // eval.cu: the Jacobian alone in IEEE double from the leading limbs of every
 // input (x, t, gamma, the coefficients), in the one-limb layout.
 cudaError_t ph_eval_launch_f64(ph_ctx *ctx, const ph_system *f, const ph_system *g,
                                const double *gamma, int k, const double *t, const double *x,
-                               double *J, long ldJ, long Jplane, const int *skip);
+                               double *J, long ldJ, long Jplane, const int *skip,
+                               const uint8_t *fixed = nullptr);
 
 // eval.cu: the summation kernel's lanes per output for f (and g), measured
 // on the first evaluation outside a stream capture (called before a capture).

@@ -28,6 +28,7 @@ struct Job {
   const double *coeff_f;
   const int32_t *nvg, *vidxg, *vexpg, *optrg, *oslotg;    // null: total-degree start
   const double *coeff_g;
+  const uint8_t *zrows_g;         // g's rows without terms (held fixed when p.fixed_rows)
   const double *gamma;            // [2L]
   ph_track_params p;
   const double *x0;               // [2L][n]
@@ -219,7 +220,8 @@ __device__ int lowprec_solve(const Job &a, const double *x, const double *tl, co
     const int o = o0 + tid / kSG, lane = tid % kSG;
     const bool act = o < nN;
     cx<LP> val = sum_output<LP, kSG>(act, o, lane, N, n, a.optrf, a.oslotf, fslots, a.nsf,
-                                     a.optrg, a.oslotg, gslots, a.nsg, spow, scal, 1);
+                                     a.optrg, a.oslotg, gslots, a.nsg, spow, scal, 1,
+                                     a.p.fixed_rows ? a.zrows_g : nullptr);
     if (act && lane == 0) {
       const int j = o / N, i = o - j * N;
       c_store<LP>(A + (long)j * a.ldA, Ap, i, val);
@@ -395,7 +397,8 @@ __device__ void track_job(const Job &a, double *smem) {
             const int o = o0 + tid / kSG, lane = tid % kSG;
             const bool act = o < a.nout;
             cx<P> val = sum_output<P, kSG>(act, o, lane, N, n, a.optrf, a.oslotf, fslots, a.nsf,
-                                           a.optrg, a.oslotg, gslots, a.nsg, spow, scal, 1);
+                                           a.optrg, a.oslotg, gslots, a.nsg, spow, scal, 1,
+                                     a.p.fixed_rows ? a.zrows_g : nullptr);
             if (act && lane == 0) {
               if (o < n * N) {
                 const int j = o / N, i = o - j * N;
@@ -421,7 +424,8 @@ __device__ void track_job(const Job &a, double *smem) {
             const int i = o0 + tid / kSG, lane = tid % kSG;
             const bool act = i < N;
             cx<P> val = sum_output<P, kSG>(act, n * N + i, lane, N, n, a.optrf, a.oslotf, fslots,
-                                           a.nsf, a.optrg, a.oslotg, gslots, a.nsg, spow, scal, 1);
+                                           a.nsf, a.optrg, a.oslotg, gslots, a.nsg, spow, scal, 1,
+                                     a.p.fixed_rows ? a.zrows_g : nullptr);
             if (act && lane == 0) {
               hl[i] = -P::lead(val.re);
               hl[a.ldA + i] = -P::lead(val.im);

@@ -126,7 +126,8 @@ PHD cx<P> shfl_down_c(const cx<P> &a, int off, int width) {
 // call this, active or not).  Returns the finished output on lane 0 of the
 // group: the sum of its slots (in the order of the terms), times t^k when a
 // homotopy is evaluated, plus gamma (1-t)^k times the start system's term
-// (from g's slots, or from spow for the total-degree system).
+// (from g's slots, or from spow for the total-degree system).  fixed (may be
+// null): rows held fixed, h_i = f_i (g_i is the zero polynomial there).
 template <class P, int G>
 __device__ cx<P> sum_output(bool active, int o, int lane, int N, int n,
                             const int32_t *__restrict__ optr, const int32_t *__restrict__ oslot,
@@ -134,7 +135,7 @@ __device__ cx<P> sum_output(bool active, int o, int lane, int N, int n,
                             const int32_t *__restrict__ goptr, const int32_t *__restrict__ goslot,
                             const double *__restrict__ gslots, long gnslots,
                             const double *__restrict__ spow, const double *__restrict__ scal,
-                            int homotopy) {
+                            int homotopy, const uint8_t *__restrict__ fixed = nullptr) {
   cx<P> af = c_zero<P>(), ag = c_zero<P>();
   if (active) {
     for (int q = optr[o] + lane; q < optr[o + 1]; q += G)
@@ -149,11 +150,12 @@ __device__ cx<P> sum_output(bool active, int o, int lane, int N, int n,
     if (goptr) ag = c_add<P>(ag, shfl_down_c<P>(ag, off, G));
   }
   if (!active || lane != 0 || !homotopy) return af;
+  const int nN = n * N;
+  if (fixed && fixed[o < nN ? o % N : o - nN]) return af;
   const typename P::real sf = r_load<P>(scal, 1, 0);
   const cx<P> sg = c_load<P>(scal + P::L, 1, 0);
   cx<P> val = c_mul_real<P>(af, sf);
   if (goptr) return c_add<P>(val, c_mul<P>(sg, ag));
-  const int nN = n * N;
   const long pl = 2L * P::L * n;
   if (o < nN) {
     int j = o / N, i = o - j * N;

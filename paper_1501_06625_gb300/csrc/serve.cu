@@ -415,6 +415,7 @@ extern "C" ph_status ph_server_submit(ph_server *s, const ph_system *f, const ph
   const ph_track_params &p = *params;
   if (p.max_newton < 1 || p.max_newton > 64 || p.pred_order < 0 || p.pred_order > 8 ||
       p.relax_k < 1 || p.relax_k > 64 || p.max_steps < 0 || p.lin_prec < 0 || p.lin_prec > 3 ||
+      p.fixed_rows < 0 || p.fixed_rows > 1 || (p.fixed_rows && !g) ||
       (p.fixed_steps <= 0 && !(p.max_dt > 0.0 && p.min_dt > 0.0 && p.min_dt <= p.max_dt)))
     return ph_fail(ctx, PH_EINVAL, "ph_server_submit: invalid parameters");
   if (!g) {

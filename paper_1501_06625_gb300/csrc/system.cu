@@ -154,6 +154,8 @@ extern "C" ph_status ph_system_load(ph_ctx *ctx, ph_prec prec, int N, int n,
   }
 
   std::vector<int32_t> degv(s->h_deg.begin(), s->h_deg.end());
+  std::vector<uint8_t> zrows(N);
+  for (int i = 0; i < N; ++i) zrows[i] = term_ptr[i + 1] == term_ptr[i] ? 1 : 0;
   ph_status st;
   if ((st = upload(s, s->poly, poly.data(), sizeof(int32_t) * Mp)) != PH_OK ||
       (st = upload(s, s->nv, nv.data(), sizeof(int32_t) * Mp)) != PH_OK ||
@@ -162,7 +164,8 @@ extern "C" ph_status ph_system_load(ph_ctx *ctx, ph_prec prec, int N, int n,
       (st = upload(s, s->coeff, co.data(), sizeof(double) * co.size())) != PH_OK ||
       (st = upload(s, s->deg, degv.data(), sizeof(int32_t) * N)) != PH_OK ||
       (st = upload(s, s->out_ptr, optr.data(), sizeof(int32_t) * optr.size())) != PH_OK ||
-      (st = upload(s, s->out_slot, oslot.data(), sizeof(int32_t) * oslot.size())) != PH_OK) {
+      (st = upload(s, s->out_slot, oslot.data(), sizeof(int32_t) * oslot.size())) != PH_OK ||
+      (st = upload(s, s->zero_rows, zrows.data(), (size_t)N)) != PH_OK) {
     ph_system_free(s);
     return st;
   }
@@ -179,6 +182,7 @@ extern "C" ph_status ph_system_free(ph_system *s) {
   if (!s) return PH_EINVAL;
   s->poly.release(); s->nv.release(); s->vidx.release(); s->vexp.release();
   s->coeff.release(); s->deg.release(); s->out_ptr.release(); s->out_slot.release();
+  s->zero_rows.release();
   delete s;
   return PH_OK;
 }

@@ -438,20 +438,22 @@ static cudaError_t record_step(ph_ctx *ctx, cudaStream_t s, const ph_system *f,
   const bool mixed = p.lin_prec == 1;
   const int n_it = mixed && p.fixed_steps <= 0 ? p.max_newton + 1 : p.max_newton;
   const int *gwp = mixed ? &st->gate_wp : &st->skip_nt;
+  const uint8_t *frows = p.fixed_rows && g ? g->zero_rows.as<uint8_t>() : nullptr;
   double *rhs = A + (long)n * ldA;
   const int fx = p.fixed_steps > 0;
   const unsigned ub = (unsigned)((n + 127) / 128);
   for (int it = 0; it < n_it && e == cudaSuccess; ++it) {
     e = ph_eval_launch(ctx, f, g, gamma, p.relax_k, st->t_dev, xw, nullptr, A, ldA, Ap, rhs, Ap,
-                       gwp, &st->res_bits);
+                       gwp, &st->res_bits, frows);
     if (e == cudaSuccess && mixed)
       e = ph_eval_values_launch(ctx, f, g, gamma, p.relax_k, st->t_dev, xw, rhs, Ap, &st->gate_lp,
-                                &st->res_bits);
+                                &st->res_bits, frows);
     if (e != cudaSuccess) break;
     k_check_res<<<1, 1, 0, s>>>(st, p);
     if (mixed) {
       k_rhs_scale<<<(N + 127) / 128, 128, 0, s>>>(st, rhs, Ap, N);
-      e = ph_eval_launch_f64(ctx, f, g, gamma, p.relax_k, st->t_dev, xw, A, ldA, Ap, &st->gate_lp);
+      e = ph_eval_launch_f64(ctx, f, g, gamma, p.relax_k, st->t_dev, xw, A, ldA, Ap, &st->gate_lp,
+                             frows);
       if (e != cudaSuccess) break;
     }
     e = ph_mgs_launch(ctx, L, N, n, A, ldA, dx, st, gwp, nullptr);
@@ -536,6 +538,7 @@ extern "C" ph_status ph_track_path(ph_ctx *ctx, const ph_system *f, const ph_sys
   const ph_track_params p = *params;
   if (p.max_newton < 1 || p.max_newton > 64 || p.pred_order < 0 || p.pred_order > 8 ||
       p.relax_k < 1 || p.relax_k > 64 || p.control < 0 || p.control > 1 || p.max_steps < 0 ||
+      p.fixed_rows < 0 || p.fixed_rows > 1 || (p.fixed_rows && !g) ||
       (p.fixed_steps <= 0 && !(p.max_dt > 0.0 && p.min_dt > 0.0 && p.min_dt <= p.max_dt)))
     return ph_fail(ctx, PH_EINVAL, "ph_track_path: invalid parameters");
   if (p.lin_prec != 0 && p.lin_prec != 1)

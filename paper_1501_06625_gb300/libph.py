@@ -31,7 +31,7 @@ class TrackParams(C.Structure):
                 ("tol_dx", C.c_double), ("max_res", C.c_double), ("max_x", C.c_double),
                 ("max_steps", C.c_int32), ("max_newton", C.c_int32), ("pred_order", C.c_int32),
                 ("relax_k", C.c_int32), ("fixed_steps", C.c_int32), ("control", C.c_int32),
-                ("lin_prec", C.c_int32), ("reserved", C.c_int32), ("endgame_t", C.c_double),
+                ("lin_prec", C.c_int32), ("fixed_rows", C.c_int32), ("endgame_t", C.c_double),
                 ("cond_f32", C.c_double)]
 
 

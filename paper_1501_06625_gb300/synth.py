@@ -301,17 +301,19 @@ def _with_linear_rows(spec: SystemSpec, coef: np.ndarray, const: np.ndarray,
                       lo.astype(np.complex128))
 
 
-def cyclic_monodromy(seed: int, n: int):
+def cyclic_monodromy(seed: int, n: int, fixed: bool = True):
     """One monodromy path on cyclic n-roots, n = m^2 (Section 4.2): the
     solution set of dimension m - 1 cut by m - 1 random hyperplanes L, moved to
-    m - 1 other random hyperplanes K.  The paper's homotopy {f = 0,
-    alpha (1-t) L + t K = 0} has the zero set of gamma (1-t) G + t F with
-    G = [f; L], F = [f; K] and gamma = alpha (its first block is f times
-    gamma (1-t) + t, which does not vanish for t in [0, 1]): N = n + m - 1
-    equations in n unknowns, corrected by least squares.  The start point is
-    backelin_point with v of unit modulus (random angles); L's constant terms
-    are -sum_k c_k x0_k, summed exactly in rationals from the double x0 and
-    stored as two limbs.  Returns (F, G, gamma, x0)."""
+    m - 1 other random hyperplanes K: N = n + m - 1 equations in n unknowns,
+    corrected by least squares.  fixed: F = [f; K] and G = [0; L], the paper's
+    homotopy {f = 0, alpha (1-t) L + t K = 0} when the tracker holds the rows
+    without a start term fixed (ph_track_params.fixed_rows = 1, gamma =
+    alpha).  Otherwise G = [f; L]: gamma (1-t) G + t F has the same zero set
+    (its first block is f times gamma (1-t) + t, which does not vanish for t in
+    [0, 1]) and evaluates f twice.  The start point is backelin_point with v of
+    unit modulus (random angles); L's constant terms are -sum_k c_k x0_k,
+    summed exactly in rationals from the double x0 and stored as two limbs.
+    Returns (F, G, gamma, x0)."""
     from fractions import Fraction
     m = int(round(np.sqrt(n)))
     if m * m != n or m < 2:
@@ -334,7 +336,11 @@ def cyclic_monodromy(seed: int, n: int):
         lo[q] = complex(float(sr - Fraction(hr)), float(si - Fraction(him)))
     f = cyclic_system(n)
     F = _with_linear_rows(f, cK, kK, np.zeros(r, dtype=np.complex128))
-    G = _with_linear_rows(f, cL, hi, lo)
+    g0 = f if not fixed else SystemSpec(n, n, np.zeros(n + 1, dtype=np.int32),
+                                        np.zeros(1, dtype=np.int32), np.zeros(0, dtype=np.int32),
+                                        np.zeros(0, dtype=np.int32),
+                                        np.zeros(0, dtype=np.complex128))
+    G = _with_linear_rows(g0, cL, hi, lo)
     return F, G, rng.unit_complex(), x0
 
 
@@ -348,8 +354,8 @@ def default_params(L: int, **over) -> dict:
     tol = {1: 1e-11, 2: 1e-24, 4: 1e-52}[L]
     p = dict(max_dt=0.1, min_dt={1: 1e-8, 2: 1e-12, 4: 1e-20}[L], tol_res=tol, tol_dx=tol,
              max_res=1e8, max_x=1e8, max_steps=10000, max_newton=4 if L == 4 else 3,
-             pred_order=4, relax_k=1, fixed_steps=0, control=0, lin_prec=0, endgame_t=0.0,
-             cond_f32=0.0)
+             pred_order=4, relax_k=1, fixed_steps=0, control=0, lin_prec=0, fixed_rows=0,
+             endgame_t=0.0, cond_f32=0.0)
     p.update(over)
     return p
 

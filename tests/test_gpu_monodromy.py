@@ -1,10 +1,11 @@
 """One monodromy path on cyclic 16-roots (Section 4.2, the paper's runs of
 Table 8): the solution set of dimension 3 (m = 4) cut by three random
 hyperplanes L, which move to three others K, a least-squares path (N = 19
-equations in n = 16 unknowns) from a start point of Backelin's family.
+equations in n = 16 unknowns) from a start point of Backelin's family, in the
+paper's form {f = 0, gamma (1-t) L + t K = 0} (the cyclic rows held fixed).
 
 * complex double: the whole adaptive path, and the oracle's replay of its
-  schedule ends at the same point;
+  schedule ends at the same point (also in the form where every row moves);
 * DD and QD: segments of the adaptive path replayed by the oracle (a whole
   path would take the oracle minutes), and whole paths that end on the same
   component (x_{4a+b} = i^a x_b, exact in every limb) and on the target
@@ -30,11 +31,14 @@ def ctx():
     c.close()
 
 
-def _mono(L, **over):
-    F, G, gam, x0 = synth.cyclic_monodromy(1, 16)
+def _mono(L, fixed=True, **over):
+    """The loop in the paper's form (F = [f; K], G = [0; L], rows without a
+    start term held fixed) or, fixed=False, with G = [f; L] and every row
+    moving (the same zero set)."""
+    F, G, gam, x0 = synth.cyclic_monodromy(1, 16, fixed=fixed)
     xs = soa_from_complex(x0, L)
     gs = soa_from_complex([gam], L).reshape(L, 2)
-    return F, G, gs, xs, synth.default_params(L, **over)
+    return F, G, gs, xs, synth.default_params(L, fixed_rows=int(fixed), **over)
 
 
 def _family_gap(x, L):
@@ -47,9 +51,10 @@ def _family_gap(x, L):
     return np.abs(tot).max() / np.abs(z[0]).max()
 
 
-def test_monodromy_path_double_replay(ctx):
+@pytest.mark.parametrize("fixed", [True, False])
+def test_monodromy_path_double_replay(ctx, fixed):
     L = 1
-    F, G, gs, xs, params = _mono(L, max_steps=3000)
+    F, G, gs, xs, params = _mono(L, fixed, max_steps=3000)
     f, g = ctx.load(F, L), ctx.load(G, L)
     x = np.zeros_like(xs)
     st, stats, log = libph.ph_track_path(ctx.h, f, g, gs, xs, params, x, log_cap=3100)
@@ -102,3 +107,33 @@ def test_monodromy_loop_through_the_serving_loop(ctx):
         libph.ph_server_destroy(srv)
     assert s2["status"] == libph.PH_OK and s2["t_final"] == 1.0
     assert cabs_diff(x1, x2).max() <= 1e3 * params["tol_dx"]
+
+
+def test_fixed_rows_needs_a_start_system(ctx):
+    L = 2
+    F, G, gs, xs, params = _mono(L)
+    f = ctx.load(F, L)
+    with pytest.raises(libph.PhError) as ei:
+        libph.ph_track_path(ctx.h, f, None, gs, xs, params, np.zeros_like(xs))
+    assert ei.value.status == libph.PH_EINVAL
+    with pytest.raises(libph.PhError) as ei:
+        libph.ph_track_paths(ctx.h, f, None, gs, np.ascontiguousarray(xs[None]), params,
+                             np.zeros((1,) + xs.shape))
+    assert ei.value.status == libph.PH_EINVAL
+
+
+def test_fixed_rows_without_empty_rows_is_the_plain_form(ctx):
+    """A start system with a term in every row: fixed_rows changes nothing, bit
+    for bit, in the single-path and the many-path forms."""
+    L = 2
+    F, G, gs, xs, params = _mono(L, fixed=False, max_steps=29, max_newton=5)
+    f, g = ctx.load(F, L), ctx.load(G, L)
+    out = []
+    for fr in (0, 1):
+        x = np.zeros_like(xs)
+        libph.ph_track_path(ctx.h, f, g, gs, xs, dict(params, fixed_rows=fr), x)
+        xb = np.zeros((1,) + xs.shape)
+        libph.ph_track_paths(ctx.h, f, g, gs, np.ascontiguousarray(xs[None]),
+                             dict(params, fixed_rows=fr), xb)
+        out.append((x, xb[0]))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])

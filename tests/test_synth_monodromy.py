@@ -73,7 +73,7 @@ def test_solution_set_dimension(m):
 @pytest.mark.parametrize("L", [2, 4])
 def test_start_slices_pass_through_x0(L):
     n, m = 16, 4
-    F, G, gam, x0 = synth.cyclic_monodromy(1, n)
+    F, G, gam, x0 = synth.cyclic_monodromy(1, n, fixed=False)      # G = [f; L]
     assert (F.N, F.n, G.N) == (n + m - 1, n, n + m - 1)
     xs = np.zeros((L, 2, n))
     xs[0, 0], xs[0, 1] = x0.real, x0.imag
@@ -84,3 +84,35 @@ def test_start_slices_pass_through_x0(L):
     assert np.abs(hv[n:]).max() < 1e-28
     h, _ = oracle.eval_h(oracle.System(F, L), xs)
     assert np.abs(h[0, 0, n:] + 1j * h[0, 1, n:]).min() > 1e-3     # K does not
+
+
+@pytest.mark.parametrize("L", [2, 4])
+def test_fixed_rows_homotopy(L):
+    """With fixed rows the oracle evaluates the paper's monodromy homotopy
+    [f; gamma (1-t) L + t K] for F = [f; K], G = [0; L]: the cyclic rows are
+    f's own values and derivatives in every limb (not scaled by t), the slice
+    rows the combination of the two slices; without fixed rows the cyclic rows
+    are t f (G has no terms there)."""
+    n = 16
+    F, G, gam, _ = synth.cyclic_monodromy(2, n)
+    x = np.zeros((L, 2, n))
+    z = synth.random_x(synth.Rng(9), n)
+    x[0, 0], x[0, 1] = z.real, z.imag
+    gs = np.zeros((L, 2))
+    gs[0] = [gam.real, gam.imag]
+    t = 0.37
+    oF, oG = oracle.System(F, L), oracle.System(G, L)
+    h, J = oracle.eval_h(oF, x, t=t, gamma=gs, g=oG, fixed_rows=1)
+    hF, JF = oracle.eval_h(oF, x)
+    hG, _ = oracle.eval_h(oG, x)
+    assert np.array_equal(h[:, :, :n], hF[:, :, :n])
+    assert np.array_equal(J[:, :, :, :n], JF[:, :, :, :n])
+
+    def lead(a):
+        return a[0, 0] + 1j * a[0, 1]
+
+    want = gam * (1 - t) * lead(hG)[n:] + t * lead(hF)[n:]
+    assert np.abs(lead(h)[n:] - want).max() < 1e-14 * np.abs(want).max()
+    h0, _ = oracle.eval_h(oF, x, t=t, gamma=gs, g=oG, fixed_rows=0)
+    ref = np.abs(lead(hF)[:n]).max()
+    assert np.abs(lead(h0)[:n] - t * lead(hF)[:n]).max() < 1e-14 * ref
