@@ -557,6 +557,44 @@ def monodromy_loops_leg(libph, synth, ctx, seed, loops, single):
     return out
 
 
+# The paper's Table 5: degrees of the cyclic n-roots solution sets (n = m^2)
+PAPER_CYCLIC_DEGREE = {16: 4, 64: 8, 144: 12}
+
+
+def monodromy_degree_leg(synth, ctx, seed, sizes):
+    """The degree of the cyclic n-roots solution set through its start point,
+    computed as the paper does (Section 4.2, Table 5): rounds of monodromy
+    loops (out to the slices K and back to L, each loop with its own alpha and
+    beta) through the serving loop, from the points found so far, until a
+    round adds no point.  Double-double, 5 Newton iterations per step; wall
+    clock around the whole computation.  The points found are checked against
+    the family's points on the slices computed from its linear
+    parametrization (monodromy.family_points_on_slices)."""
+    from paper_1501_06625_gb300 import monodromy
+    out = {}
+    for n, per_round in sizes:
+        m = int(round(np.sqrt(n)))
+        loop = synth.cyclic_monodromy_loop(seed, n)
+        params = synth.default_params(2, max_newton=5, max_steps=5000)
+        t0 = time.perf_counter()
+        res = monodromy.loops(ctx, loop, 2, params, rounds=12, per_round=per_round,
+                              seed=seed + 7, patience=2)
+        wall = time.perf_counter() - t0
+        G = loop["out"][1]
+        c = G.coeff.reshape(m - 1, n + 1)
+        ref = monodromy.family_points_on_slices(
+            m, c[:, :n], c[:, n] + G.coeff_lo.reshape(m - 1, n + 1)[:, n])
+        match = [float(np.abs(ref - (q[0, 0] + 1j * q[0, 1])[None, :]).max(axis=1).min())
+                 for q in res["points"]]
+        out[f"cyclic{n}_dd"] = {
+            "degree_found": len(res["points"]), "paper_degree": PAPER_CYCLIC_DEGREE[n],
+            "found_after_each_round": res["found"], "loops": res["loops"],
+            "failed_paths": res["failed"], "paths": res["paths"],
+            "newton_iters": res["newton_iters"], "wall_s": wall,
+            "max_distance_to_parametrized_points": max(match)}
+    return out
+
+
 def serve_leg(libph, synth, ctx, nreq, seed, lin=0, seq_rate=None):
     """A stream of path-tracking requests through the continuous-batching loop
     (ph_server_*).  A pool of 16 systems per (recipe, precision): n =
@@ -767,6 +805,8 @@ def main():
                     help="steps of the cyclic monodromy paths not tracked whole")
     ap.add_argument("--monodromy-loops", type=int, default=152,
                     help="monodromy loops tracked at once through the serving loop (0 skips)")
+    ap.add_argument("--monodromy-degree-64", action="store_true",
+                    help="also compute the degree of the cyclic 64-roots set (about a minute)")
     ap.add_argument("--no-sparse", action="store_true",
                     help="skip the n=512 QD solver roofline measurement")
     args = ap.parse_args()
@@ -879,6 +919,8 @@ def main():
         if args.monodromy_loops > 0:
             monodromy["loops_in_flight"] = monodromy_loops_leg(
                 libph, synth, ctx, args.seed, args.monodromy_loops, monodromy)
+        monodromy["degree"] = monodromy_degree_leg(
+            synth, ctx, args.seed, [(16, 32)] + ([(64, 76)] if args.monodromy_degree_64 else []))
 
     precision = None
     if args.precision_paths > 0 and rank == 0:

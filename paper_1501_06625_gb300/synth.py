@@ -344,6 +344,33 @@ def cyclic_monodromy(seed: int, n: int, fixed: bool = True):
     return F, G, rng.unit_complex(), x0
 
 
+def cyclic_monodromy_loop(seed: int, n: int) -> dict:
+    """Both halves of a monodromy loop on cyclic n-roots, n = m^2 (Section
+    4.2), in the fixed-row form: "out" moves the slices L (through the start
+    point) to K: target [f; K], start [0; L]; "back" moves K to L: target
+    [f; L], start [0; K].  A loop is one path of each, with its own constants
+    (gamma = alpha out, beta back).  Returns {"out": (F, G), "back": (F, G),
+    "x0": start point on L}."""
+    F, G, _, x0 = cyclic_monodromy(seed, n, fixed=True)
+    m = int(round(np.sqrt(n)))
+    r = m - 1
+    f = cyclic_system(n)
+    zero = SystemSpec(n, n, np.zeros(n + 1, dtype=np.int32), np.zeros(1, dtype=np.int32),
+                      np.zeros(0, dtype=np.int32), np.zeros(0, dtype=np.int32),
+                      np.zeros(0, dtype=np.complex128))
+    # the slice rows of F (K) and of G (L): n + 1 terms each after the cyclic part
+    def rows(spec, base):
+        c = spec.coeff[base:].reshape(r, n + 1)
+        lo = (spec.coeff_lo[base:].reshape(r, n + 1)[:, n] if spec.coeff_lo is not None
+              else np.zeros(r, dtype=np.complex128))
+        return c[:, :n], c[:, n], lo
+    cK, kK, kKlo = rows(F, f.M)
+    cL, kL, kLlo = rows(G, 0)
+    return {"out": (F, G),
+            "back": (_with_linear_rows(f, cL, kL, kLlo), _with_linear_rows(zero, cK, kK, kKlo)),
+            "x0": x0}
+
+
 def default_params(L: int, **over) -> dict:
     """Path-tracking parameters (the paper leaves them open).  Newton's
     method roughly squares the error per iteration, so from a predictor error

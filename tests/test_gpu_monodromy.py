@@ -137,3 +137,24 @@ def test_fixed_rows_without_empty_rows_is_the_plain_form(ctx):
                              dict(params, fixed_rows=fr), xb)
         out.append((x, xb[0]))
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def test_monodromy_loops_find_the_degree(ctx):
+    """The paper's use of these paths (Section 4.2, Table 5: degree 4 for
+    n = 16): rounds of monodromy loops through the serving loop, from the
+    points found so far, until a round adds nothing.  They find exactly the
+    m = 4 points of the component on the start slices, each equal to one of
+    the points computed from the family's linear parametrization."""
+    from paper_1501_06625_gb300 import monodromy
+    L, n, m = 2, 16, 4
+    loop = synth.cyclic_monodromy_loop(1, n)
+    params = synth.default_params(L, max_newton=5, max_steps=3000)
+    res = monodromy.loops(ctx, loop, L, params, rounds=8, per_round=16, seed=3, patience=2)
+    pts = [lead_complex(p) for p in res["points"]]
+    assert len(pts) == m, res["found"]
+    G = loop["out"][1]
+    c = G.coeff.reshape(m - 1, n + 1)
+    ref = monodromy.family_points_on_slices(m, c[:, :n],
+                                            c[:, n] + G.coeff_lo.reshape(m - 1, n + 1)[:, n])
+    for z in pts:
+        assert np.abs(ref - z[None, :]).max(axis=1).min() < 1e-12

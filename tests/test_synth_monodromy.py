@@ -116,3 +116,36 @@ def test_fixed_rows_homotopy(L):
     h0, _ = oracle.eval_h(oF, x, t=t, gamma=gs, g=oG, fixed_rows=0)
     ref = np.abs(lead(hF)[:n]).max()
     assert np.abs(lead(h0)[:n] - t * lead(hF)[:n]).max() < 1e-14 * ref
+
+
+def _slices(spec, n, m):
+    """coefficients and constants of the slice rows of a start system [0; L]"""
+    r = m - 1
+    c = spec.coeff.reshape(r, n + 1)
+    lo = spec.coeff_lo.reshape(r, n + 1)[:, n]
+    return c[:, :n], c[:, n] + lo
+
+
+def _cyclic_np(x):
+    n = len(x)
+    out = [sum(np.prod([x[(j + k) % n] for k in range(i)]) for j in range(n)) for i in range(1, n)]
+    return np.array(out + [np.prod(x) - 1])
+
+
+@pytest.mark.parametrize("m", [2, 3, 4])
+def test_family_points_on_the_slices(m):
+    """The m points of Backelin's family on the start slices, computed from the
+    linear parametrization: they satisfy the cyclic equations and the slices,
+    are distinct, and the start point is one of them."""
+    from paper_1501_06625_gb300 import monodromy
+    n = m * m
+    loop = synth.cyclic_monodromy_loop(4, n)
+    coef, const = _slices(loop["out"][1], n, m)
+    pts = monodromy.family_points_on_slices(m, coef, const)
+    assert pts.shape == (m, n)
+    for x in pts:
+        assert np.abs(_cyclic_np(x)).max() < 1e-10 * max(1.0, np.abs(x).max() ** n)
+        assert np.abs(coef @ x + const).max() < 1e-12 * np.abs(coef).sum(axis=1).max() * np.abs(x).max()
+    d = np.abs(pts[:, None, :] - pts[None, :, :]).max(axis=2) + np.eye(m)
+    assert d.min() > 1e-6
+    assert np.abs(pts - loop["x0"][None, :]).max(axis=1).min() < 1e-12
