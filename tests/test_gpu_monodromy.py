@@ -158,3 +158,19 @@ def test_monodromy_loops_find_the_degree(ctx):
                                             c[:, n] + G.coeff_lo.reshape(m - 1, n + 1)[:, n])
     for z in pts:
         assert np.abs(ref - z[None, :]).max(axis=1).min() < 1e-12
+
+
+def test_monodromy_precision_form_ends_on_the_component(ctx):
+    """The precision form (Newton systems in double) with the cyclic rows held
+    fixed: the QD path ends on the component and on the target slices, where
+    the all-QD path ends."""
+    L = 4
+    F, G, gs, xs, params = _mono(L, max_steps=3000, max_newton=6)
+    f, g = ctx.load(F, L), ctx.load(G, L)
+    x0 = np.zeros_like(xs)
+    st0, _, _ = libph.ph_track_path(ctx.h, f, g, gs, xs, params, x0)
+    x1 = np.zeros_like(xs)
+    st1, s1, _ = libph.ph_track_path(ctx.h, f, g, gs, xs, dict(params, lin_prec=1), x1)
+    assert st0 == libph.PH_OK and st1 == libph.PH_OK and s1["solves_f64"] > 0
+    assert _family_gap(x1, L) < 1e3 * U[L]
+    assert cabs_diff(x0, x1).max() <= 1e3 * params["tol_dx"]
