@@ -505,29 +505,6 @@ def monodromy_leg(libph, synth, ctx, torch, dev, seed, segment):
                 "per_step_vs_paper": (1e3 * pgpu / pm) / per_step}
             if whole and st == libph.PH_OK:
                 out[f"cyclic{n}_{name}"]["per_path_vs_paper"] = 1e3 * pgpu / ms
-            if L == 4 and n >= 64:
-                # the precision form on the same path: Newton systems in double,
-                # residual and update in quad-double (the end game at t = 1 in QD)
-                pm_ = dict(params, lin_prec=1)
-                xm = torch.empty_like(dx0)
-                e0.record(stream)
-                st2, sd2, _ = libph.ph_track_path(ctx.h, f, g, dg, dx0, pm_, xm)
-                e1.record(stream)
-                e1.synchronize()
-                ms2 = e0.elapsed_time(e1)
-                a_, b_ = xm.cpu().numpy(), xo.cpu().numpy()
-                dd = (a_ - b_)[::-1].sum(axis=0)
-                r2 = {"status": int(st2), "t_final": sd2["t_final"], "steps": sd2["steps"],
-                      "newton_iters": sd2["newton_iters"], "solves_f64": sd2["solves_f64"],
-                      "escalated": sd2["escalated"], "ms": ms2,
-                      "ms_per_step": ms2 / max(1, sd2["steps"]),
-                      "per_step_vs_paper": (1e3 * pgpu / pm) / (ms2 / max(1, sd2["steps"])),
-                      "graph_built_in_timing": True}
-                if whole:                      # the same end point t = 1 in both forms
-                    r2["end_point_diff_vs_plain"] = float(np.abs(dd[0] + 1j * dd[1]).max())
-                if whole and st2 == libph.PH_OK:
-                    r2["per_path_vs_paper"] = 1e3 * pgpu / ms2
-                out[f"cyclic{n}_{name}"]["precision_form"] = r2
             ctx.free(f)
             ctx.free(g)
     return out

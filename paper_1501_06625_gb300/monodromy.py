@@ -6,13 +6,15 @@ the homotopy {f = 0, alpha (1-t) L + t K = 0} to the slices K, then
 {f = 0, beta (1-t) K + t L = 0} back to L, with random constants alpha and
 beta.  Its end point is again a point of the set on L, often another one.
 After enough loops with different constants every point of the set on L has
-been reached, and their number is the degree.  Every loop is an independent
-path, so a round of loops runs at once through the serving loop
-(ph_server_*, one persistent block per path); the host only collects the
+been reached, and their number is the degree.  Every loop is two independent
+paths, so many loops run at once through the serving loop (ph_server_*, one
+persistent block per path); the host submits and collects them and keeps the
 distinct end points.  Host orchestration only: every path runs in the
 library's kernels.
 """
 from __future__ import annotations
+
+import time
 
 import numpy as np
 
@@ -29,32 +31,19 @@ def _lead(x: np.ndarray) -> np.ndarray:
     return x[0, 0] + 1j * x[0, 1]
 
 
-def _track_all(ctx, srv, f, g, gammas, starts, params, L, timeout_ms):
-    """One path per (gamma, start) through the server; returns (end points
-    [L][2][n] or None for a failed path, stats)."""
-    ids = []
-    for gam, x0 in zip(gammas, starts):
-        gs = np.zeros((L, 2))
-        gs[0] = [gam.real, gam.imag]
-        ids.append(libph.ph_server_submit(ctx.h, srv, f, g, gs, x0, params))
-    ends, stats = [], []
-    for jid, x0 in zip(ids, starts):
-        x = np.zeros_like(x0)
-        st, _ = libph.ph_server_wait(ctx.h, srv, jid, timeout_ms, x)
-        stats.append(st)
-        ends.append(x if st["status"] == libph.PH_OK else None)
-    return ends, stats
-
-
 def loops(ctx, loop: dict, L: int, params: dict, rounds: int, per_round: int, seed: int = 1,
           tol: float = 1e-8, patience: int = 1, timeout_ms: int = 600000) -> dict:
-    """Runs rounds of `per_round` monodromy loops (synth.cyclic_monodromy_loop
-    systems) from the points found so far, each loop with its own alpha and
-    beta, until a round adds no new point `patience` times or `rounds` have
-    run.  Points are distinct when their leading limbs differ by more than
-    tol (relative).  params: tracking parameters (fixed_rows is set).
-    Returns {"points": [L][2][n] arrays, "found": count after each round,
-    "loops", "failed", "paths", "newton_iters"}."""
+    """Monodromy loops (synth.cyclic_monodromy_loop systems) kept `per_round`
+    at a time in the serving loop: a loop's way back is submitted as soon as
+    its way out ends, and a new loop starts, from the points found so far in
+    turn, as soon as one ends, each loop with its own alpha and beta.  No new
+    loop starts once `patience * per_round` loops in a row have found no new
+    point, or `rounds * per_round` have started; the loops in flight then
+    finish (their points count).  Points are distinct when their leading
+    limbs differ by more than tol (relative).  params: tracking parameters
+    (fixed_rows is set).  Returns {"points": [L][2][n] arrays, "found": count
+    after every per_round finished loops, "loops", "failed", "paths",
+    "newton_iters"}."""
     F, G = loop["out"]
     Fb, Gb = loop["back"]
     x0 = loop["x0"]
@@ -65,37 +54,64 @@ def loops(ctx, loop: dict, L: int, params: dict, rounds: int, per_round: int, se
     fb, gb = ctx.load(Fb, L), ctx.load(Gb, L)
     srv = libph.ph_server_create(ctx.h, max_n=n, pool_bytes=8 << 30, queue_cap=2 * per_round)
     points = [_soa(x0, L)]
-    found, failed, paths, iters, idle = [], 0, 0, 0, 0
+    found = []
+    failed = paths = iters = started = finished = since_new = 0
+    inflight = {}                                  # job id -> ("out" | "back", submit time)
+
+    def submit(f, g, x, kind):
+        gs = np.zeros((L, 2))
+        gam = rng.unit_complex()
+        gs[0] = [gam.real, gam.imag]
+        inflight[libph.ph_server_submit(ctx.h, srv, f, g, gs, x, p)] = (kind, time.monotonic())
+
+    def start_loop():
+        nonlocal started
+        if started < rounds * per_round and since_new < patience * per_round:
+            submit(fo, go, points[started % len(points)], "out")
+            started += 1
+
     try:
-        for _ in range(rounds):
-            starts = [points[i % len(points)] for i in range(per_round)]
-            alphas = [rng.unit_complex() for _ in range(per_round)]
-            betas = [rng.unit_complex() for _ in range(per_round)]
-            mid, s1 = _track_all(ctx, srv, fo, go, alphas, starts, p, L, timeout_ms)
-            ok = [i for i, y in enumerate(mid) if y is not None]
-            ends, s2 = _track_all(ctx, srv, fb, gb, [betas[i] for i in ok],
-                                  [mid[i] for i in ok], p, L, timeout_ms)
-            paths += len(s1) + len(s2)
-            iters += sum(s["newton_iters"] for s in s1 + s2)
-            failed += (per_round - len(ok)) + sum(1 for z in ends if z is None)
-            before = len(points)
-            for z in ends:
-                if z is None:
+        for _ in range(per_round):
+            start_loop()
+        while inflight:
+            progressed = False
+            for jid, (kind, t0) in list(inflight.items()):
+                x = np.zeros((L, 2, n))
+                done, st, _ = libph.ph_server_poll(ctx.h, srv, jid, x)
+                if not done:
+                    if (time.monotonic() - t0) * 1e3 > timeout_ms:
+                        raise RuntimeError("monodromy: a path did not finish in time")
                     continue
-                zl = _lead(z)
-                scale = max(1.0, np.abs(zl).max())
-                if all(np.abs(zl - _lead(q)).max() > tol * scale for q in points):
-                    points.append(z)
-            found.append(len(points))
-            idle = idle + 1 if len(points) == before else 0
-            if idle >= patience:
-                break
+                progressed = True
+                del inflight[jid]
+                paths += 1
+                iters += st["newton_iters"]
+                ok = st["status"] == libph.PH_OK
+                if kind == "out" and ok:
+                    submit(fb, gb, x, "back")
+                    continue
+                finished += 1                      # the loop ends here
+                new = False
+                if ok:
+                    zl = _lead(x)
+                    scale = max(1.0, np.abs(zl).max())
+                    if all(np.abs(zl - _lead(q)).max() > tol * scale for q in points):
+                        points.append(x)
+                        new = True
+                else:
+                    failed += 1
+                since_new = 0 if new else since_new + 1
+                if finished % per_round == 0:
+                    found.append(len(points))
+                start_loop()
+            if not progressed:
+                time.sleep(0.0005)
     finally:
         libph.ph_server_destroy(srv)
-        for s in (fo, go, fb, gb):
-            ctx.free(s)
-    return {"points": points, "found": found, "loops": len(found) * per_round,
-            "failed": failed, "paths": paths, "newton_iters": iters}
+        for s_ in (fo, go, fb, gb):
+            ctx.free(s_)
+    return {"points": points, "found": found, "loops": started, "failed": failed,
+            "paths": paths, "newton_iters": iters}
 
 
 def family_points_on_slices(m: int, coef: np.ndarray, const: np.ndarray) -> np.ndarray:
