@@ -1,13 +1,17 @@
 """Host-side checks of the C ABI (no GPU needed): the library builds for
-sm_103a, loads, exports every function include/ph.h declares, and its
-step-size controller (the code the device controller runs) agrees with the
-oracle's independent implementation on scripted and random outcome sequences."""
+sm_103a, loads, exports every function include/ph.h declares, its structs
+and the oracle's have the field names and types, in order, that their
+headers declare, and its step-size controller (the code the device
+controller runs) agrees with the oracle's independent implementation on
+scripted and random outcome sequences."""
+import ctypes as C
 import os
 import re
 
 import numpy as np
 import pytest
 
+import oracle
 from paper_1501_06625_gb300 import build, libph, synth
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -76,3 +80,51 @@ def test_controller_hand_trace(lib):
     ts, st = _ph_drive(synth.default_params(2, max_dt=0.25, min_dt=0.01), [1, 0, 1, 1, 1, 1, 0, 1, 1])
     assert ts == [0.25, 0.5, 0.375, 0.5, 0.625, 0.875, 1.0, 1.0]
     assert st["done"] == 1 and st["status"] == libph.PH_OK
+
+
+# ---- struct layouts: the header's typedefs against the ctypes mirrors -----------
+
+_CTYPES = {"double": C.c_double, "int32_t": C.c_int32, "int64_t": C.c_int64}
+
+
+def _header_structs(path):
+    """{typedef name: [(field, C type name), ...]} of the anonymous-struct
+    typedefs of a C header, fields in declaration order (comments removed,
+    `type a, b;` lists expanded)."""
+    import re
+    src = open(path).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for body, name in re.findall(r"typedef struct\s*\{(.*?)\}\s*(\w+)\s*;", src, flags=re.S):
+        fields = []
+        for decl in body.split(";"):
+            decl = decl.strip()
+            if not decl:
+                continue
+            ctype, rest = decl.split(None, 1)
+            fields += [(f.strip(), ctype) for f in rest.split(",")]
+        out[name] = fields
+    return out
+
+
+def _check_mirror(structs, cname, pyclass):
+    fields = structs[cname]
+    mirror = [(n, t) for n, t in pyclass._fields_]
+    assert [n for n, _ in fields] == [n for n, _ in mirror], cname
+    for (_, ct), (_, pt) in zip(fields, mirror):
+        assert _CTYPES[ct] is pt, (cname, ct, pt)
+
+
+def test_library_structs_match_the_header():
+    structs = _header_structs(os.path.join(ROOT, "include", "ph.h"))
+    for cname, py in (("ph_track_params", libph.TrackParams), ("ph_path_stats", libph.PathStats),
+                      ("ph_step_record", libph.StepRecord), ("ph_server_config", libph.ServerConfig),
+                      ("ph_ctrl_state", libph.CtrlState)):
+        _check_mirror(structs, cname, py)
+
+
+def test_oracle_structs_match_its_header():
+    structs = _header_structs(os.path.join(ROOT, "oracle", "oracle.h"))
+    for cname, py in (("orc_params", oracle.Params), ("orc_stats", oracle.Stats),
+                      ("orc_record", oracle.Record), ("orc_ctrl", oracle.Ctrl)):
+        _check_mirror(structs, cname, py)
