@@ -505,6 +505,26 @@ def monodromy_leg(libph, synth, ctx, torch, dev, seed, segment):
                 "per_step_vs_paper": (1e3 * pgpu / pm) / per_step}
             if whole and st == libph.PH_OK:
                 out[f"cyclic{n}_{name}"]["per_path_vs_paper"] = 1e3 * pgpu / ms
+            if L == 4 and n >= 64:
+                # the precision form on the same path (Newton systems in double,
+                # residual and update in QD); it leaves the rest of the path to QD
+                # once a failed double corrector contracted only linearly
+                xm = torch.empty_like(dx0)
+                e0.record(stream)
+                st2, sd2, _ = libph.ph_track_path(ctx.h, f, g, dg, dx0, dict(params, lin_prec=1), xm)
+                e1.record(stream)
+                e1.synchronize()
+                ms2 = e0.elapsed_time(e1)
+                r2 = {"status": int(st2), "t_final": sd2["t_final"], "steps": sd2["steps"],
+                      "accepted": sd2["accepted"], "newton_iters": sd2["newton_iters"],
+                      "solves_f64": sd2["solves_f64"], "escalated": sd2["escalated"],
+                      "wp_rest": sd2["wp_rest"], "ms": ms2,
+                      "ms_per_step": ms2 / max(1, sd2["steps"]), "graph_built_in_timing": True}
+                if whole and st2 == libph.PH_OK:
+                    dd = (xm.cpu().numpy() - xo.cpu().numpy())[::-1].sum(axis=0)
+                    r2["end_point_diff_vs_plain"] = float(np.abs(dd[0] + 1j * dd[1]).max())
+                    r2["vs_plain"] = ms / ms2
+                out[f"cyclic{n}_{name}"]["precision_form"] = r2
             ctx.free(f)
             ctx.free(g)
     return out

@@ -150,6 +150,10 @@ typedef struct {
    * below sqrt(tol_dx) was followed by another.
    * A corrector that fails while its updates are still large follows the
    * working-precision iterates to kappa u_low, and so does their failure.
+   * A failed corrector whose last three updates contracted, but more slowly
+   * than quadratically (ratios r1, r0 below 1 with r0 > r1^1.5: its solves
+   * limit it, whatever kappa shows), is corrected again in working precision,
+   * and the rest of the path runs in working precision (stats wp_rest).
    * Steps to t >= endgame_t run in working precision throughout (the end
    * game).
    * ph_track_paths and the serving loop take 0..3; ph_track_path takes 0 and
@@ -182,7 +186,9 @@ typedef struct {
   int32_t solves_f32;   /* ... and in single                                       */
   int32_t escalated;    /* steps whose low-precision corrector failed and that
                            were corrected again one precision up                 */
-  int32_t reserved;
+  int32_t wp_rest;      /* 1 if the precision form left the rest of the path to
+                           working precision (a failed low-precision corrector
+                           whose updates contracted only linearly)              */
   double cond;          /* condition estimate of the last low-precision solve    */
 } ph_path_stats;
 

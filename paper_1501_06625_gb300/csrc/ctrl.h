@@ -11,6 +11,8 @@
 // (PH_MAXSTEPS).  A fixed schedule (fixed_steps > 0) tries t_j = j / fixed_steps
 // and accepts every step.
 #pragma once
+#include <math.h>
+
 #include "ph.h"
 
 #ifdef __CUDACC__
@@ -68,3 +70,14 @@ PH_HD void ctrl_report(ph_ctrl_state *c, const ph_track_params *p, double t_new,
 // u_double above this: below it the double corrector contracts like the
 // working-precision one.
 constexpr double kEscalateRho = 1e-6;
+
+// Whether three successive updates d2, d1, d0 of a low-precision corrector
+// contract, but more slowly than Newton's quadratic convergence.  With
+// r1 = d1 / d2 and r0 = d0 / d1, quadratic convergence gives r0 ~ r1^2; a
+// corrector limited by its solves (relative error kappa u_low per iteration)
+// gives r0 ~ r1.  The test: both ratios below 1 and r0 > r1^1.5.
+PH_HD bool linear_contraction(double d2, double d1, double d0) {
+  if (!(d2 > 0.0) || !(d1 > 0.0) || !(d0 >= 0.0) || !(d0 < INFINITY)) return false;
+  const double r1 = d1 / d2, r0 = d0 / d1;
+  return r1 < 1.0 && r0 < 1.0 && r0 > r1 * sqrt(r1);
+}

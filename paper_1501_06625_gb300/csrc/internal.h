@@ -61,7 +61,8 @@ struct PathState {
   // the precision form (lin_prec 1): the precision of the current solve (0
   // working, 1 double), the scale exponent of the right-hand side, the
   // escalation state of the step, and the gates of the two kernel sets
-  int32_t lin, scale_e, force, escalate, onpath, retry, pass;
+  int32_t lin, scale_e, force, escalate, onpath, retry, pass, linear, wp_rest;
+  double dxn2;                  // the update before the last one (this pass)
   int32_t gate_wp, gate_lp;
   int32_t solves_f64, escalated;
   double cond;

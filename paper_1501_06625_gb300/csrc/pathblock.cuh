@@ -257,7 +257,8 @@ __device__ void track_job(const Job &a, double *smem) {
   __shared__ double s_tn, s_last, s_res, s_dxn, s_dxmax, s_xmax;
   __shared__ unsigned long long s_resbits;
   __shared__ ph_path_stats s_st;
-  __shared__ int s_lin, s_scale_e, s_force, s_escalate, s_onpath;
+  __shared__ int s_lin, s_scale_e, s_force, s_escalate, s_onpath, s_linear, s_wp;
+  __shared__ double s_dxn2;
   __shared__ double s_cond, s_kappa;
 
   const int n = a.n, N = a.N, tid = threadIdx.x;
@@ -285,6 +286,7 @@ __device__ void track_job(const Job &a, double *smem) {
     ctrl_init(&s_ctrl, &a.p);
     memset(&s_st, 0, sizeof s_st);
     s_cond = INFINITY;
+    s_wp = 0;
     s_head = 0;
     s_count = 1;
     s_t[0] = 0.0;
@@ -350,6 +352,7 @@ __device__ void track_job(const Job &a, double *smem) {
         s_iters = 0;
         s_escalate = 0;
         s_onpath = 0;
+        s_linear = 0;
       }
       __syncthreads();
       for (int i = tid; i < n; i += kBT) {
@@ -370,7 +373,7 @@ __device__ void track_job(const Job &a, double *smem) {
         __syncthreads();
         if (tid == 0) {                              // the precision of this iteration's solve
           int lin = a.p.lin_prec;
-          if (tn >= endgame || s_force == 2) lin = 0;
+          if (tn >= endgame || s_force == 2 || s_wp) lin = 0;
           // automatic: single on a step's first iteration and while the current
           // error, estimated as the square of the last update, is at least the
           // single-precision solve's relative error kappa u_single
@@ -501,6 +504,8 @@ __device__ void track_job(const Job &a, double *smem) {
           const double d = ms != PH_OK ? NAN : (lin == 0 ? s_dxmax : ldexp(s_dxmax, e));
           const bool prev_on_path = lin != 0 && s_upd >= 1 && s_dxn <= sqrt(a.p.tol_dx);
           if (prev_on_path) s_onpath = 1;
+          if (lin != 0 && s_upd >= 2 && linear_contraction(s_dxn2, s_dxn, d)) s_linear = 1;
+          s_dxn2 = s_dxn;
           s_dxn = d;
           s_st.dx = d;
           s_upd += 1;
@@ -523,6 +528,14 @@ __device__ void track_job(const Job &a, double *smem) {
       // sqrt(tol_dx) followed by another: the working-precision corrector
       // would have succeeded
       if (tid == 0 && !s_ok && s_onpath) s_escalate = 2;
+      // a low-precision corrector that failed while contracting only linearly:
+      // its solves limit it, the working-precision corrector might not fail;
+      // the rest of the path runs in working precision
+      if (tid == 0 && !s_ok && s_linear && !fixed) {
+        s_escalate = 2;
+        s_wp = 1;
+        s_st.wp_rest = 1;
+      }
       __syncthreads();
       if (pass == 0 && !s_ok && s_escalate && !fixed) {
         if (tid == 0) {

@@ -96,8 +96,9 @@ __global__ void k_step_begin(PathState *st, ph_track_params p, int L) {
   st->skip_nt = 0;
   st->escalate = 0;
   st->onpath = 0;
+  st->linear = 0;
   const double endgame = p.endgame_t > 0.0 ? p.endgame_t : 1.0;
-  st->lin = (p.lin_prec == 1 && !(tn >= endgame) && st->force != 2) ? 1 : 0;
+  st->lin = (p.lin_prec == 1 && !(tn >= endgame) && st->force != 2 && !st->wp_rest) ? 1 : 0;
   set_gates(st);
 }
 
@@ -255,6 +256,8 @@ __global__ void k_check_dx(PathState *st, ph_track_params p, const double *__res
   if (lin) d = ldexp(d, st->scale_e);
   const bool prev_on_path = lin && st->nt_updates >= 1 && st->dxn <= sqrt(p.tol_dx);
   if (prev_on_path) st->onpath = 1;
+  if (lin && st->nt_updates >= 2 && linear_contraction(st->dxn2, st->dxn, d)) st->linear = 1;
+  st->dxn2 = st->dxn;
   st->dxn = d;
   st->dx_last = d;
   st->nt_updates += 1;
@@ -303,6 +306,12 @@ __global__ void k_step_end(PathState *st, ph_track_params p, double *__restrict_
     s_retry = 0;
     if (p.lin_prec != 0 && !ok) {
       if (st->onpath) st->escalate = 2;
+      // a failed low-precision corrector that contracted only linearly: its
+      // solves limit it; the rest of the path runs in working precision
+      if (st->linear && p.fixed_steps <= 0) {
+        st->escalate = 2;
+        st->wp_rest = 1;
+      }
       if (st->pass == 0 && st->escalate && p.fixed_steps <= 0) {
         st->force = st->escalate;
         st->escalated += 1;
@@ -661,7 +670,7 @@ extern "C" ph_status ph_track_path(ph_ctx *ctx, const ph_system *f, const ph_sys
     stats->solves_f64 = hs.solves_f64;
     stats->solves_f32 = 0;
     stats->escalated = hs.escalated;
-    stats->reserved = 0;
+    stats->wp_rest = hs.wp_rest;
     stats->cond = hs.cond;
   }
   if (status == PH_TIMEOUT) return ph_fail(ctx, PH_TIMEOUT, "ph_track_path: a grid barrier timed out");

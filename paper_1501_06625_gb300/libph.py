@@ -40,7 +40,7 @@ class PathStats(C.Structure):
                 ("rejected", C.c_int32), ("newton_iters", C.c_int32), ("updates", C.c_int32),
                 ("t_final", C.c_double), ("res", C.c_double), ("dx", C.c_double),
                 ("launches", C.c_int64), ("solves_f64", C.c_int32), ("solves_f32", C.c_int32),
-                ("escalated", C.c_int32), ("reserved", C.c_int32), ("cond", C.c_double)]
+                ("escalated", C.c_int32), ("wp_rest", C.c_int32), ("cond", C.c_double)]
 
 
 class StepRecord(C.Structure):

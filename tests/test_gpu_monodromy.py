@@ -174,3 +174,25 @@ def test_monodromy_precision_form_ends_on_the_component(ctx):
     assert st0 == libph.PH_OK and st1 == libph.PH_OK and s1["solves_f64"] > 0
     assert _family_gap(x1, L) < 1e3 * U[L]
     assert cabs_diff(x0, x1).max() <= 1e3 * params["tol_dx"]
+
+
+def test_precision_form_leaves_an_ill_conditioned_path_to_working_precision(ctx):
+    """cyclic144 in QD: the double solves of these least-squares Jacobians do
+    not contract (kappa u_double near 1, far above what the pivot ratio
+    shows).  The first failed low-precision corrector whose updates contracted
+    only linearly sends the step, and the rest of the path, to working
+    precision, which accepts steps where the double corrector accepted none."""
+    L, n = 4, 144
+    F, G, gam, x0 = synth.cyclic_monodromy(1, n)
+    f, g = ctx.load(F, L), ctx.load(G, L)
+    xs = soa_from_complex(x0, L)
+    gs = soa_from_complex([gam], L).reshape(L, 2)
+    params = synth.default_params(L, max_newton=6, max_steps=11, fixed_rows=1, lin_prec=1)
+    x = np.zeros_like(xs)
+    st, stats, log = libph.ph_track_path(ctx.h, f, g, gs, xs, params, x, log_cap=12)
+    assert stats["wp_rest"] == 1 and stats["escalated"] >= 1
+    assert stats["accepted"] >= 1 and stats["t_final"] > 0.0
+    xo = np.zeros((1,) + xs.shape)
+    sb, _ = libph.ph_track_paths(ctx.h, f, g, gs, np.ascontiguousarray(xs[None]), params, xo)
+    assert (sb[0]["steps"], sb[0]["accepted"], sb[0]["wp_rest"]) == \
+        (stats["steps"], stats["accepted"], 1)
