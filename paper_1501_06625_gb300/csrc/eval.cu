@@ -9,7 +9,7 @@
 //          factor CF = prod x_j^{a_j - 1} from the power table is folded into
 //          the coefficient, then the Speelpenning product of the v variables is
 //          differentiated in the reverse mode (forward prefix products, backward
-//          suffix and cross products, Table "Evaluating four monomials"):
+//          suffix and cross products, Section 3.2, Table 1):
 //            d/dx_j (c x^a) = a_j * (c CF x_1..x_{j-1}) * (x_{j+1}..x_v).
 //          Monomials are sorted by v so a warp runs monomials of equal length,
 //          and the instructions are stored position-major so lanes read

@@ -1,7 +1,7 @@
 """The paper's worked example of reverse-mode differentiation of products of
-variables (Section 3.2, Table "Evaluating four monomials"), as a golden
-fixture for the oracle: at dyadic points every value and partial derivative is
-exact, so the Jacobian must equal the products of the other variables."""
+variables (Section 3.2, Table 1), as a golden fixture for the oracle: at
+dyadic points every value and partial derivative is exact, so the Jacobian
+must equal the products of the other variables."""
 import os
 from fractions import Fraction
 
