@@ -149,3 +149,25 @@ def test_family_points_on_the_slices(m):
     d = np.abs(pts[:, None, :] - pts[None, :, :]).max(axis=2) + np.eye(m)
     assert d.min() > 1e-6
     assert np.abs(pts - loop["x0"][None, :]).max(axis=1).min() < 1e-12
+
+
+def test_loop_halves_swap_the_slices():
+    """The way back moves K to L: its target carries the start system's slices
+    L (with their two-limb constants) after the cyclic rows, its start system
+    the target's slices K with empty cyclic rows; the way out is the fixed-row
+    form of cyclic_monodromy."""
+    n, m = 16, 4
+    r = m - 1
+    loop = synth.cyclic_monodromy_loop(6, n)
+    F, G = loop["out"]
+    Fb, Gb = loop["back"]
+    F0, G0, _, x0 = synth.cyclic_monodromy(6, n)
+    assert np.array_equal(F.coeff, F0.coeff) and np.array_equal(G.coeff, G0.coeff)
+    assert np.array_equal(x0, loop["x0"])
+    k = r * (n + 1)
+    assert np.array_equal(Fb.coeff[-k:], G.coeff[-k:])
+    assert np.array_equal(Fb.coeff_lo[-k:], G.coeff_lo[-k:])
+    assert np.array_equal(Gb.coeff, F.coeff[-k:])
+    assert np.array_equal(Fb.coeff[:-k], F.coeff[:-k])          # the cyclic rows
+    assert (Gb.term_ptr[:n + 1] == 0).all() and (G.term_ptr[:n + 1] == 0).all()
+    assert Fb.N == Gb.N == F.N == n + r
