@@ -852,6 +852,13 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        # the legs that describe one GPU (serving, precision form, cyclic and
+        # monodromy, the n = 512 solve) run in the one-GPU run; a run on N GPUs
+        # measures the replicated step and holds its GPUs no longer than that
+        args.serve_requests = 0
+        args.precision_paths = 0
+        args.no_cyclic = True
+        args.no_sparse = True
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     build.build()
@@ -987,7 +994,7 @@ def main():
                    "kernel_ms": dict(zip(names, k5)), "ops_per_launch": o5}
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         it_c, wall_c, pcs_c = oracle_sample(wl, seconds=args.cpu_seconds)
         cpu = {"value": it_c / wall_c, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"first {pcs_c} predictor-corrector steps of the {wl.name} path "
