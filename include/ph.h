@@ -323,6 +323,11 @@ void ph_ctrl_init(ph_ctrl_state *c, const ph_track_params *p);
 double ph_ctrl_next_t(ph_ctrl_state *c, const ph_track_params *p);
 /* Reports the corrector's outcome at t_new. */
 void ph_ctrl_report(ph_ctrl_state *c, const ph_track_params *p, double t_new, int success);
+/* The precision form's test on three successive update norms d2, d1, d0 of a
+ * low-precision corrector (see ph_track_params.lin_prec): 1 if they contract
+ * (d1/d2 < 1, d0/d1 < 1) more slowly than quadratically (d0/d1 > (d1/d2)^1.5),
+ * else 0; 0 for non-positive or non-finite input. */
+int ph_ctrl_linear_contraction(double d2, double d1, double d0);
 
 /* Measurement support (Section 5 reports per-kernel times; the roofline of
  * this FP64-bound path needs the FP64 rate of the device it runs on).

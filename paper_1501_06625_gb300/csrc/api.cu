@@ -204,3 +204,6 @@ extern "C" double ph_ctrl_next_t(ph_ctrl_state *c, const ph_track_params *p) { r
 extern "C" void ph_ctrl_report(ph_ctrl_state *c, const ph_track_params *p, double t_new, int success) {
   ctrl_report(c, p, t_new, success);
 }
+extern "C" int ph_ctrl_linear_contraction(double d2, double d1, double d0) {
+  return linear_contraction(d2, d1, d0) ? 1 : 0;
+}

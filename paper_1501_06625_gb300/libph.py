@@ -63,7 +63,7 @@ EXPORTS = ["ph_init", "ph_destroy", "ph_last_error", "ph_system_load", "ph_syste
            "ph_ctrl_report", "ph_version", "ph_profile_newton", "ph_fp64_peak",
            "ph_mgs_solve_static", "ph_track_paths", "ph_server_create", "ph_server_submit",
            "ph_server_poll", "ph_server_wait", "ph_server_info", "ph_server_destroy",
-           "ph_server_job_bytes", "ph_mgs_variant", "ph_sum_lanes"]
+           "ph_server_job_bytes", "ph_mgs_variant", "ph_sum_lanes", "ph_ctrl_linear_contraction"]
 
 
 class PhError(RuntimeError):
@@ -101,6 +101,8 @@ def lib():
             L.ph_ctrl_report.argtypes = [C.POINTER(CtrlState), C.POINTER(TrackParams), C.c_double,
                                          C.c_int]
             L.ph_ctrl_report.restype = None
+            L.ph_ctrl_linear_contraction.argtypes = [C.c_double, C.c_double, C.c_double]
+            L.ph_ctrl_linear_contraction.restype = C.c_int
             L.ph_version.restype = C.c_char_p
             L.ph_profile_newton.argtypes = [vp, vp, vp, vp, C.c_int, vp, vp, C.c_int, dp]
             L.ph_mgs_variant.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int),
@@ -316,6 +318,10 @@ def ph_ctrl_next_t(state: CtrlState, p: TrackParams) -> float:
 
 def ph_ctrl_report(state: CtrlState, p: TrackParams, t_new: float, success: bool):
     lib().ph_ctrl_report(C.byref(state), C.byref(p), float(t_new), int(success))
+
+
+def ph_ctrl_linear_contraction(d2: float, d1: float, d0: float) -> bool:
+    return bool(lib().ph_ctrl_linear_contraction(float(d2), float(d1), float(d0)))
 
 
 def ph_profile_newton(ctx, f, g, gamma, k, t, x, reps: int = 10):

@@ -128,3 +128,31 @@ def test_oracle_structs_match_its_header():
     for cname, py in (("orc_params", oracle.Params), ("orc_stats", oracle.Stats),
                       ("orc_record", oracle.Record), ("orc_ctrl", oracle.Ctrl)):
         _check_mirror(structs, cname, py)
+
+
+def test_linear_contraction_rule(lib):
+    """The precision form's test on three successive update norms (the code
+    the device runs): quadratic convergence passes, a corrector limited by
+    its solves (a constant contraction) is caught; stalling, diverging and
+    degenerate input are not."""
+    lc = libph.ph_ctrl_linear_contraction
+    assert not lc(1e-2, 1e-4, 1e-8)            # r0 = r1^2
+    assert lc(1e-3, 1e-6, 1e-9)                # r0 = r1
+    assert not lc(1e-3, 1e-3, 1e-3)            # not contracting
+    assert not lc(1e-3, 1e-2, 1e-1)            # diverging
+    for bad in ((0.0, 1.0, 0.5), (1.0, 0.0, 0.0), (1.0, 0.5, float("inf")),
+                (1.0, 0.5, float("nan")), (-1.0, 0.5, 0.25)):
+        assert not lc(*bad), bad
+
+    def updates(delta, x, steps=3):
+        # Newton on x^2 - 2 with the derivative off by a relative delta, as a
+        # low-precision solve of relative error delta would leave it
+        out = []
+        for _ in range(steps):
+            dx = (x * x - 2.0) / (2.0 * x * (1.0 + delta))
+            out.append(abs(dx))
+            x -= dx
+        return out
+
+    assert not lc(*updates(0.0, 1.5))          # exact derivative: quadratic
+    assert lc(*updates(1e-2, 2.0 ** 0.5 + 1e-3))   # error contracts by ~delta per step
