@@ -171,3 +171,39 @@ def test_loop_halves_swap_the_slices():
     assert np.array_equal(Fb.coeff[:-k], F.coeff[:-k])          # the cyclic rows
     assert (Gb.term_ptr[:n + 1] == 0).all() and (G.term_ptr[:n + 1] == 0).all()
     assert Fb.N == Gb.N == F.N == n + r
+
+
+def test_oracle_monodromy_loops_find_the_degree():
+    """The oracle alone, with the cyclic rows held fixed, runs monodromy loops
+    on cyclic 4-roots (m = 2): out to the slices K and back to L with random
+    alpha and beta, from the points found so far.  It finds the m = 2 points of
+    the component on L, each equal to a point of the family's linear
+    parametrization, and no other."""
+    from paper_1501_06625_gb300 import monodromy
+    n, m, L = 4, 2, 2
+    loop = synth.cyclic_monodromy_loop(2, n)
+    F, G = loop["out"]
+    Fb, Gb = loop["back"]
+    oF, oG, oFb, oGb = (oracle.System(s, L) for s in (F, G, Fb, Gb))
+    rng = synth.Rng(11)
+    p = synth.default_params(L, max_newton=5, max_steps=3000, fixed_rows=1)
+    x0 = np.zeros((L, 2, n))
+    x0[0, 0], x0[0, 1] = loop["x0"].real, loop["x0"].imag
+    pts = [x0]
+    for i in range(6):
+        ga, gb = np.zeros((L, 2)), np.zeros((L, 2))
+        a, b = rng.unit_complex(), rng.unit_complex()
+        ga[0], gb[0] = [a.real, a.imag], [b.real, b.imag]
+        st, y, _, _ = oracle.track(oF, pts[i % len(pts)], ga, p, g=oG)
+        assert st == oracle.OK
+        st, z, _, _ = oracle.track(oFb, y, gb, p, g=oGb)
+        assert st == oracle.OK
+        zl = z[0, 0] + 1j * z[0, 1]
+        if all(np.abs(zl - (q[0, 0] + 1j * q[0, 1])).max() > 1e-8 for q in pts):
+            pts.append(z)
+    assert len(pts) == m
+    c = G.coeff.reshape(m - 1, n + 1)
+    ref = monodromy.family_points_on_slices(
+        m, c[:, :n], c[:, n] + G.coeff_lo.reshape(m - 1, n + 1)[:, n])
+    for q in pts:
+        assert np.abs(ref - (q[0, 0] + 1j * q[0, 1])[None, :]).max(axis=1).min() < 1e-12
