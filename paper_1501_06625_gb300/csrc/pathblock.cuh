@@ -340,9 +340,12 @@ __device__ void track_job(const Job &a, double *smem) {
     // precision if a double solve had kappa u_double above kEscalateRho (the
     // estimate is only a lower bound of kappa) or if it failed although an
     // update below sqrt(tol_dx) was followed by another one (the working-
-    // precision corrector would have succeeded there).  A corrector that fails
-    // while its updates are still large takes the working-precision iterates,
-    // to kappa u_low, and fails as that one would: the step size halves.
+    // precision corrector would have succeeded there), or if its last three
+    // updates contracted more slowly than quadratically (linear_contraction:
+    // its solves limit it, whatever the estimate shows; the rest of the path
+    // then runs in working precision).  A corrector that fails while its
+    // updates are still large takes the working-precision iterates, to
+    // kappa u_low, and fails as that one would: the step size halves.
     for (int pass = 0;; ++pass) {
       if (tid == 0) {
         s_last = a.p.max_res;
