@@ -64,6 +64,11 @@ class Stats(C.Structure):
                 ("t_final", C.c_double), ("res", C.c_double), ("dx", C.c_double)]
 
 
+class MixedStats(C.Structure):
+    _fields_ = [("solves_f64", C.c_int32), ("escalated", C.c_int32), ("wp_rest", C.c_int32),
+                ("reserved", C.c_int32), ("cond", C.c_double)]
+
+
 class Record(C.Structure):
     _fields_ = [("t", C.c_double), ("res", C.c_double), ("dx", C.c_double),
                 ("accepted", C.c_int32), ("updates", C.c_int32)]
@@ -102,6 +107,10 @@ def lib():
                                     C.POINTER(C.c_int)]
             L.orc_replay.argtypes = [C.c_void_p, C.c_void_p, _dp, _dp, C.POINTER(Params),
                                      C.POINTER(Record), C.c_int, _dp]
+            L.orc_track_mixed.argtypes = [C.c_void_p, C.c_void_p, _dp, _dp, C.POINTER(Params),
+                                          C.c_double, _dp, C.POINTER(Stats),
+                                          C.POINTER(MixedStats), C.POINTER(Record), C.c_int,
+                                          C.POINTER(C.c_int)]
             L.orc_lowprec_solve.argtypes = [C.c_int, C.c_int, C.c_int, _dp, _dp, _dp, _dp]
             L.orc_newton_mixed.argtypes = [C.c_void_p, C.c_void_p, _dp, C.c_int, C.c_double,
                                            _dp, C.POINTER(Params), C.c_int, C.c_int,
@@ -329,6 +338,31 @@ def track(f: System, x0, gamma, params: dict, g: System | None = None, log_cap: 
     status = lib().orc_track(f.h, g.h if g else None, _d(gm), _d(x0), C.byref(p), _d(xo),
                              C.byref(st), log, log_cap, C.byref(nlog))
     stats = {name: getattr(st, name) for name, _ in Stats._fields_}
+    recs = [dict(t=log[i].t, res=log[i].res, dx=log[i].dx, accepted=log[i].accepted,
+                 updates=log[i].updates) for i in range(nlog.value)]
+    return status, xo, stats, recs
+
+
+def track_mixed(f: System, x0, gamma, params: dict, g: System | None = None,
+                log_cap: int = 20000):
+    """Track one path in the precision form (Newton systems in double; the
+    rules at orc_track_mixed); params' endgame_t as in the library.  Returns
+    (status, x_end, stats dict (with solves_f64, escalated, wp_rest, cond),
+    log list)."""
+    L = f.L
+    x0 = _f64(x0)
+    gm = _gamma(gamma, L)
+    p = make_params(params)
+    xo = np.zeros_like(x0)
+    st = Stats()
+    ms = MixedStats()
+    log = (Record * log_cap)()
+    nlog = C.c_int(0)
+    status = lib().orc_track_mixed(f.h, g.h if g else None, _d(gm), _d(x0), C.byref(p),
+                                   float(params.get("endgame_t", 0.0)), _d(xo), C.byref(st),
+                                   C.byref(ms), log, log_cap, C.byref(nlog))
+    stats = {name: getattr(st, name) for name, _ in Stats._fields_}
+    stats.update({name: getattr(ms, name) for name, _ in MixedStats._fields_ if name != "reserved"})
     recs = [dict(t=log[i].t, res=log[i].res, dx=log[i].dx, accepted=log[i].accepted,
                  updates=log[i].updates) for i in range(nlog.value)]
     return status, xo, stats, recs

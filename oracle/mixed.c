@@ -184,3 +184,89 @@ int orc_newton_mixed(const orc_system *f, const orc_system *g, const double *gam
   free(h); free(J); free(jl); free(rl); free(d);
   return success;
 }
+
+/* Whether three successive update norms d2, d1, d0 contract (both ratios
+   below 1) more slowly than quadratically (d0/d1 > (d1/d2)^1.5). */
+static int contracts_linearly(double d2, double d1, double d0) {
+  if (!(d2 > 0.0) || !(d1 > 0.0) || !(d0 >= 0.0) || !isfinite(d0)) return 0;
+  double r1 = d1 / d2, r0 = d0 / d1;
+  return r1 < 1.0 && r0 < 1.0 && r0 > r1 * sqrt(r1);
+}
+
+/* One step's corrector of the precision form with the signals the step
+   control needs (the rules stated in oracle.h at orc_track_mixed). */
+int orc_corrector_mixed(const orc_system *f, const orc_system *g, const double *gamma, int k,
+                        double t, double *x, const orc_params *p, int fixed, int lin,
+                        orc_mixed_out *o) {
+  int L = f->L, N = f->N, n = f->n;
+  memset(o, 0, sizeof *o);
+  o->res = o->dxn = NAN;
+  o->cond = INFINITY;
+  if (lin != 1) return -ORC_EINVAL;
+  double *h = malloc(sizeof(double) * 2 * L * N);
+  double *J = malloc(sizeof(double) * 2 * L * (size_t)N * n);
+  double *jl = malloc(sizeof(double) * 2 * (size_t)N * n);
+  double *rl = malloc(sizeof(double) * 2 * N);
+  double *d = malloc(sizeof(double) * 2 * n);
+  if (!h || !J || !jl || !rl || !d) {
+    free(h); free(J); free(jl); free(rl); free(d);
+    return -ORC_ENOMEM;
+  }
+  const double u_lin = ldexp(1.0, -53);
+  double tl[ORC_MAXL] = {t, 0.0, 0.0, 0.0};
+  double last = p->max_res, d1 = NAN, d2 = NAN;
+  int success = fixed ? 1 : 0;
+  int max_it = fixed ? p->max_newton : p->max_newton + 1;
+  long NN = (long)N * n;
+  for (int it = 0; it < max_it; it++) {
+    orc_eval(f, g, gamma, k, tl, x, h, J, p->fixed_rows);
+    o->iters++;
+    double r = max_mag_lead(h, N);
+    o->res = r;
+    if (!fixed) {
+      if (!isfinite(r) || r > last) { success = 0; break; }
+      if (r < p->tol_res) { success = 1; break; }
+    }
+    memcpy(jl, J, sizeof(double) * 2 * NN);
+    int e = (r > 0.0 && isfinite(r)) ? ilogb(r) : 0;
+    for (int i = 0; i < N; i++) { rl[i] = -ldexp(h[i], -e); rl[N + i] = -ldexp(h[N + i], -e); }
+    double c = NAN;
+    int st = orc_lowprec_solve(lin, N, n, jl, rl, d, &c);
+    o->solves++;
+    o->cond = st == ORC_OK ? c : INFINITY;
+    if (!(o->cond * u_lin <= 1e-6)) o->escalate = 2;   /* kappa u_low above the threshold */
+    if (st != ORC_OK) {
+      if (!fixed) { success = 0; break; }
+      for (int q = 0; q < 2 * n; q++) d[q] = NAN;
+    }
+    for (int q = 0; q < 2 * n; q++) d[q] = ldexp(d[q], e);
+    double dm = max_mag_lead(d, n);
+    /* the previous update was below sqrt(tol_dx): the working-precision
+       corrector would square it below tol_dx by now */
+    int prev_small = o->updates >= 1 && d1 <= sqrt(p->tol_dx);
+    if (prev_small) o->onpath = 1;
+    if (o->updates >= 2 && contracts_linearly(d2, d1, dm)) o->linear = 1;
+    d2 = d1;
+    d1 = dm;
+    o->dxn = dm;
+    for (int i = 0; i < n; i++) {
+      orc_cplx di;
+      memset(&di, 0, sizeof di);
+      di.re.v[0] = d[i];
+      di.im.v[0] = d[n + i];
+      orc_c_store(L, x, n, i, orc_c_add(L, orc_c_load(L, x, n, i), di));
+    }
+    o->updates++;
+    if (!fixed) {
+      if (!isfinite(dm)) { success = 0; break; }
+      if (dm < p->tol_dx) { success = 1; break; }
+      last = r;
+    }
+    if (o->iters >= p->max_newton && !(prev_small && o->iters < max_it)) {
+      success = fixed ? 1 : 0;
+      break;
+    }
+  }
+  free(h); free(J); free(jl); free(rl); free(d);
+  return success;
+}

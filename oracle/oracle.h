@@ -131,6 +131,40 @@ int orc_replay(const orc_system *f, const orc_system *g, const double *gamma,
                const double *x0, const orc_params *p, const orc_record *log, int nrec,
                double *x_out);
 
+/* ---- the precision form's path tracker (lin = 1: Newton systems in double) ----
+   A step below t = endgame runs the mixed corrector (orc_newton_mixed's
+   iteration) with these rules, restated from the library's precision form:
+   * one iteration beyond max_newton when the previous update was below
+     sqrt(tol_dx) (the working-precision corrector would have squared it below
+     tol_dx by then);
+   * a failed step is corrected once more from the predicted point in working
+     precision when a double solve had kappa_hat u_double above 1e-6 (kappa_hat
+     = max r_kk / min r_kk), when an update below sqrt(tol_dx) was followed by
+     another, or when the last three updates contracted more slowly than
+     quadratically (d0/d1 > (d1/d2)^1.5, both ratios below 1); in the last case
+     the rest of the path runs in working precision;
+   * steps at or beyond endgame, and every step once the path runs in working
+     precision, use the working-precision corrector (orc_newton).
+   Logs record the last pass of each step; statistics count both passes. */
+typedef struct {
+  int32_t iters, updates, escalate, onpath, linear, solves;
+  double res, dxn, cond;
+} orc_mixed_out;
+
+int orc_corrector_mixed(const orc_system *f, const orc_system *g, const double *gamma, int k,
+                        double t, double *x, const orc_params *p, int fixed, int lin,
+                        orc_mixed_out *o);
+
+typedef struct {
+  int32_t solves_f64, escalated, wp_rest, reserved;
+  double cond;                      /* condition estimate of the last double solve */
+} orc_mixed_stats;
+
+int orc_track_mixed(const orc_system *f, const orc_system *g, const double *gamma,
+                    const double *x0, const orc_params *p, double endgame, double *x_out,
+                    orc_stats *st, orc_mixed_stats *ms, orc_record *log, int log_cap,
+                    int *log_len);
+
 /* ---- mixed-precision corrector (mixed.c) ---------------------------------- */
 /* Least squares in low precision (lin = 1: double, 2: single) by textbook MGS
    on [J | rhs]; J is [re|im][col][row] and rhs [re|im][N] in double (rounded to

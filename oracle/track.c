@@ -295,3 +295,97 @@ int orc_replay(const orc_system *f, const orc_system *g, const double *gamma,
   hist_free(&H); free(ts); free(xs); free(x);
   return ORC_OK;
 }
+
+/* The precision form's tracker: Fig. 3 with the mixed corrector and the rules
+   stated in oracle.h. */
+int orc_track_mixed(const orc_system *f, const orc_system *g, const double *gamma,
+                    const double *x0, const orc_params *p, double endgame, double *x_out,
+                    orc_stats *st, orc_mixed_stats *ms, orc_record *log, int log_cap,
+                    int *log_len) {
+  int L = f->L, n = f->n;
+  long pt = (long)2 * L * n;
+  memset(st, 0, sizeof *st);
+  memset(ms, 0, sizeof *ms);
+  if (log_len) *log_len = 0;
+  if (!check_params(p) || !gamma) return st->status = ORC_EINVAL;
+  if (!(endgame > 0.0)) endgame = 1.0;
+  for (long e = 0; e < pt; e++)
+    if (!isfinite(x0[e])) {
+      memcpy(x_out, x0, sizeof(double) * pt);
+      return st->status = ORC_NONFINITE;
+    }
+  history H;
+  int npmax = p->pred_order + 1;
+  double *ts = malloc(sizeof(double) * npmax);
+  double *xs = malloc(sizeof(double) * pt * npmax);
+  double *x = malloc(sizeof(double) * pt);
+  if (!hist_init(&H, L, n, npmax) || !ts || !xs || !x) {
+    hist_free(&H); free(ts); free(xs); free(x);
+    return st->status = ORC_ENOMEM;
+  }
+  hist_push(&H, 0.0, x0);
+  orc_ctrl c;
+  orc_ctrl_init(&c, p);
+  int fixed = p->fixed_steps > 0, wp_rest = 0;
+  for (;;) {
+    double tn = orc_ctrl_next_t(&c, p);
+    if (tn < 0.0) break;
+    int m = H.count < npmax ? H.count : npmax;
+    hist_last(&H, m, ts, xs);
+    orc_predict(L, n, m, ts, xs, tn, x);
+    int iters = 0, upd = 0, ok;
+    double res = NAN, dxn = NAN;
+    if (tn < endgame && !wp_rest) {
+      orc_mixed_out o;
+      ok = orc_corrector_mixed(f, g, gamma, p->relax_k, tn, x, p, fixed, 1, &o);
+      if (ok < 0) { c.status = -ok; break; }
+      st->newton_iters += o.iters;
+      st->updates += o.updates;
+      ms->solves_f64 += o.solves;
+      if (o.solves) ms->cond = o.cond;
+      iters = o.iters; upd = o.updates; res = o.res; dxn = o.dxn;
+      int esc = o.escalate;
+      if (!ok && o.onpath) esc = 2;
+      if (!ok && o.linear && !fixed) {
+        esc = 2;
+        wp_rest = 1;
+      }
+      if (!ok && esc && !fixed) {                /* once more, in working precision */
+        ms->escalated++;
+        orc_predict(L, n, m, ts, xs, tn, x);
+        ok = orc_newton(f, g, gamma, p->relax_k, tn, x, p, fixed, &iters, &upd, &res, &dxn);
+        if (ok < 0) { c.status = -ok; break; }
+        st->newton_iters += iters;
+        st->updates += upd;
+      }
+    } else {
+      ok = orc_newton(f, g, gamma, p->relax_k, tn, x, p, fixed, &iters, &upd, &res, &dxn);
+      if (ok < 0) { c.status = -ok; break; }
+      st->newton_iters += iters;
+      st->updates += upd;
+    }
+    st->steps++;
+    st->res = res;
+    st->dx = dxn;
+    if (ok) st->accepted++; else st->rejected++;
+    if (log && log_len && *log_len < log_cap) {
+      orc_record *r = &log[(*log_len)++];
+      r->t = tn; r->res = res; r->dx = dxn; r->accepted = ok; r->updates = upd;
+    }
+    orc_ctrl_report(&c, p, tn, ok);
+    if (ok) {
+      hist_push(&H, tn, x);
+      if (!fixed && max_mag(L, x, n) > p->max_x) {
+        c.status = ORC_DIVERGED;
+        break;
+      }
+    }
+  }
+  ms->wp_rest = wp_rest;
+  hist_last(&H, 1, ts, xs);
+  memcpy(x_out, xs, sizeof(double) * pt);
+  st->t_final = ts[0];
+  st->status = c.status;
+  hist_free(&H); free(ts); free(xs); free(x);
+  return st->status;
+}
