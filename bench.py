@@ -615,7 +615,7 @@ def monodromy_degree_leg(synth, ctx, seed, sizes):
     return out
 
 
-def serve_leg(libph, synth, ctx, nreq, seed, lin=0, seq_rate=None):
+def serve_leg(libph, synth, ctx, nreq, seed, lin=0, seq_rate=None, sweep_requests=48):
     """A stream of path-tracking requests through the continuous-batching loop
     (ph_server_*).  A pool of 16 systems per (recipe, precision): n =
     round(exp(U[ln 16, ln 64])); the dense recipe (n terms per polynomial over
@@ -624,9 +624,11 @@ def serve_leg(libph, synth, ctx, nreq, seed, lin=0, seq_rate=None):
     request: double-double with probability 0.7, else quad-double; a system of
     the pool; a random total-degree start root; the first 20 predictor-corrector
     steps (adaptive).  Closed loop first (all submitted at once: the capacity),
-    then Poisson arrivals at 0.8 x that capacity (latency under load).  The
-    sequential figure tracks a sample of the same requests one by one with
-    ph_track_path."""
+    then Poisson arrivals at 0.8 x that capacity (latency under load), then
+    Poisson arrivals of the first `sweep_requests` requests at 0.5, 1 and 2 x
+    the sequential capacity.  The sequential figure tracks a sample of the
+    same requests one by one with ph_track_path (measured first when not
+    given)."""
     rng = np.random.default_rng(seed + 1000)
     systems = {}
     reqs = []
@@ -651,6 +653,14 @@ def serve_leg(libph, synth, ctx, nreq, seed, lin=0, seq_rate=None):
         x0[0, 0], x0[0, 1] = z.real, z.imag
         reqs.append((f, gam, x0, synth.default_params(L, max_steps=19, lin_prec=lin)))
 
+    k = min(16, nreq)
+    if seq_rate is None:                        # the plain single-path form
+        t0 = time.perf_counter()
+        for f, gam, x0, params in reqs[:k]:
+            libph.ph_track_path(ctx.h, f, None, gam, x0, dict(params, lin_prec=0),
+                                np.zeros_like(x0))
+        seq_rate = k / (time.perf_counter() - t0)
+
     srv = libph.ph_server_create(ctx.h, max_n=64, pool_bytes=8 << 30, queue_cap=1024)
     try:
         def run(arrivals):
@@ -672,17 +682,19 @@ def serve_leg(libph, synth, ctx, nreq, seed, lin=0, seq_rate=None):
         cap = nreq / wall
         arrivals = np.cumsum(rng.exponential(1.0 / (0.8 * cap), nreq))
         wall2, lats2, _ = run(list(arrivals))
+        # offered loads relative to what sequential single-path tracking sustains
+        m = min(sweep_requests, nreq)
+        sweep = {}
+        for mult in (0.5, 1.0, 2.0):
+            arr = np.cumsum(rng.exponential(1.0 / (mult * seq_rate), m))
+            w3, l3, _ = run(list(arr))
+            sweep[f"{mult:g}x"] = {"offered_per_s": mult * seq_rate, "paths_per_s": m / w3,
+                                   "p50_ms": float(np.percentile(l3, 50)),
+                                   "p99_ms": float(np.percentile(l3, 99))}
         info = libph.ph_server_info(srv)
     finally:
         libph.ph_server_destroy(srv)
 
-    k = min(16, nreq)
-    if seq_rate is None:                        # the plain single-path form
-        t0 = time.perf_counter()
-        for f, gam, x0, params in reqs[:k]:
-            libph.ph_track_path(ctx.h, f, None, gam, x0, dict(params, lin_prec=0),
-                                np.zeros_like(x0))
-        seq_rate = k / (time.perf_counter() - t0)
     return {"requests": nreq, "lin_prec": lin,
             "mix": "n log-uniform in [16,64]; dense/sparse 50/50; DD/QD 70/30; "
                    "20 adaptive steps per request; 16 systems per recipe and precision",
@@ -692,6 +704,7 @@ def serve_leg(libph, synth, ctx, nreq, seed, lin=0, seq_rate=None):
             "poisson_0.8": {"offered_per_s": 0.8 * cap, "paths_per_s": nreq / wall2,
                             "p50_ms": float(np.percentile(lats2, 50)),
                             "p99_ms": float(np.percentile(lats2, 99))},
+            "poisson_vs_sequential_capacity": {"requests_per_rate": m, "rates": sweep},
             "sequential_single_path": {"paths_per_s": seq_rate, "sample": k,
                                        "form": "ph_track_path, all DD/QD"},
             "vs_sequential": cap / seq_rate,

@@ -1,0 +1,73 @@
+"""Host logic of bench.py's serving leg against a fake library, no GPU: the
+sequential rate is measured before the server runs, every request of the
+closed loop, the Poisson stream and the sweep of offered loads (0.5, 1 and 2
+x the sequential capacity) is submitted and waited for, and the figures come
+out with the keys the JSON line carries."""
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+from paper_1501_06625_gb300 import synth  # noqa: E402
+
+
+class FakeLib:
+    def __init__(self):
+        self.submitted, self.waited, self.tracked = 0, 0, 0
+
+    def ph_server_create(self, h, max_n, pool_bytes, queue_cap):
+        return object()
+
+    def ph_server_submit(self, h, srv, f, g, gam, x0, params):
+        self.submitted += 1
+        return self.submitted
+
+    def ph_server_wait(self, h, srv, jid, timeout_ms):
+        self.waited += 1
+        return {"status": 0, "newton_iters": 4}, 2.0
+
+    def ph_server_info(self, srv):
+        return {"kernel_launches": 3}
+
+    def ph_server_destroy(self, srv):
+        pass
+
+    def ph_track_path(self, h, f, g, gam, x0, params, x):
+        self.tracked += 1
+        time.sleep(0.002)
+        return 0, {}, []
+
+
+class FakeCtx:
+    h = None
+
+    def load(self, spec, L):
+        return (spec.n, L)
+
+
+def test_serving_leg_sweeps_offered_loads():
+    lib = FakeLib()
+    nreq, m = 20, 12
+    out = bench.serve_leg(lib, synth, FakeCtx(), nreq, seed=1, sweep_requests=m)
+    assert lib.tracked == 16                                    # the sequential sample
+    expected = min(64, nreq) + nreq + nreq + 3 * m
+    assert lib.submitted == lib.waited == expected
+    seq = out["sequential_single_path"]["paths_per_s"]
+    rates = out["poisson_vs_sequential_capacity"]["rates"]
+    assert sorted(rates) == ["0.5x", "1x", "2x"]
+    for key, mult in (("0.5x", 0.5), ("1x", 1.0), ("2x", 2.0)):
+        assert np.isclose(rates[key]["offered_per_s"], mult * seq)
+        assert rates[key]["paths_per_s"] > 0 and rates[key]["p99_ms"] == 2.0
+    assert out["poisson_vs_sequential_capacity"]["requests_per_rate"] == m
+    for key in ("closed_loop", "poisson_0.8", "vs_sequential", "kernel_launches"):
+        assert key in out
+    # a given sequential rate is used as it is, and nothing is tracked alone
+    lib2 = FakeLib()
+    out2 = bench.serve_leg(lib2, synth, FakeCtx(), nreq, seed=1, seq_rate=50.0, sweep_requests=m)
+    assert lib2.tracked == 0
+    assert np.isclose(out2["poisson_vs_sequential_capacity"]["rates"]["2x"]["offered_per_s"], 100.0)
