@@ -174,6 +174,38 @@ def oracle_sample(wl, seconds: float = 15.0, max_pc_steps: int = 50):
     return iters, wall, pcs
 
 
+def _oracle_path_worker(job):
+    """One independent dense64 path (its own seed) for the all-cores oracle
+    figure: (corrector steps, wall seconds) of its bounded sample."""
+    seed, prec, seconds = job
+    sys.path.insert(0, ROOT)
+    from paper_1501_06625_gb300 import synth
+    it, wall, _ = oracle_sample(synth.dense64(seed, prec), seconds=seconds)
+    return it, wall
+
+
+def oracle_all_cores(seed: int, prec: str, seconds: float, cores: int | None = None) -> dict:
+    """The oracle with one independent path per host core (the dense64 system
+    of seeds seed .. seed + cores - 1), each a bounded sample of about
+    `seconds`; the figure is all corrector steps over the slowest worker's
+    wall time.  Worker processes are started with spawn: a process forked
+    after the first GPU call can hang."""
+    import multiprocessing as mp
+    if not cores:
+        try:
+            cores = len(os.sched_getaffinity(0))        # the cores this process may use
+        except AttributeError:
+            cores = os.cpu_count() or 1
+    jobs = [(seed + i, prec, seconds) for i in range(cores)]
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_path_worker, jobs)
+    its = sum(r[0] for r in res)
+    wall = max(r[1] for r in res)
+    return {"value": its / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"one dense64 {prec} path per core (seeds {seed}..{seed + cores - 1}), "
+                      f"each its first predictor-corrector steps for about {seconds:g} s"}
+
+
 def run_reference(args):
     from paper_1501_06625_gb300 import synth
     rank = int(os.environ.get("RANK", "0"))
@@ -817,6 +849,8 @@ def main():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--qd-steps", type=int, default=None)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-all-cores-seconds", type=float, default=10.0,
+                    help="seconds per core of the all-cores oracle figure (0 skips it)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--control", choices=["device", "host"], default="device",
                     help="step control on the device (one graph per path segment) or on the "
@@ -1012,6 +1046,8 @@ def main():
         cpu = {"value": it_c / wall_c, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"first {pcs_c} predictor-corrector steps of the {wl.name} path "
                          f"({it_c} corrector steps, {wall_c:.1f} s, one thread)"}
+        if args.cpu_all_cores_seconds > 0:
+            cpu["all_cores"] = oracle_all_cores(args.seed, args.prec, args.cpu_all_cores_seconds)
 
     if rank == 0:
         line = {

@@ -71,3 +71,11 @@ def test_serving_leg_sweeps_offered_loads():
     out2 = bench.serve_leg(lib2, synth, FakeCtx(), nreq, seed=1, seq_rate=50.0, sweep_requests=m)
     assert lib2.tracked == 0
     assert np.isclose(out2["poisson_vs_sequential_capacity"]["rates"]["2x"]["offered_per_s"], 100.0)
+
+
+def test_oracle_all_cores_figure():
+    """The all-cores oracle figure: one independent path per worker process
+    (spawned), all corrector steps over the slowest worker's time."""
+    out = bench.oracle_all_cores(1, "dd", 0.5, cores=2)
+    assert out["cores"] == 2 and out["kind"] == "oracle" and out["value"] > 0
+    assert "seeds 1..2" in out["sample"]
