@@ -5,10 +5,12 @@ Submodules, imported on first use:
   libph  -- Python binding of the C ABI in include/ph.h (libph.so, sm_103a)
   build  -- compiles libph.so in tree
   synth  -- seeded synthetic workloads
+  monodromy -- monodromy loops through the serving loop (the degree of a
+               solution set, Section 4.2)
 """
 import importlib
 
-__all__ = ["libph", "build", "synth"]
+__all__ = ["libph", "build", "synth", "monodromy"]
 
 
 def __getattr__(name):
