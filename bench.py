@@ -873,7 +873,7 @@ def main():
     ap.add_argument("--monodromy-loops", type=int, default=152,
                     help="monodromy loops tracked at once through the serving loop (0 skips)")
     ap.add_argument("--monodromy-degree-64", action="store_true",
-                    help="also compute the degree of the cyclic 64-roots set (about a minute)")
+                    help="also compute the degree of the cyclic 64-roots set (about two minutes)")
     ap.add_argument("--no-sparse", action="store_true",
                     help="skip the n=512 QD solver roofline measurement")
     args = ap.parse_args()
