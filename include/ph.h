@@ -168,6 +168,12 @@ typedef struct {
   int32_t fixed_rows;
   double endgame_t;   /* <= 0: 1.0 (only the step that lands on t = 1)           */
   double cond_f32;    /* threshold of lin_prec 3; <= 0: 1e3                       */
+  /* > 0: the corrector's tolerance, for both of its tests, on the steps to
+   * t < 1; the step that lands on t = 1 keeps tol_res and tol_dx, so the end
+   * point has their accuracy.  0: tol_res and tol_dx on every step.  (The
+   * paper's corrector tests, Section 2, Eq. (3), and Fig. 2, name tolerances
+   * without values; how tight they must be on the way is left open.) */
+  double tol_path;
 } ph_track_params;
 
 /* Outcome of one tracked path. */
@@ -290,16 +296,38 @@ ph_status ph_server_job_bytes(ph_server *srv, const ph_system *f, const ph_syste
 /* Stops the loop (running jobs finish first) and frees the server. */
 ph_status ph_server_destroy(ph_server *srv);
 
-/* The variant of the least-squares solve this context uses for an N x n
- * system of precision prec: *cluster = 0 for the grid kernel (one block per
- * column, pivots handed over through L2), C > 0 for the cluster kernel (the
- * matrix in the shared memory of one cluster of C blocks).  The choice is
- * measured once per context and shape on a scratch matrix (the fastest of the
- * two; the grid kernel where the matrix does not fit a cluster);
- * ms_grid / ms_cluster (optional) receive the measured times, -1 where only
- * one variant applies.  The paper has no counterpart (it has one MGS kernel). */
-ph_status ph_mgs_variant(ph_ctx *ctx, ph_prec prec, int N, int n, int *cluster, double *ms_grid,
-                         double *ms_cluster);
+/* The least-squares solve has three variants (the paper has one MGS kernel;
+ * the choice is this library's, per GPU and shape):
+ *   PH_MGS_GRID     one block per column, each pivot handed to the blocks
+ *                   that need it through a flag in L2 (size 0);
+ *   PH_MGS_CLUSTER  the whole matrix in the shared memory of one thread-block
+ *                   cluster, pivots passed by cluster barrier and distributed
+ *                   shared memory (size: the cluster's CTAs, 8 or 16; only
+ *                   where the matrix fits);
+ *   PH_MGS_TILED    the trailing matrix cut into tiles of R row blocks by
+ *                   column groups over every SM, one grid barrier per pivot,
+ *                   the next pivot's dot products fused into the update
+ *                   (size: R; after the paper's tiled MGS, Introduction).
+ * ph_mgs_variant reports the variant this context uses for an N x n system
+ * of precision prec: the first use of a shape times every variant that
+ * applies (the tiled one for each row-block count worth trying) on a scratch
+ * matrix and keeps the fastest.  ms (optional, 3 doubles) receives the
+ * measured milliseconds of the grid, cluster and best tiled variant, -1 where
+ * a variant does not apply or was not measured (a pinned shape). */
+typedef enum { PH_MGS_GRID = 0, PH_MGS_CLUSTER = 1, PH_MGS_TILED = 2 } ph_mgs_kind;
+ph_status ph_mgs_variant(ph_ctx *ctx, ph_prec prec, int N, int n, int *kind, int *size,
+                         double *ms);
+
+/* Pins the variant this context uses for an N x n system of precision prec,
+ * in place of the timing: kind PH_MGS_GRID (size ignored), PH_MGS_CLUSTER
+ * with the cluster size the shape takes (PH_EINVAL otherwise, or if the shape
+ * does not fit a cluster), PH_MGS_TILED with R row blocks (PH_EINVAL if R
+ * exceeds the SMs or the rows, or its tiles do not fit shared memory); kind
+ * -1 returns the shape to the timed choice.  The variants round differently
+ * (their dot products are summed in different orders), so pinning one makes
+ * a context's results the same from run to run; tests pin each to check it.
+ * A path graph captured with the previous choice is rebuilt on next use. */
+ph_status ph_mgs_set_variant(ph_ctx *ctx, ph_prec prec, int N, int n, int kind, int size);
 
 /* The number of lanes (threads) per output of the summation kernel used for f
  * (with g): *lanes = 1, 2, 4, 8, 16 or 32, chosen by timing each on the
@@ -346,22 +374,28 @@ ph_status ph_profile_newton(ph_ctx *ctx, const ph_system *f, const ph_system *g,
                             int reps, double *ms_out);
 ph_status ph_fp64_peak(ph_ctx *ctx, double ms_target, double *gops);
 
-/* The least-squares solve of ph_mgs_solve for callers that must not allocate
- * device memory: code running while a CUDA graph is being captured, processes
- * whose device memory belongs to another allocator, real-time loops that cannot
- * afford an allocation's implicit synchronisation.  The paper has no
- * counterpart; this is a convenience of this library.
+/* A least-squares solve like ph_mgs_solve for callers that must not allocate
+ * device memory: processes whose device memory belongs to another allocator
+ * (a framework's caching allocator or a fixed arena, where one more
+ * cudaMalloc fails or takes the owner's memory), and real-time loops that
+ * cannot afford an allocation's implicit device synchronisation.  The paper
+ * has no counterpart; this is a convenience of this library.
  *   No context is needed and nothing is allocated: the scratch is one static
  *   4 MiB device array that each GPU loading the library keeps until exit.
  *   Sizes whose scratch (augmented matrix, projections, norms, solution) does
- *   not fit return PH_EINVAL (n = N up to about 250 in DD, 180 in QD).
+ *   not fit return PH_EINVAL (n = N up to 353 in D, 254 in DD, 175 in QD).
  *   device, cuda_stream  the GPU (made current for the call) and the stream
  *                        (a cudaStream_t, may be NULL) the work runs on;
  *   J, rhs, dx, resid_norm  as in ph_mgs_solve (host or device arrays).
+ *   It always runs the grid MGS kernel (one block per column), whereas a
+ *   context may pick the cluster variant by timing (ph_mgs_variant): the
+ *   results agree with ph_mgs_solve to the solver's rounding tolerance, not
+ *   bit for bit.
  *   The first call on a device looks up the array's device address
- *   (cudaGetSymbolAddress) and may load the module: make it before any stream
- *   capture.  Every call shares the array, so calls that overlap on the GPU
- *   race: serialise them.  The call returns after synchronising its stream. */
+ *   (cudaGetSymbolAddress) and may load the module.  Every call shares the
+ *   array, so calls that overlap on the GPU race: serialise them.  The call
+ *   reads its status back and returns after synchronising its stream; a
+ *   stream that is being captured is refused (PH_EINVAL, nothing enqueued). */
 ph_status ph_mgs_solve_static(int device, void *cuda_stream, ph_prec prec, int N, int n,
                               const double *J, const double *rhs, double *dx,
                               double *resid_norm);

@@ -55,7 +55,8 @@ class Params(C.Structure):
     _fields_ = [("max_dt", C.c_double), ("min_dt", C.c_double), ("tol_res", C.c_double),
                 ("tol_dx", C.c_double), ("max_res", C.c_double), ("max_x", C.c_double),
                 ("max_steps", C.c_int32), ("max_newton", C.c_int32), ("pred_order", C.c_int32),
-                ("relax_k", C.c_int32), ("fixed_steps", C.c_int32), ("fixed_rows", C.c_int32)]
+                ("relax_k", C.c_int32), ("fixed_steps", C.c_int32), ("fixed_rows", C.c_int32),
+                ("tol_path", C.c_double)]
 
 
 class Stats(C.Structure):

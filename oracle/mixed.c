@@ -151,7 +151,7 @@ int orc_newton_mixed(const orc_system *f, const orc_system *g, const double *gam
     *res = r;
     if (!fixed) {
       if (!isfinite(r) || r > last) break;
-      if (r < p->tol_res) { success = 1; break; }
+      if (r < orc_tol_res(p, t)) { success = 1; break; }
     }
     /* leading limbs: J is [limb][re|im][NN], h is [limb][re|im][N] */
     memcpy(jl, J, sizeof(double) * 2 * NN);
@@ -177,7 +177,7 @@ int orc_newton_mixed(const orc_system *f, const orc_system *g, const double *gam
     (*updates)++;
     if (!fixed) {
       if (!isfinite(dm)) break;
-      if (dm < p->tol_dx) { success = 1; break; }
+      if (dm < orc_tol_dx(p, t)) { success = 1; break; }
     }
     last = r;
   }
@@ -225,7 +225,7 @@ int orc_corrector_mixed(const orc_system *f, const orc_system *g, const double *
     o->res = r;
     if (!fixed) {
       if (!isfinite(r) || r > last) { success = 0; break; }
-      if (r < p->tol_res) { success = 1; break; }
+      if (r < orc_tol_res(p, t)) { success = 1; break; }
     }
     memcpy(jl, J, sizeof(double) * 2 * NN);
     int e = (r > 0.0 && isfinite(r)) ? ilogb(r) : 0;
@@ -243,7 +243,7 @@ int orc_corrector_mixed(const orc_system *f, const orc_system *g, const double *
     double dm = max_mag_lead(d, n);
     /* the previous update was below sqrt(tol_dx): the working-precision
        corrector would square it below tol_dx by now */
-    int prev_small = o->updates >= 1 && d1 <= sqrt(p->tol_dx);
+    int prev_small = o->updates >= 1 && d1 <= sqrt(orc_tol_dx(p, t));
     if (prev_small) o->onpath = 1;
     if (o->updates >= 2 && contracts_linearly(d2, d1, dm)) o->linear = 1;
     d2 = d1;
@@ -259,7 +259,7 @@ int orc_corrector_mixed(const orc_system *f, const orc_system *g, const double *
     o->updates++;
     if (!fixed) {
       if (!isfinite(dm)) { success = 0; break; }
-      if (dm < p->tol_dx) { success = 1; break; }
+      if (dm < orc_tol_dx(p, t)) { success = 1; break; }
       last = r;
     }
     if (o->iters >= p->max_newton && !(prev_small && o->iters < max_it)) {

@@ -96,7 +96,13 @@ typedef struct {
   double max_dt, min_dt, tol_res, tol_dx, max_res, max_x;
   int32_t max_steps, max_newton, pred_order, relax_k, fixed_steps;
   int32_t fixed_rows;   /* rows where g has no terms are held fixed: h_i = f_i */
+  double tol_path;      /* > 0: the corrector's tolerance (both tests) on steps
+                           to t < 1; the step to t = 1 keeps tol_res, tol_dx */
 } orc_params;
+
+/* The corrector's tolerances for a step to t. */
+double orc_tol_res(const orc_params *p, double t);
+double orc_tol_dx(const orc_params *p, double t);
 
 typedef struct {
   int32_t status, steps, accepted, rejected, newton_iters, updates;

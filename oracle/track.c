@@ -9,7 +9,8 @@
  * Corrector (Fig. 2): at most max_newton
  *   iterations of: evaluate h and J; fail if ||h|| grew past the previous
  *   residual (the first bound is max_res); succeed if ||h|| < tol_res; solve
- *   J dx = -h; x := x + dx; succeed if ||dx|| < tol_dx.  Norms are max norms
+ *   J dx = -h; x := x + dx; succeed if ||dx|| < tol_dx (with tol_path > 0, both
+ *   tests use tol_path on the steps to t < 1).  Norms are max norms
  *   of |z| taken in double from the leading limbs (Section 3.1).
  * Step control (Fig. 3): t := min(1,
  *   t + dt); predict; correct; on success keep the point, count it, and after
@@ -61,6 +62,14 @@ static double max_mag(int L, const double *v, int m) {
   return r;
 }
 
+double orc_tol_res(const orc_params *p, double t) {
+  return (p->tol_path > 0.0 && t < 1.0) ? p->tol_path : p->tol_res;
+}
+
+double orc_tol_dx(const orc_params *p, double t) {
+  return (p->tol_path > 0.0 && t < 1.0) ? p->tol_path : p->tol_dx;
+}
+
 int orc_newton(const orc_system *f, const orc_system *g, const double *gamma, int k,
                double t, double *x, const orc_params *p, int fixed,
                int *iters, int *updates, double *res, double *dxn) {
@@ -82,7 +91,7 @@ int orc_newton(const orc_system *f, const orc_system *g, const double *gamma, in
     *res = r;
     if (!fixed) {
       if (!isfinite(r) || r > last) break;
-      if (r < p->tol_res) { success = 1; break; }
+      if (r < orc_tol_res(p, t)) { success = 1; break; }
     }
     for (int e = 0; e < 2 * L * N; e++) rhs[e] = -h[e];
     int st = orc_mgs_solve(L, N, n, J, rhs, dx, NULL, NULL, NULL);
@@ -99,7 +108,7 @@ int orc_newton(const orc_system *f, const orc_system *g, const double *gamma, in
     (*updates)++;
     if (!fixed) {
       if (!isfinite(d)) break;
-      if (d < p->tol_dx) { success = 1; break; }
+      if (d < orc_tol_dx(p, t)) { success = 1; break; }
     }
     last = r;
   }

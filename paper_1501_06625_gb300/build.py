@@ -14,7 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
-SOURCES = ["api.cu", "system.cu", "eval.cu", "mgs.cu", "mgs_cluster.cu", "track.cu", "noalloc.cu",
+SOURCES = ["api.cu", "system.cu", "eval.cu", "mgs.cu", "mgs_cluster.cu", "mgs_tile.cu", "track.cu",
+           "noalloc.cu",
            "batch.cu", "serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -65,6 +65,15 @@ PH_HD void ctrl_report(ph_ctrl_state *c, const ph_track_params *p, double t_new,
   c->nsteps += 1;
 }
 
+// The corrector's tolerances for a step to t_new: tol_path (when positive) on
+// the way, tol_res / tol_dx for the step that lands on t = 1.
+PH_HD double ctrl_tol_res(const ph_track_params *p, double t_new) {
+  return (p->tol_path > 0.0 && t_new < 1.0) ? p->tol_path : p->tol_res;
+}
+PH_HD double ctrl_tol_dx(const ph_track_params *p, double t_new) {
+  return (p->tol_path > 0.0 && t_new < 1.0) ? p->tol_path : p->tol_dx;
+}
+
 // The precision form (lin_prec != 0): a failed step is corrected again in
 // working precision only if one of its double-precision solves had kappa
 // u_double above this: below it the double corrector contracts like the

@@ -68,6 +68,13 @@ struct PathState {
   double cond;
 };
 
+// Measured times (ms) of the MGS variants of one shape: grid, cluster, tiled
+// (the best row-block count, tile_R); 1e30 where a variant does not apply.
+struct MgsTimes {
+  float ms[3] = {1e30f, 1e30f, 1e30f};
+  int tile_R = 0;
+};
+
 struct ph_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -80,8 +87,10 @@ struct ph_ctx {
   // the MGS variant chosen for each shape (key (L, N, n)): 0 the grid kernel,
   // C > 0 the cluster kernel with C CTAs; scratch buffers of the choice
   std::map<long long, int> mgs_variant;
-  std::map<long long, std::pair<float, float>> mgs_times;   // ms: grid, cluster
-  DevBuf tuneA, tuneW, tuneN, tuneF, tuneX, tuneS;
+  std::map<long long, MgsTimes> mgs_times;
+  DevBuf tuneA, tuneW, tuneN, tuneF, tuneX, tuneS, mgs_part;
+  // limit of every bounded device-side wait (ns)
+  unsigned long long wait_ns = 2000000000ull;
 };
 
 // A loaded polynomial system: the instruction layout of Section 3.2 (terms
@@ -89,6 +98,9 @@ struct ph_ctx {
 // threads read consecutive addresses) plus the summation lists.
 struct ph_system {
   ph_ctx *ctx = nullptr;
+  // unique per load in this process: caches key on it, never on the address,
+  // which a later load may reuse after ph_system_free
+  uint64_t serial = 0;
   int L = 2, N = 0, n = 0, M = 0, Mp = 0, maxv = 0, emax = 1;
   int nout = 0;                 // n*N Jacobian entries + N values
   int max_contrib = 0;          // longest summation list
@@ -179,6 +191,17 @@ int ph_mgs_tune(ph_ctx *ctx, int L, int N, int n);
 // modified).  ph_mgs_cluster_size: 16 or 8 CTAs, or 0 if the matrix does not
 // fit in a cluster's shared memory.
 int ph_mgs_cluster_size(int L, int N, int n);
+
+// mgs_tile.cu: the same solve as a tiled right-looking MGS (R row blocks x
+// column groups, one grid barrier per pivot).  ph_mgs_tile_grid: its blocks
+// for R row blocks, 0 if R does not fit; ph_mgs_tile_part: doubles of its
+// partial-sum buffer.
+int ph_mgs_tile_grid(int sm_count, int L, int N, int n, int R);
+long ph_mgs_tile_part(int L, int n, int R);
+cudaError_t ph_mgs_tile_launch(int sm_count, cudaStream_t stream, int L, int N, int n, int R,
+                               double *A, long ldA, double *W, double *nrm2, double *part,
+                               double *dx, PathState *st, const int *skip, double *resid,
+                               unsigned long long limit_ns);
 cudaError_t ph_mgs_cluster_launch(cudaStream_t stream, int C, int L, int N, int n, const double *A,
                                   long ldA, double *W, double *dx, PathState *st, const int *skip,
                                   double *resid, double *nrm_out);   // nrm_out: r_kk^2 (may be null)

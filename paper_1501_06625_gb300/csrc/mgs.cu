@@ -421,8 +421,57 @@ cudaError_t ph_mgs_launch_buffers(int sm_count, cudaStream_t stream, int L, int 
                                   double *A, long ldA, double *W, double *nrm2, double *dx,
                                   int *ready, PathState *st, double *resid);
 
+// Variant codes (ph_ctx::mgs_variant): the kind times 4096 plus its size.
+static int mgs_code(int kind, int size) { return kind * 4096 + size; }
+static int mgs_kind(int code) { return code / 4096; }
+static int mgs_size(int code) { return code % 4096; }
+static long long mgs_key(int L, int N, int n) {
+  return ((long long)L << 48) | ((long long)N << 24) | (long long)n;
+}
+
+// Row-block counts of the tiled kernel worth timing for a shape: powers of
+// two with at least 8 rows per block that fit (ph_mgs_tile_grid).
+static std::vector<int> tile_candidates(ph_ctx *ctx, int L, int N, int n) {
+  std::vector<int> out;
+  for (int R = 1; R <= 64; R *= 2)
+    if ((R == 1 || N / R >= 8) && ph_mgs_tile_grid(ctx->sm_count, L, N, n, R) > 0) out.push_back(R);
+  return out;
+}
+
+// Buffers a variant needs beyond A and dx (sized before any graph capture).
+static cudaError_t mgs_buffers(ph_ctx *ctx, int L, int n, int code) {
+  const int nc = n + 1;
+  cudaError_t e;
+  if ((e = ctx->R.ensure(sizeof(double) * 2 * L * (size_t)nc * nc)) != cudaSuccess) return e;
+  if ((e = ctx->nrm2.ensure(sizeof(double) * 2 * L * (size_t)nc)) != cudaSuccess) return e;
+  if ((e = ctx->flags.ensure(sizeof(int) * (size_t)nc)) != cudaSuccess) return e;
+  if (mgs_kind(code) == PH_MGS_TILED)
+    e = ctx->mgs_part.ensure(sizeof(double) * (size_t)ph_mgs_tile_part(L, n, mgs_size(code)));
+  return e;
+}
+
+static cudaError_t mgs_launch_code(ph_ctx *ctx, int code, cudaStream_t s, int L, int N, int n,
+                                   double *A, long ldA, double *W, double *nrm2, double *dx,
+                                   int *flags, PathState *st, const int *skip, double *resid) {
+  const int kind = mgs_kind(code), size = mgs_size(code);
+  if (kind == PH_MGS_CLUSTER)
+    return ph_mgs_cluster_launch(s, size, L, N, n, A, ldA, W, dx, st, skip, resid, nrm2);
+  if (kind == PH_MGS_TILED)
+    return ph_mgs_tile_launch(ctx->sm_count, s, L, N, n, size, A, ldA, W, nrm2,
+                              ctx->mgs_part.as<double>(), dx, st, skip, resid, ctx->wait_ns);
+  if (L == 1)
+    return launch_p<F64>(ctx->sm_count, s, N, n, A, ldA, W, nrm2, dx, flags, st, skip, resid);
+  if (L == 2) return launch_p<DD>(ctx->sm_count, s, N, n, A, ldA, W, nrm2, dx, flags, st, skip, resid);
+  return launch_p<QD>(ctx->sm_count, s, N, n, A, ldA, W, nrm2, dx, flags, st, skip, resid);
+}
+
+// Times the variants of a shape once per context on a scratch matrix and
+// keeps the fastest (the grid kernel, the cluster kernel where the matrix
+// fits a cluster, the tiled kernel for each row-block count worth trying).
+// Outside stream capture only; during a capture an unmeasured shape gets the
+// grid kernel.  Returns the variant code.
 int ph_mgs_tune(ph_ctx *ctx, int L, int N, int n) {
-  const long long key = ((long long)L << 48) | ((long long)N << 24) | (long long)n;
+  const long long key = mgs_key(L, N, n);
   auto it = ctx->mgs_variant.find(key);
   if (it != ctx->mgs_variant.end()) return it->second;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -431,51 +480,72 @@ int ph_mgs_tune(ph_ctx *ctx, int L, int N, int n) {
     cudaGetLastError();
     return 0;
   }
+  std::vector<int> codes = {mgs_code(PH_MGS_GRID, 0)};
   const int C = ph_mgs_cluster_size(L, N, n);
   cudaGetLastError();
+  if (C > 0) codes.push_back(mgs_code(PH_MGS_CLUSTER, C));
+  for (int R : tile_candidates(ctx, L, N, n)) codes.push_back(mgs_code(PH_MGS_TILED, R));
+  const int nc = n + 1;
+  const long ldA = ph_lda(N), Ap = (long)nc * ldA, total = 2L * L * Ap;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = ctx->tuneA.ensure(sizeof(double) * total);
+  if (e == cudaSuccess) e = ctx->tuneW.ensure(sizeof(double) * 2 * L * (size_t)nc * nc);
+  if (e == cudaSuccess) e = ctx->tuneN.ensure(sizeof(double) * 2 * L * (size_t)nc);
+  if (e == cudaSuccess) e = ctx->tuneF.ensure(sizeof(int) * (size_t)nc);
+  if (e == cudaSuccess) e = ctx->tuneX.ensure(sizeof(double) * 2 * L * (size_t)n);
+  if (e == cudaSuccess) e = ctx->tuneS.ensure(sizeof(PathState));
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  PathState *st = ctx->tuneS.as<PathState>();
+  double *A = ctx->tuneA.as<double>();
+  float best_all = 1e30f;
   int choice = 0;
-  if (C > 0) {
-    const int nc = n + 1;
-    const long ldA = ph_lda(N), Ap = (long)nc * ldA, total = 2L * L * Ap;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    cudaError_t e = ctx->tuneA.ensure(sizeof(double) * total);
-    if (e == cudaSuccess) e = ctx->tuneW.ensure(sizeof(double) * 2 * L * (size_t)nc * nc);
-    if (e == cudaSuccess) e = ctx->tuneN.ensure(sizeof(double) * 2 * L * (size_t)nc);
-    if (e == cudaSuccess) e = ctx->tuneF.ensure(sizeof(int) * (size_t)nc);
-    if (e == cudaSuccess) e = ctx->tuneX.ensure(sizeof(double) * 2 * L * (size_t)n);
-    if (e == cudaSuccess) e = ctx->tuneS.ensure(sizeof(PathState));
-    if (e == cudaSuccess) e = cudaEventCreate(&e0);
-    if (e == cudaSuccess) e = cudaEventCreate(&e1);
-    float best[2] = {1e30f, 1e30f};
-    PathState *st = ctx->tuneS.as<PathState>();
-    double *A = ctx->tuneA.as<double>();
-    for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
-      for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {   // rep 0 warms up
-        k_tune_fill<<<64, 256, 0, ctx->stream>>>(A, N, ldA, Ap, total);
-        e = cudaGetLastError();
-        if (e == cudaSuccess) e = cudaMemsetAsync(st, 0, sizeof(PathState), ctx->stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(ctx->tuneF.p, 0, sizeof(int) * nc, ctx->stream);
-        if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
-        if (e == cudaSuccess)
-          e = v == 0 ? ph_mgs_launch_buffers(ctx->sm_count, ctx->stream, L, N, n, A, ldA,
-                                             ctx->tuneW.as<double>(), ctx->tuneN.as<double>(),
-                                             ctx->tuneX.as<double>(), ctx->tuneF.as<int>(), st,
-                                             nullptr)
-                     : ph_mgs_cluster_launch(ctx->stream, C, L, N, n, A, ldA,
-                                             ctx->tuneW.as<double>(), ctx->tuneX.as<double>(), st,
-                                             nullptr, nullptr, nullptr);
-        if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
-        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-        float ms = 0.0f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-        if (e == cudaSuccess && rep > 0 && ms < best[v]) best[v] = ms;
-      }
+  MgsTimes times;
+  for (int code : codes) {
+    if (e != cudaSuccess) break;
+    if (mgs_kind(code) == PH_MGS_TILED &&
+        (e = mgs_buffers(ctx, L, n, code)) != cudaSuccess)
+      break;
+    float best = 1e30f;
+    for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {     // rep 0 warms up
+      k_tune_fill<<<64, 256, 0, ctx->stream>>>(A, N, ldA, Ap, total);
+      e = cudaGetLastError();
+      if (e == cudaSuccess) e = cudaMemsetAsync(st, 0, sizeof(PathState), ctx->stream);
+      if (e == cudaSuccess) e = cudaMemsetAsync(ctx->tuneF.p, 0, sizeof(int) * nc, ctx->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
+      if (e == cudaSuccess)
+        e = mgs_launch_code(ctx, code, ctx->stream, L, N, n, A, ldA, ctx->tuneW.as<double>(),
+                            ctx->tuneN.as<double>(), ctx->tuneX.as<double>(),
+                            ctx->tuneF.as<int>(), st, nullptr, nullptr);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.0f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e == cudaSuccess && rep > 0 && ms < best) best = ms;
+      if (e == cudaSuccess && rep == 1 && ms > 50.0f) break;    // long solves: one timed run
     }
-    if (e0) cudaEventDestroy(e0);
-    if (e1) cudaEventDestroy(e1);
-    if (e == cudaSuccess && best[1] < best[0]) choice = C;
-    if (e == cudaSuccess) ctx->mgs_times[key] = std::make_pair(best[0], best[1]);
+    if (e != cudaSuccess) break;
+    const int kind = mgs_kind(code);
+    if (best < times.ms[kind]) {
+      times.ms[kind] = best;
+      if (kind == PH_MGS_TILED) times.tile_R = mgs_size(code);
+    }
+    if (best < best_all) {
+      best_all = best;
+      choice = code;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e != cudaSuccess) {
     cudaGetLastError();
+    choice = 0;
+  } else {
+    ctx->mgs_times[key] = times;
+  }
+  if (mgs_buffers(ctx, L, n, choice) != cudaSuccess) {
+    cudaGetLastError();
+    choice = 0;
   }
   ctx->mgs_variant[key] = choice;
   return choice;
@@ -483,23 +553,11 @@ int ph_mgs_tune(ph_ctx *ctx, int L, int N, int n) {
 
 cudaError_t ph_mgs_launch(ph_ctx *ctx, int L, int N, int n, double *A, long ldA, double *dx,
                           PathState *st, const int *skip, double *resid) {
-  const int nc = n + 1;
-  cudaError_t e;
-  if ((e = ctx->R.ensure(sizeof(double) * 2 * L * (size_t)nc * nc)) != cudaSuccess) return e;
-  if ((e = ctx->nrm2.ensure(sizeof(double) * 2 * L * (size_t)nc)) != cudaSuccess) return e;
-  if ((e = ctx->flags.ensure(sizeof(int) * (size_t)nc)) != cudaSuccess) return e;
-  double *W = ctx->R.as<double>(), *nrm2 = ctx->nrm2.as<double>();
-  const int C = ph_mgs_tune(ctx, L, N, n);
-  if (C > 0)
-    return ph_mgs_cluster_launch(ctx->stream, C, L, N, n, A, ldA, W, dx, st, skip, resid, nrm2);
-  if (L == 1)
-    return launch_p<F64>(ctx->sm_count, ctx->stream, N, n, A, ldA, W, nrm2, dx,
-                         ctx->flags.as<int>(), st, skip, resid);
-  if (L == 2)
-    return launch_p<DD>(ctx->sm_count, ctx->stream, N, n, A, ldA, W, nrm2, dx,
-                        ctx->flags.as<int>(), st, skip, resid);
-  return launch_p<QD>(ctx->sm_count, ctx->stream, N, n, A, ldA, W, nrm2, dx, ctx->flags.as<int>(),
-                      st, skip, resid);
+  const int code = ph_mgs_tune(ctx, L, N, n);
+  cudaError_t e = mgs_buffers(ctx, L, n, code);
+  if (e != cudaSuccess) return e;
+  return mgs_launch_code(ctx, code, ctx->stream, L, N, n, A, ldA, ctx->R.as<double>(),
+                         ctx->nrm2.as<double>(), dx, ctx->flags.as<int>(), st, skip, resid);
 }
 
 // The same solve with every buffer supplied by the caller and the launch
@@ -517,17 +575,47 @@ cudaError_t ph_mgs_launch_buffers(int sm_count, cudaStream_t stream, int L, int 
   return launch_p<QD>(sm_count, stream, N, n, A, ldA, W, nrm2, dx, ready, st, nullptr, resid);
 }
 
-extern "C" ph_status ph_mgs_variant(ph_ctx *ctx, ph_prec prec, int N, int n, int *cluster,
-                                    double *ms_grid, double *ms_cluster) {
+extern "C" ph_status ph_mgs_variant(ph_ctx *ctx, ph_prec prec, int N, int n, int *kind, int *size,
+                                    double *ms) {
   if (!ctx) return PH_EINVAL;
   const int L = (int)prec;
-  if ((L != 1 && L != 2 && L != 4) || n < 1 || N < n || !cluster)
+  if ((L != 1 && L != 2 && L != 4) || n < 1 || N < n || !kind || !size)
     return ph_fail(ctx, PH_EINVAL, "ph_mgs_variant: invalid argument");
   cudaSetDevice(ctx->device);
-  *cluster = ph_mgs_tune(ctx, L, N, n);
-  const long long key = ((long long)L << 48) | ((long long)N << 24) | (long long)n;
-  auto it = ctx->mgs_times.find(key);
-  if (ms_grid) *ms_grid = it != ctx->mgs_times.end() ? it->second.first : -1.0;
-  if (ms_cluster) *ms_cluster = it != ctx->mgs_times.end() ? it->second.second : -1.0;
+  const int code = ph_mgs_tune(ctx, L, N, n);
+  *kind = mgs_kind(code);
+  *size = mgs_size(code);
+  if (ms) {
+    auto it = ctx->mgs_times.find(mgs_key(L, N, n));
+    for (int q = 0; q < 3; ++q)
+      ms[q] = it != ctx->mgs_times.end() && it->second.ms[q] < 1e29f ? it->second.ms[q] : -1.0;
+  }
+  return PH_OK;
+}
+
+void ph_track_release(ph_ctx *ctx);
+
+extern "C" ph_status ph_mgs_set_variant(ph_ctx *ctx, ph_prec prec, int N, int n, int kind,
+                                        int size) {
+  if (!ctx) return PH_EINVAL;
+  const int L = (int)prec;
+  if ((L != 1 && L != 2 && L != 4) || n < 1 || N < n || kind < -1 || kind > PH_MGS_TILED)
+    return ph_fail(ctx, PH_EINVAL, "ph_mgs_set_variant: invalid argument");
+  cudaSetDevice(ctx->device);
+  const long long key = mgs_key(L, N, n);
+  if (kind == PH_MGS_CLUSTER && (size < 1 || size != ph_mgs_cluster_size(L, N, n)))
+    return ph_fail(ctx, PH_EINVAL, "ph_mgs_set_variant: the shape does not take that cluster size");
+  if (kind == PH_MGS_TILED && ph_mgs_tile_grid(ctx->sm_count, L, N, n, size) < 1)
+    return ph_fail(ctx, PH_EINVAL, "ph_mgs_set_variant: no tiled solve with that many row blocks");
+  if (kind < 0) {
+    ctx->mgs_variant.erase(key);
+    ctx->mgs_times.erase(key);
+  } else {
+    const int code = mgs_code(kind, kind == PH_MGS_GRID ? 0 : size);
+    PH_CUDA(ctx, mgs_buffers(ctx, L, n, code));
+    ctx->mgs_variant[key] = code;
+  }
+  // a captured path graph holds the previous choice: rebuild it on next use
+  ph_track_release(ctx);
   return PH_OK;
 }

@@ -1,24 +1,30 @@
-// noalloc.cu -- ph_mgs_solve_static: the least-squares solve of ph_mgs_solve
-// for callers that must not allocate device memory.
+// noalloc.cu -- ph_mgs_solve_static: a least-squares solve like
+// ph_mgs_solve for callers that must not allocate device memory.
 //
-// Some callers cannot call cudaMalloc: code running while a CUDA graph is
-// being captured (an allocation would break the capture), processes whose
-// device memory is fully reserved by another allocator (a framework's caching
-// allocator, a fixed arena), and real-time loops where an allocation's
-// implicit synchronisation is not acceptable.  This entry point allocates
-// nothing.  Its scratch memory (the augmented matrix, the projections, the
-// pivot norms and flags, the solution, the status words) is one file-scope
-// device array of kScratchBytes, which every GPU that loads the library holds
-// until the process exits.
+// Some callers cannot call cudaMalloc: processes whose device memory is fully
+// reserved by another allocator (a framework's caching allocator, a fixed
+// arena), so that a further allocation would fail or evict the owner's
+// buffers, and real-time loops where an allocation's implicit device
+// synchronisation is not acceptable.  This entry point allocates nothing.
+// Its scratch memory (the augmented matrix, the projections, the pivot norms
+// and flags, the solution, the status words) is one file-scope device array
+// of kScratchBytes, which every GPU that loads the library holds until the
+// process exits.
 //
 // The host cannot use the array's name as a device address (in host code it
 // names a host-side stand-in), so the first call on each device looks the
 // address up with cudaGetSymbolAddress, with that device current, and keeps
-// it.  That first call may load the module; make it before any stream
-// capture.  All calls share the one array: calls that overlap on the GPU
-// (other streams, other host threads) race and must be serialised by the
-// caller.  What must start at zero (the status words and the pivot flags) is
-// cleared on the caller's stream at the start of every call.
+// it.  All calls share the one array: calls that overlap on the GPU (other
+// streams, other host threads) race and must be serialised by the caller.
+// What must start at zero (the status words and the pivot flags) is cleared
+// on the caller's stream at the start of every call.
+//
+// The solve always runs the grid MGS kernel (one block per column); it does
+// not time the cluster variant the way a context does.  Its results agree
+// with ph_mgs_solve to the solver's rounding tolerance, not bit for bit.
+// The call ends by reading the status and residual back to the host and
+// synchronising its stream, so a stream that is being captured into a graph
+// is refused with PH_EINVAL before anything is enqueued on it.
 #include <mutex>
 
 #include "internal.h"
@@ -86,6 +92,15 @@ extern "C" ph_status ph_mgs_solve_static(int device, void *cuda_stream, ph_prec 
     sms = g_sms[device];
   }
   cudaStream_t s = (cudaStream_t)cuda_stream;
+  if (status == PH_OK) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+      cudaGetLastError();
+      status = PH_ECUDA;
+    } else if (cs != cudaStreamCaptureStatusNone) {
+      status = PH_EINVAL;                        // nothing was enqueued on the stream
+    }
+  }
   PathState *st = (PathState *)(base + o_st);
   double *A = (double *)(base + o_A), *W = (double *)(base + o_W), *nrm2 = (double *)(base + o_n);
   int *ready = (int *)(base + o_i);

@@ -450,7 +450,7 @@ __device__ void track_job(const Job &a, double *smem) {
           s_st.res = r;
           if (!fixed) {
             if (!(r <= s_last) || !isfinite(r)) { s_dec = 1; s_ok = 0; }
-            else if (r < a.p.tol_res) { s_dec = 1; s_ok = 1; }
+            else if (r < ctrl_tol_res(&a.p, s_tn)) { s_dec = 1; s_ok = 1; }
           }
           s_scale_e = (r > 0.0 && isfinite(r)) ? ilogb(r) : 0;
         }
@@ -505,7 +505,8 @@ __device__ void track_job(const Job &a, double *smem) {
         }
         if (tid == 0) {                              // update test
           const double d = ms != PH_OK ? NAN : (lin == 0 ? s_dxmax : ldexp(s_dxmax, e));
-          const bool prev_on_path = lin != 0 && s_upd >= 1 && s_dxn <= sqrt(a.p.tol_dx);
+          const double tol_dx = ctrl_tol_dx(&a.p, s_tn);
+          const bool prev_on_path = lin != 0 && s_upd >= 1 && s_dxn <= sqrt(tol_dx);
           if (prev_on_path) s_onpath = 1;
           if (lin != 0 && s_upd >= 2 && linear_contraction(s_dxn2, s_dxn, d)) s_linear = 1;
           s_dxn2 = s_dxn;
@@ -515,7 +516,7 @@ __device__ void track_job(const Job &a, double *smem) {
           s_st.updates += 1;
           if (!fixed) {
             if (!isfinite(d)) { s_dec = 1; s_ok = 0; }
-            else if (d < a.p.tol_dx) { s_dec = 1; s_ok = 1; }
+            else if (d < tol_dx) { s_dec = 1; s_ok = 1; }
             else s_last = s_res;
           }
           if (!s_dec && s_iters >= a.p.max_newton && !(prev_on_path && s_iters < max_it)) {

@@ -12,6 +12,7 @@
 //    the list of slots to add, in the order of the terms of polynomial i.
 // Everything crosses to the device once, at load time (Section 3.1).
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <numeric>
 
@@ -77,9 +78,11 @@ extern "C" ph_status ph_system_load(ph_ctx *ctx, ph_prec prec, int N, int n,
   }
   if (emax > 64) return ph_fail(ctx, PH_EINVAL, "ph_system_load: exponents above 64 are not supported");
 
+  static std::atomic<uint64_t> next_serial{1};
   ph_system *s = new (std::nothrow) ph_system();
   if (!s) return ph_fail(ctx, PH_ENOMEM, "ph_system_load: out of host memory");
   s->ctx = ctx;
+  s->serial = next_serial.fetch_add(1);
   s->L = L; s->N = N; s->n = n; s->M = M; s->maxv = maxv; s->emax = emax;
   s->Mp = std::max(32, (M + 31) / 32 * 32);
   const int Mp = s->Mp;

@@ -161,7 +161,7 @@ __global__ void k_check_res(PathState *st, ph_track_params p) {
       st->nt_done = 1;
       st->nt_success = 0;
       st->skip_nt = 1;
-    } else if (r < p.tol_res) {
+    } else if (r < ctrl_tol_res(&p, st->t_new)) {
       st->nt_done = 1;
       st->nt_success = 1;
       st->skip_nt = 1;
@@ -254,7 +254,8 @@ __global__ void k_check_dx(PathState *st, ph_track_params p, const double *__res
   }
   double d = st->mgs_status != 0 ? NAN : __longlong_as_double((long long)st->dx_bits);
   if (lin) d = ldexp(d, st->scale_e);
-  const bool prev_on_path = lin && st->nt_updates >= 1 && st->dxn <= sqrt(p.tol_dx);
+  const double tol_dx = ctrl_tol_dx(&p, st->t_new);
+  const bool prev_on_path = lin && st->nt_updates >= 1 && st->dxn <= sqrt(tol_dx);
   if (prev_on_path) st->onpath = 1;
   if (lin && st->nt_updates >= 2 && linear_contraction(st->dxn2, st->dxn, d)) st->linear = 1;
   st->dxn2 = st->dxn;
@@ -271,7 +272,7 @@ __global__ void k_check_dx(PathState *st, ph_track_params p, const double *__res
       set_gates(st);
       return;
     }
-    if (d < p.tol_dx) {
+    if (d < tol_dx) {
       st->nt_done = 1;
       st->nt_success = 1;
       st->skip_nt = 1;
@@ -376,7 +377,7 @@ struct TrackGraph {
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
   // what the graph was built for
-  const ph_system *f = nullptr, *g = nullptr;
+  uint64_t f_serial = 0, g_serial = 0;    // the systems (0: none)
   ph_track_params p;
   void *bufs[16] = {};
   int log_cap = -1;
@@ -527,8 +528,8 @@ static ph_status build_graph(ph_ctx *ctx, TrackCache *c, const ph_system *f, con
   tg.kernels_per_step = (long)nodes;
   e = cudaGraphInstantiate(&tg.exec, tg.graph, 0);
   if (e != cudaSuccess) { drop_graph(tg); return ph_cuda_fail(ctx, e, "cudaGraphInstantiate"); }
-  tg.f = f;
-  tg.g = g;
+  tg.f_serial = f->serial;
+  tg.g_serial = g ? g->serial : 0;
   tg.p = p;
   tg.log_cap = log_cap;
   tg.valid = true;
@@ -621,7 +622,8 @@ extern "C" ph_status ph_track_path(ph_ctx *ctx, const ph_system *f, const ph_sys
   TrackCache *c = get_cache(ctx);
   void *bufs[16] = {st, hist, xw, dx, A, dgam, dlog, ctx->slots.p, ctx->ptab.p, ctx->scal.p,
                     ctx->R.p, ctx->nrm2.p, ctx->irkk.p, ctx->flags.p, ctx->spow.p, nullptr};
-  bool same = c->tg.valid && c->tg.f == f && c->tg.g == g && c->tg.log_cap == log_cap &&
+  bool same = c->tg.valid && c->tg.f_serial == f->serial &&
+              c->tg.g_serial == (g ? g->serial : 0) && c->tg.log_cap == log_cap &&
               memcmp(&c->tg.p, &p, sizeof p) == 0 && memcmp(c->tg.bufs, bufs, sizeof bufs) == 0 &&
               c->tg.stream == ctx->stream;
   if (!same) {

@@ -32,7 +32,7 @@ class TrackParams(C.Structure):
                 ("max_steps", C.c_int32), ("max_newton", C.c_int32), ("pred_order", C.c_int32),
                 ("relax_k", C.c_int32), ("fixed_steps", C.c_int32), ("control", C.c_int32),
                 ("lin_prec", C.c_int32), ("fixed_rows", C.c_int32), ("endgame_t", C.c_double),
-                ("cond_f32", C.c_double)]
+                ("cond_f32", C.c_double), ("tol_path", C.c_double)]
 
 
 class PathStats(C.Structure):
@@ -63,7 +63,8 @@ EXPORTS = ["ph_init", "ph_destroy", "ph_last_error", "ph_system_load", "ph_syste
            "ph_ctrl_report", "ph_version", "ph_profile_newton", "ph_fp64_peak",
            "ph_mgs_solve_static", "ph_track_paths", "ph_server_create", "ph_server_submit",
            "ph_server_poll", "ph_server_wait", "ph_server_info", "ph_server_destroy",
-           "ph_server_job_bytes", "ph_mgs_variant", "ph_sum_lanes", "ph_ctrl_linear_contraction"]
+           "ph_server_job_bytes", "ph_mgs_variant", "ph_sum_lanes", "ph_ctrl_linear_contraction",
+           "ph_mgs_set_variant"]
 
 
 class PhError(RuntimeError):
@@ -105,8 +106,9 @@ def lib():
             L.ph_ctrl_linear_contraction.restype = C.c_int
             L.ph_version.restype = C.c_char_p
             L.ph_profile_newton.argtypes = [vp, vp, vp, vp, C.c_int, vp, vp, C.c_int, dp]
+            L.ph_mgs_set_variant.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]
             L.ph_mgs_variant.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int),
-                                         C.POINTER(C.c_double), C.POINTER(C.c_double)]
+                                         C.POINTER(C.c_int), dp]
             L.ph_sum_lanes.argtypes = [vp, vp, vp, C.POINTER(C.c_int), dp]
             L.ph_fp64_peak.argtypes = [vp, C.c_double, dp]
             L.ph_server_create.argtypes = [vp, C.POINTER(ServerConfig), C.POINTER(vp)]
@@ -331,12 +333,22 @@ def ph_profile_newton(ctx, f, g, gamma, k, t, x, reps: int = 10):
     return list(out)
 
 
+MGS_GRID, MGS_CLUSTER, MGS_TILED = 0, 1, 2
+MGS_KINDS = ["grid", "cluster", "tiled"]
+
+
 def ph_mgs_variant(ctx, prec: int, N: int, n: int):
-    """(cluster size or 0 for the grid kernel, ms grid, ms cluster) of the MGS solve."""
-    c = C.c_int(0)
-    g, k = C.c_double(0.0), C.c_double(0.0)
-    _check(ctx, lib().ph_mgs_variant(ctx, prec, N, n, C.byref(c), C.byref(g), C.byref(k)))
-    return c.value, g.value, k.value
+    """(kind, size, [ms grid, ms cluster, ms tiled]) of the MGS solve of a shape
+    (-1 where a variant was not measured)."""
+    kind, size = C.c_int(0), C.c_int(0)
+    ms = (C.c_double * 3)()
+    _check(ctx, lib().ph_mgs_variant(ctx, prec, N, n, C.byref(kind), C.byref(size), ms))
+    return kind.value, size.value, list(ms)
+
+
+def ph_mgs_set_variant(ctx, prec: int, N: int, n: int, kind: int, size: int = 0):
+    """Pins the solve variant of a shape (kind -1: back to the timed choice)."""
+    return _check(ctx, lib().ph_mgs_set_variant(ctx, prec, N, n, kind, size))
 
 
 def ph_sum_lanes(ctx, f, g=None):

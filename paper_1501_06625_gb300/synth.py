@@ -184,7 +184,8 @@ def sparse_system(rng: Rng, n: int, extra_terms: int = 3, vars_per_term: int = 2
 
 
 def planted_system(rng: Rng, n: int, terms_per_poly: int, vars_per_term: int,
-                   exps: tuple[int, ...], log10_mag: float) -> tuple[SystemSpec, np.ndarray]:
+                   exps: tuple[int, ...], log10_mag: float,
+                   per_equation: bool = False) -> tuple[SystemSpec, np.ndarray]:
     """A dense system (the recipe of dense_system) whose coefficient moduli
     spread log-uniformly over log10_mag decades within each polynomial, with a
     planted root x*.  Each polynomial is scaled so that its largest modulus is
@@ -196,6 +197,10 @@ def planted_system(rng: Rng, n: int, terms_per_poly: int, vars_per_term: int,
     c (x*)^a is c with its parts swapped or negated, exactly; each polynomial
     gets the constant term b_i = -sum_k c_ik (x*)^{a_ik}, summed exactly in
     rationals and stored as two limbs, so f(x*) = 0 holds exactly.
+    With per_equation, the spread is between the equations instead: every
+    term of polynomial i has modulus 10^{log10_mag u_i} (one draw u_i per
+    polynomial, no rescaling), so the rows of the Jacobian differ in scale by
+    up to 10^log10_mag and its condition number grows with them.
     Returns (system, x*)."""
     from fractions import Fraction
     units = (1 + 0j, 1j, -1 + 0j, -1j)
@@ -208,6 +213,10 @@ def planted_system(rng: Rng, n: int, terms_per_poly: int, vars_per_term: int,
             mono = [(v, rng.choice(exps)) for v in vs]
             drawn.append((mono, rng.unit_complex(), rng.uniform()))
         umax = max(u for _, _, u in drawn)
+        if per_equation:
+            ue = rng.uniform()
+            drawn = [(mono, e, ue) for mono, e, _ in drawn]
+            umax = 0.0
         terms = []
         bre, bim = Fraction(0), Fraction(0)
         for mono, e, u in drawn:
@@ -382,7 +391,7 @@ def default_params(L: int, **over) -> dict:
     p = dict(max_dt=0.1, min_dt={1: 1e-8, 2: 1e-12, 4: 1e-20}[L], tol_res=tol, tol_dx=tol,
              max_res=1e8, max_x=1e8, max_steps=10000, max_newton=4 if L == 4 else 3,
              pred_order=4, relax_k=1, fixed_steps=0, control=0, lin_prec=0, fixed_rows=0,
-             endgame_t=0.0, cond_f32=0.0)
+             endgame_t=0.0, cond_f32=0.0, tol_path=0.0)
     p.update(over)
     return p
 
@@ -475,6 +484,73 @@ def precision128(seed: int = 1, prec="qd") -> tuple[Workload, np.ndarray]:
     return wl, xs
 
 
+def total_degree_start(f: SystemSpec) -> SystemSpec:
+    """The total-degree start system g_i = x_i^{d_i} - 1 of f as an explicit
+    system (d_i the degree of f_i), for homotopies that need it as a system
+    of their own, such as tracking backwards from a root of f."""
+    d = f.degrees()
+    return build_system(f.N, f.n, [[(1.0, [(i, int(d[i]))]), (-1.0, [])] for i in range(f.n)])
+
+
+def nearest_start_root(f: SystemSpec, x: np.ndarray) -> np.ndarray:
+    """The root of x_i^{d_i} = 1 nearest to x coordinate by coordinate:
+    exp(2 pi i m_i / d_i) with m_i the rounded angle, rounded to double."""
+    d = f.degrees()
+    m = np.round(np.angle(x) * d / (2 * np.pi)) % d
+    return np.exp(2j * np.pi * m / d)
+
+
+def dense64_planted(seed: int = 1, prec="dd") -> tuple[Workload, np.ndarray]:
+    """The dense n = 64 recipe (64 unit-modulus terms per polynomial over 16
+    distinct variables, exponents in {1, 2, 3}) with a planted root x*: each
+    polynomial also gets the constant term that makes f(x*) = 0 exactly
+    (planted_system with one decade of spread switched off), so the
+    total-degree path that ends at x* converges.  The workload's start point is
+    the all-ones root; the start root of x*'s path comes from tracking x*
+    backwards.  Returns (workload, x*)."""
+    L = _limbs(prec)
+    rng = Rng(seed)
+    f, xs = planted_system(rng, 64, 64, 16, (1, 2, 3), 0.0)
+    gamma = rng.unit_complex()
+    wl = Workload(f"dense64_planted_{'dd' if L == 2 else 'qd'}", seed, L, f, gamma,
+                  np.ones(64, dtype=np.complex128), default_params(L))
+    return wl, xs
+
+
+def precision128_equations(seed: int = 1, prec="qd", decades: float = 12.0):
+    """precision128's shape (n = 128, 128 terms per polynomial over 16
+    variables, exponents {1, 2, 3}, planted root x*) with the coefficient
+    moduli spread over `decades` decades between the equations
+    (planted_system with per_equation): the Jacobian's rows differ in scale
+    by up to 10^decades, which pushes its condition number up by as much.
+    Returns (workload, x*)."""
+    L = _limbs(prec)
+    rng = Rng(seed)
+    f, xs = planted_system(rng, 128, 128, 16, (1, 2, 3), decades, per_equation=True)
+    gamma = rng.unit_complex()
+    wl = Workload(f"precision128eq_{'dd' if L == 2 else 'qd'}", seed, L, f, gamma,
+                  np.ones(128, dtype=np.complex128), default_params(L))
+    return wl, xs
+
+
 def random_x(rng: Rng, n: int, radius: float = 1.0) -> np.ndarray:
     """Points with coordinates of modulus radius*U[0.5, 1.5] and uniform angle."""
     return np.array([rng.unit_complex() * radius * (0.5 + rng.uniform()) for _ in range(n)])
+
+
+def random_lsq(seed: int, L: int, N: int, n: int) -> tuple[np.ndarray, np.ndarray]:
+    """A seeded least-squares problem in the library's layout: J [L][2][n][N]
+    (column-major) and rhs [L][2][N].  Leading limbs: real and imaginary parts
+    uniform in [-1, 1) (53-bit draws, so the same on every machine); limb l > 0
+    is the leading limb times 2^(-60 l), an exact scaling that keeps the limbs
+    non-overlapping and makes every limb of the solver's input matter."""
+    rng = Rng(seed)
+    lead = np.array([2.0 * rng.uniform() - 1.0 for _ in range(2 * (n + 1) * N)])
+    lead = lead.reshape(n + 1, 2, N)                  # column, part, row
+    J = np.zeros((L, 2, n, N))
+    rhs = np.zeros((L, 2, N))
+    for l in range(L):
+        s = 2.0 ** (-60 * l)
+        J[l] = np.transpose(lead[:n], (1, 0, 2)) * s
+        rhs[l] = lead[n] * s
+    return J, rhs

@@ -93,3 +93,22 @@ def soa_matrix(A, L: int) -> np.ndarray:
     out[0, 0] = A.T.real
     out[0, 1] = A.T.imag
     return out
+
+
+def mgs_tol(A: np.ndarray, b: np.ndarray, L: int, c: float = 2.0) -> float:
+    """Normwise bound on the difference of two backward-stable least-squares
+    solutions of A x = b (A complex N x n, leading limbs) in L limbs:
+    c n u (kappa + kappa^2 rho), rho = ||b - A x|| / (||A|| ||x||), the
+    first-order forward error of least squares (the kappa^2 term vanishes
+    for consistent systems), relative to ||x||_inf."""
+    n = A.shape[1]
+    s = np.linalg.svd(A, compute_uv=False)
+    kappa = s[0] / s[-1]
+    x = np.linalg.lstsq(A, b, rcond=None)[0]
+    rho = np.linalg.norm(b - A @ x) / (s[0] * np.linalg.norm(x))
+    return c * n * U[L] * (kappa + kappa * kappa * rho)
+
+
+def complex_matrix(J: np.ndarray) -> np.ndarray:
+    """[L][2][n][N] -> complex N x n of the leading limbs."""
+    return (J[0, 0] + 1j * J[0, 1]).T

@@ -7,7 +7,8 @@ the same seeded inputs.
   exponents, k = 2, a general start system, f alone, and the full-size dense
   n = 64 (4096 monomials over 16 variables) and sparse n = 512 systems.
 * ph_mgs_solve: solutions of square and tall systems against the oracle's
-  textbook MGS within 1e3 * kappa * n * u; rank deficiency is reported.
+  textbook MGS within the first-order least-squares forward error bound
+  2 n u (kappa + kappa^2 rho); rank deficiency is reported.
 * ph_track_path: the fixed schedule of the 8-variable dense system (100 steps,
   3 updates each) ends within 1e-24 (DD) / 1e-52 (QD) of the oracle; adaptive
   runs are replayed by the oracle from the GPU's own step log and must end at
@@ -17,8 +18,8 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_common import (TOL_END, U, assert_eval_close, cabs_diff, lead_complex, soa_from_complex,
-                        soa_matrix)
+from gpu_common import (TOL_END, assert_eval_close, cabs_diff, complex_matrix, lead_complex,
+                        mgs_tol, soa_from_complex, soa_matrix)
 from paper_1501_06625_gb300 import libph, synth
 
 pytestmark = pytest.mark.gpu
@@ -126,8 +127,10 @@ def test_eval_full_size_sparse512(ctx):
 
 
 @pytest.mark.parametrize("L", [2, 4])
-@pytest.mark.parametrize("N,n", [(1, 1), (8, 8), (37, 37), (50, 33), (64, 64), (200, 200)])
+@pytest.mark.parametrize("N,n", [(1, 1), (8, 8), (37, 37), (50, 33), (64, 64)])
 def test_mgs_parity(ctx, L, N, n):
+    """The solve of whichever variant the context picks by timing (each variant
+    pinned, and the sizes beyond 256 rows: test_gpu_mgs_parity.py)."""
     rng = np.random.default_rng(N * 1000 + n + L)
     A = rng.standard_normal((N, n)) + 1j * rng.standard_normal((N, n))
     b = rng.standard_normal(N) + 1j * rng.standard_normal(N)
@@ -136,17 +139,11 @@ def test_mgs_parity(ctx, L, N, n):
     rhs = soa_from_complex(b, L)
     dx = np.zeros((L, 2, n))
     rn = libph.ph_mgs_solve(ctx.h, L, N, n, J, rhs, dx)
-    if n > 64:
-        # the oracle's MGS at n = 200 takes too long: check the normal equations
-        r = A @ lead_complex(dx) - b
-        assert np.linalg.norm(A.conj().T @ r) < 1e-10 * np.linalg.norm(b)
-        return
     st, dxo, rno = oracle.mgs_solve(J, rhs)
     assert st == oracle.OK
-    kappa = np.linalg.cond(A)
     err = cabs_diff(dx, dxo).max() / np.abs(lead_complex(dxo)).max()
-    assert err < 1e3 * kappa * n * U[L], err
-    assert abs(rn - rno) <= 1e-12 * (1 + rno) + 1e3 * kappa * U[L] * np.linalg.norm(b)
+    assert err <= mgs_tol(complex_matrix(J), lead_complex(rhs), L), err
+    assert abs(rn - rno) <= 1e-12 * (1 + rno)
 
 
 def test_mgs_rank_deficient(ctx):
@@ -278,3 +275,93 @@ def test_invalid_arguments(ctx):
     with pytest.raises(libph.PhError):
         libph.ph_mgs_solve(ctx.h, 2, 3, 5, np.zeros((2, 2, 5, 3)), np.zeros((2, 2, 3)),
                            np.zeros((2, 2, 5)))
+
+
+def _first_decision_difference(glog, olog):
+    """Index of the first step whose (t, accepted, updates) differ, or None."""
+    for i, (a, b) in enumerate(zip(glog, olog)):
+        if a["t"] != b["t"] or a["accepted"] != b["accepted"] or a["updates"] != b["updates"]:
+            return i
+    return None if len(glog) == len(olog) else min(len(glog), len(olog))
+
+
+def _near_threshold(rec, params, rel=1e-6):
+    """A corrector outcome decided by a norm within rounding of its tolerance."""
+    return any(abs(rec[k] / params[tk] - 1.0) < rel
+               for k, tk in (("res", "tol_res"), ("dx", "tol_dx")) if rec[k] > 0)
+
+
+@pytest.mark.parametrize("L", [2, 4])
+@pytest.mark.parametrize("case", ["linear6", "dense5_first300", "dense64_first10"])
+def test_step_decisions_against_the_oracle(ctx, L, case):
+    """The library and the oracle each track the path and take their own
+    decisions (Fig. 3 step control, Fig. 2 corrector tests); their schedules
+    (every t tried, accepted or not, updates applied) must be identical until a
+    decision that rests on a norm within rounding of its tolerance, and the
+    end points must then agree to the end-point tolerance."""
+    if case == "linear6":
+        rng = np.random.default_rng(17)
+        n = 6
+        A = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)) + 3 * np.eye(n)
+        b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+        spec = synth.build_system(n, n, [[(A[i, j], [(j, 1)]) for j in range(n)] + [(-b[i], [])]
+                                         for i in range(n)])
+        gam = soa_from_complex([0.6 + 0.8j], L).reshape(L, 2)
+        x0 = soa_from_complex(np.ones(n), L)
+        params = synth.default_params(L)
+    elif case == "dense5_first300":
+        rng = synth.Rng(31)
+        spec = synth.dense_system(rng, 5, 5, 3, (1, 2))
+        gam = _gamma(rng, L)
+        x0 = soa_from_complex(np.ones(5), L)
+        params = synth.default_params(L, max_dt=0.2, max_steps=299)
+    else:
+        if L == 4:
+            pytest.skip("the QD dense64 oracle steps take minutes; DD covers the full size")
+        wl = synth.dense64(1, "dd")
+        spec, gam, x0 = wl.f, wl.gamma_soa(), wl.x0_soa()
+        params = dict(wl.params, max_steps=9)
+    f = ctx.load(spec, L)
+    xg = np.zeros_like(x0)
+    st, stats, glog = libph.ph_track_path(ctx.h, f, None, gam, x0, params, xg, log_cap=20000)
+    so, xo, ostats, olog = oracle.track(oracle.System(spec, L), x0, gam, params)
+    i = _first_decision_difference(glog, olog)
+    print(f"{case} L{L}: {len(glog)} steps, first differing decision: {i}")
+    if i is not None:
+        assert _near_threshold(glog[i], params) or _near_threshold(olog[i], params), (i, glog[i],
+                                                                                      olog[i])
+        return
+    assert st == so and stats["steps"] == ostats["steps"]
+    assert stats["accepted"] == ostats["accepted"] and stats["updates"] == ostats["updates"]
+    err = cabs_diff(xg, xo).max()
+    assert err <= TOL_END[L] * max(1.0, np.abs(lead_complex(xo)).max()), err
+
+
+def test_track_after_a_system_is_freed_and_another_loaded(ctx):
+    """A path graph is cached per context; freeing a system and loading
+    another of the same shape (which may get the freed one's address) must not
+    replay the old graph.  The second system is linear, so its fixed schedule
+    (Newton exact on a linear system) ends on the solution A^-1 b."""
+    L, n = 2, 8
+    wl = synth.dense8(1, "dd")
+    params = wl.params
+    f = ctx.load(wl.f, L)
+    xg = np.zeros_like(wl.x0_soa())
+    st, _, _ = libph.ph_track_path(ctx.h, f, None, wl.gamma_soa(), wl.x0_soa(), params, xg)
+    ctx.free(f)
+    assert st == libph.PH_OK
+    rng = np.random.default_rng(88)
+    A = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)) + 4 * np.eye(n)
+    b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    spec = synth.build_system(n, n, [[(A[i, j], [(j, 1)]) for j in range(n)] + [(-b[i], [])]
+                                     for i in range(n)])
+    f2 = ctx.load(spec, L)
+    x0 = soa_from_complex(np.ones(n), L)
+    xg = np.zeros_like(x0)
+    st, _, _ = libph.ph_track_path(ctx.h, f2, None, wl.gamma_soa(), x0, params, xg)
+    ctx.free(f2)
+    assert st == libph.PH_OK
+    so, xo, _, _ = oracle.track(oracle.System(spec, L), x0, wl.gamma_soa(), params)
+    assert so == oracle.OK
+    assert np.abs(lead_complex(xg) - np.linalg.solve(A, b)).max() < 1e-12
+    assert cabs_diff(xg, xo).max() <= TOL_END[L]

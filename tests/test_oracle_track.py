@@ -194,3 +194,34 @@ def test_nonfinite_start(orc):
     x0 = soa_from_complex([1.0, np.nan], L)
     status, x, st, log = orc.track(f, x0, gam, synth.default_params(L))
     assert status == orc.NONFINITE and not log
+
+
+@pytest.mark.parametrize("L", [2, 4])
+def test_path_tolerance_applies_before_t_1_only(orc, L):
+    """With tol_path > 0 the corrector's tests use it on the steps to t < 1,
+    and tol_res / tol_dx on the step that lands on t = 1: the interior steps
+    stop as soon as an update is below tol_path (some well above tol_dx, so the
+    path takes fewer corrector iterations), while the end point still meets
+    the closed form x(1)^3 = c to the working-precision tolerance."""
+    mp = mpmath.mp
+    mp.prec = 400
+    c = 0.3 + 0.4j
+    spec = synth.build_system(1, 1, [[(1.0, [(0, 3)]), (-c, [])]])
+    f = orc.System(spec, L)
+    g = complex(np.cos(1.1), np.sin(1.1))
+    gam = np.zeros((L, 2)); gam[0] = [g.real, g.imag]
+    x0 = soa_from_complex([1.0], L)
+    tight = synth.default_params(L)
+    loose = dict(tight, tol_path=1e-6)
+    st0, x_t, s_t, log_t = orc.track(f, x0, gam, tight)
+    st1, x_l, s_l, log_l = orc.track(f, x0, gam, loose)
+    assert st0 == orc.OK and st1 == orc.OK
+    interior = [r for r in log_l if r["accepted"] and r["t"] < 1.0]
+    assert interior and all(min(r["res"], r["dx"]) < 1e-6 for r in interior)
+    assert any(r["dx"] > tight["tol_dx"] and r["res"] > tight["tol_res"] for r in interior)
+    last = log_l[-1]
+    assert last["t"] == 1.0 and last["accepted"]
+    assert min(last["res"], last["dx"]) < tight["tol_res"]
+    assert s_l["newton_iters"] < s_t["newton_iters"]
+    cm = mp.mpc(c.real, c.imag)
+    assert abs(mp_vec(x_l, mp)[0] ** 3 - cm) < 10 * tight["tol_res"]
