@@ -225,7 +225,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * sum(per_step) / len(per_step), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "dd", "data": "synthetic",
             "config": {"workload": wl.name, "n": wl.n, "terms_per_poly": 64, "vars_per_term": 16,
                        "exponents": [1, 2, 3], "homotopy": "total-degree, k=1", "seed": args.seed},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -743,6 +743,278 @@ def serve_leg(libph, synth, ctx, nreq, seed, lin=0, seq_rate=None, sweep_request
             "kernel_launches": info["kernel_launches"]}
 
 
+def _planted_worker(job):
+    """One planted dense64 workload (its generation is pure Python: spread over
+    spawned worker processes)."""
+    seed, prec = job
+    sys.path.insert(0, ROOT)
+    from paper_1501_06625_gb300 import synth
+    wl, xs = synth.dense64_planted(seed, prec)
+    return wl, xs
+
+
+def planted_workloads(seeds, prec, workers=16):
+    import multiprocessing as mp
+    jobs = [(s, prec) for s in seeds]
+    if len(jobs) <= 2:
+        return [_planted_worker(j) for j in jobs]
+    with mp.get_context("spawn").Pool(min(workers, len(jobs))) as pool:
+        return pool.map(_planted_worker, jobs)
+
+
+def _soa(z, L):
+    out = np.zeros((L, 2, len(z)))
+    out[0, 0], out[0, 1] = np.real(z), np.imag(z)
+    return out
+
+
+def _err_vs(x, xs):
+    """max_i |x_i - x*_i| of an [L][2][n] end point against a double vector x*
+    (limb by limb from the smallest)."""
+    d = x.copy()
+    d[0, 0] -= np.real(xs)
+    d[0, 1] -= np.imag(xs)
+    d = d[::-1].sum(0)
+    return float(np.abs(d[0] + 1j * d[1]).max())
+
+
+def whole_path_leg(libph, synth, ctx, torch, dev, seed, npaths_dd, nsingle, qd_paths):
+    """Whole solution paths of the dense n = 64 workload (the headline system's shape) to
+    t = 1, each checked against its planted root.
+
+    The all-ones start root's total-degree path does not end at a regular root
+    for these systems (no seed tried does within thousands of steps), so every
+    path here is planted: synth.dense64_planted adds the constant term that
+    makes f(x*) = 0 exactly; tracking x* backwards (start system f, target the
+    total-degree system, gamma' = 1/gamma) lands on a start root of
+    x_i^{d_i} = 1, and the forward path from that root -- a path of the
+    dense64 total-degree homotopy -- ends at x*.  Corrector tolerance on the way
+    tol_path = 1e-8, at t = 1 the working precision (1e-24 DD, 1e-52 QD).
+
+    DD: `npaths_dd` systems; the backward paths run through the serving loop
+    (untimed preparation).  Timed: the plain single-path form (ph_track_path,
+    all DD) on the first `nsingle` paths, one by one (CUDA events); then all
+    paths at once through the serving loop, plain (lin_prec 0) and in the
+    precision form (lin_prec 3).  QD: `qd_paths` systems, single path.  A path
+    counts as successful when it reaches t = 1 within 1e-20 (DD) / 1e-48 (QD)
+    of x*."""
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    for prec, count in (("dd", npaths_dd), ("qd", qd_paths)):
+        if count <= 0:
+            continue
+        L = 2 if prec == "dd" else 4
+        tol_ok = 1e-20 if L == 2 else 1e-48
+        t0 = time.perf_counter()
+        wls = planted_workloads([seed + 100 + i for i in range(count)], prec)
+        gen_s = time.perf_counter() - t0
+        loaded = []
+        for wl, xs in wls:
+            f = ctx.load(wl.f, L)
+            G = ctx.load(synth.total_degree_start(wl.f), L)
+            loaded.append((wl, xs, f, G))
+        base = dict(synth.default_params(L), max_steps=4000, tol_path=1e-8,
+                    max_newton=3 if L == 2 else 5)
+        # backward paths: start roots (untimed)
+        t0 = time.perf_counter()
+        srv = libph.ph_server_create(ctx.h, max_n=64, pool_bytes=8 << 30, queue_cap=1024)
+        starts = []
+        try:
+            ids = []
+            for wl, xs, f, G in loaded:
+                gi = 1.0 / wl.gamma
+                gb = _soa([gi], L).reshape(L, 2)
+                ids.append(libph.ph_server_submit(ctx.h, srv, G, f, gb, _soa(xs, L), base))
+            for (wl, xs, f, G), jid in zip(loaded, ids):
+                xl = np.zeros((L, 2, 64))
+                st, _ = libph.ph_server_wait(ctx.h, srv, jid, 600000, x_out=xl)
+                ok = st["status"] == libph.PH_OK
+                starts.append(_soa(synth.nearest_start_root(wl.f, xl[0, 0] + 1j * xl[0, 1]), L)
+                              if ok else None)
+        finally:
+            libph.ph_server_destroy(srv)
+        prep_s = time.perf_counter() - t0
+        idx = [i for i, s0 in enumerate(starts) if s0 is not None]
+        row = {"systems": count, "start_roots_found": len(idx), "generation_s": gen_s,
+               "backward_s": prep_s, "params": {"tol_path": 1e-8, "max_newton": base["max_newton"],
+                                                "max_dt": base["max_dt"]}}
+        # the plain single-path form, one path at a time
+        single = []
+        for i in idx[:nsingle]:
+            wl, xs, f, G = loaded[i]
+            x0 = torch.tensor(starts[i], device=dev)
+            gam = torch.tensor(wl.gamma_soa(), device=dev)
+            xo = torch.empty_like(x0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st, sd, _ = libph.ph_track_path(ctx.h, f, None, gam, x0, base, xo)
+            e1.record(stream)
+            e1.synchronize()
+            err = _err_vs(xo.cpu().numpy(), xs)
+            single.append({"ms": e0.elapsed_time(e1), "status": libph.STATUS_NAMES[st],
+                           "steps": sd["steps"], "accepted": sd["accepted"],
+                           "newton_iters": sd["newton_iters"], "err_vs_planted": err,
+                           "ok": bool(st == libph.PH_OK and err <= tol_ok)})
+        if single:
+            ms = [r["ms"] for r in single]
+            row["single_path"] = {
+                "form": "ph_track_path, all " + prec.upper(), "paths": len(single),
+                "successful": sum(r["ok"] for r in single),
+                "paths_per_s": len(single) / (sum(ms) / 1e3),
+                "corrector_steps_per_s": sum(r["newton_iters"] for r in single) / (sum(ms) / 1e3),
+                "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
+                "steps_median": float(np.median([r["steps"] for r in single])),
+                "max_err_vs_planted": max(r["err_vs_planted"] for r in single),
+                "paths": single if len(single) <= 4 else None}
+        # all paths at once through the serving loop
+        if L == 2 and len(idx) > nsingle:
+            for lin in (0, 3):
+                params = dict(base, lin_prec=lin)
+                srv = libph.ph_server_create(ctx.h, max_n=64, pool_bytes=8 << 30, queue_cap=1024)
+                try:
+                    t0 = time.perf_counter()
+                    ids = [libph.ph_server_submit(ctx.h, srv, loaded[i][2], None,
+                                                  loaded[i][0].gamma_soa(), starts[i], params)
+                           for i in idx]
+                    lats, iters, oks, errs, f32, f64 = [], 0, 0, [], 0, 0
+                    for i, jid in zip(idx, ids):
+                        xe = np.zeros((L, 2, 64))
+                        st, lat = libph.ph_server_wait(ctx.h, srv, jid, 900000, x_out=xe)
+                        e = _err_vs(xe, loaded[i][1])
+                        lats.append(lat)
+                        errs.append(e)
+                        iters += st["newton_iters"]
+                        f32 += st["solves_f32"]
+                        f64 += st["solves_f64"]
+                        oks += int(st["status"] == libph.PH_OK and e <= tol_ok)
+                    wall = time.perf_counter() - t0
+                finally:
+                    libph.ph_server_destroy(srv)
+                r = {"form": "serving loop, " + ("all DD" if lin == 0 else
+                                                 "precision form (lin_prec 3)"),
+                     "paths": len(idx), "successful": oks, "wall_s": wall,
+                     "paths_per_s": len(idx) / wall, "corrector_steps_per_s": iters / wall,
+                     "p50_ms": float(np.percentile(lats, 50)),
+                     "p99_ms": float(np.percentile(lats, 99)),
+                     "max_err_vs_planted": float(max(errs)),
+                     "solves_f32": f32, "solves_f64": f64}
+                if "single_path" in row:
+                    r["paths_per_s_vs_single_path"] = r["paths_per_s"] / row["single_path"]["paths_per_s"]
+                row["served_lin%d" % lin] = r
+        for wl, xs, f, G in loaded:
+            ctx.free(f)
+            ctx.free(G)
+        out[f"dense64_planted_{prec}"] = row
+    return out
+
+
+def sparse512_leg(libph, synth, ctx, torch, dev, seed, steps):
+    """The very sparse n = 512 system in QD, total-degree homotopy
+    from the all-ones root, adaptive steps: the first `steps` predictor-corrector
+    steps through ph_track_path (the MGS solve of the 512 x 512 Jacobian
+    dominates), CUDA events, and one corrector iteration's kernels."""
+    stream = torch.cuda.current_stream(dev)
+    wl = synth.sparse512(seed, "qd")
+    f = ctx.load(wl.f, wl.L)
+    x0 = torch.tensor(wl.x0_soa(), device=dev)
+    gam = torch.tensor(wl.gamma_soa(), device=dev)
+    xo = torch.empty_like(x0)
+    params = dict(wl.params, max_steps=steps - 1)
+    libph.ph_track_path(ctx.h, f, None, gam, x0, dict(params, max_steps=0), xo)   # graph, tuning
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    st, sd, _ = libph.ph_track_path(ctx.h, f, None, gam, x0, params, xo)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    kind, size, vms = libph.ph_mgs_variant(ctx.h, 4, 512, 512)
+    ctx.free(f)
+    return {"workload": wl.name, "steps": sd["steps"], "accepted": sd["accepted"],
+            "rejected": sd["rejected"], "newton_iters": sd["newton_iters"],
+            "t_final": sd["t_final"], "status": libph.STATUS_NAMES[st], "ms": ms,
+            "corrector_steps_per_s": sd["newton_iters"] / (ms * 1e-3),
+            "ms_per_corrector_step": ms / max(1, sd["newton_iters"]),
+            "mgs_variant": {"kind": libph.MGS_KINDS[kind], "size": size,
+                            "ms_grid_cluster_tiled": vms}}
+
+
+def hard_precision_leg(libph, synth, ctx, torch, dev, seed, steps):
+    """The planted n = 128 workload where it is hard: precision128's shape with the coefficient
+    moduli spread over 12 decades between the equations (each polynomial's
+    terms share a modulus 10^{12 u_i}), so the Jacobian's rows differ in scale
+    by up to 1e12 (condition number about 2e13 at the planted root, in numpy).
+    The path is tracked backwards from x* (start system f, target the
+    total-degree system, gamma' = 1/gamma), where the Jacobian is the
+    ill-conditioned J_f: the first `steps` steps, single path, plain (lin_prec
+    0) against the precision form (lin_prec 1: Newton systems in double), the
+    same tolerances; then 152 copies at once through ph_track_paths with
+    lin_prec 0, 1 and 3 for the FP32/FP64 split."""
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    for prec in ("dd", "qd"):
+        wl, xs = synth.precision128_equations(seed, prec)
+        L = wl.L
+        f = ctx.load(wl.f, L)
+        G = ctx.load(synth.total_degree_start(wl.f), L)
+        gi = 1.0 / wl.gamma
+        gb = torch.tensor(_soa([gi], L).reshape(L, 2), device=dev)
+        x0 = torch.tensor(_soa(xs, L), device=dev)
+        mn = 5 if L == 2 else 6
+        row = {"steps": steps, "max_newton": mn, "max_dt": 1e-3}
+        ref = None
+        for lin in (0, 1):
+            params = dict(wl.params, max_steps=steps - 1, max_dt=1e-3, max_newton=mn, lin_prec=lin)
+            xo = torch.empty_like(x0)
+            libph.ph_track_path(ctx.h, G, f, gb, x0, dict(params, max_steps=0), xo)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st, sd, _ = libph.ph_track_path(ctx.h, G, f, gb, x0, params, xo)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            x = xo.cpu().numpy()
+            r = {"status": libph.STATUS_NAMES[st], "ms": ms, "accepted": sd["accepted"],
+                 "rejected": sd["rejected"], "t_final": sd["t_final"],
+                 "newton_iters": sd["newton_iters"], "solves_f64": sd["solves_f64"],
+                 "escalated": sd["escalated"], "wp_rest": sd["wp_rest"],
+                 "cond_estimate": sd["cond"],
+                 "ms_per_accepted_step": ms / max(1, sd["accepted"])}
+            if ref is None:
+                ref = (r, x)
+            else:
+                d = (x - ref[1])[::-1].sum(0)
+                r["end_point_diff_vs_plain"] = float(np.abs(d[0] + 1j * d[1]).max())
+                r["speedup_per_accepted_step"] = (ref[0]["ms_per_accepted_step"]
+                                                  / r["ms_per_accepted_step"])
+            row[f"single_lin{lin}"] = r
+        bx = torch.tensor(np.repeat(_soa(xs, L)[None], 152, axis=0), device=dev)
+        for lin in (0, 1, 3):
+            params = dict(wl.params, max_steps=steps - 1, max_dt=1e-3, max_newton=mn, lin_prec=lin)
+            bo = torch.empty_like(bx)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            stats, _ = libph.ph_track_paths(ctx.h, G, f, gb, bx, params, bo)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            acc = sum(x["accepted"] for x in stats)
+            row[f"batch152_lin{lin}"] = {
+                "ms": ms, "accepted_steps_per_s": acc / (ms * 1e-3),
+                "solves_f32": sum(x["solves_f32"] for x in stats),
+                "solves_f64": sum(x["solves_f64"] for x in stats),
+                "escalated": sum(x["escalated"] for x in stats),
+                "wp_rest": sum(x["wp_rest"] for x in stats),
+                "cond_estimate_max": float(max(x["cond"] for x in stats))}
+        ctx.free(f)
+        ctx.free(G)
+        out[f"precision128eq_{prec}"] = row
+    return out
+
+
 def combine_ranks(dist, torch, tot_ms: float, iters: int, device):
     """Whole-job figures of a replicas run: the slowest rank's timed ms and the
     corrector steps of all ranks (each rank tracks its own path; the only
@@ -793,11 +1065,11 @@ def mgs_case(spec: str) -> None:
     ctx = libph.Context(0)
     for _ in range(reps):
         libph.ph_mgs_solve(ctx.h, L, N, n, J, rhs, dx)
-    cl, ms_grid, ms_cluster = libph.ph_mgs_variant(ctx.h, L, N, n)
+    kind, size, ms = libph.ph_mgs_variant(ctx.h, L, N, n)
     ctx.close()
     print(json.dumps({"mgs_case": {"L": L, "N": N, "n": n, "solves": reps,
-                                   "cluster": cl, "ms_grid": ms_grid,
-                                   "ms_cluster": ms_cluster}}))
+                                   "variant": libph.MGS_KINDS[kind], "size": size,
+                                   "ms_grid_cluster_tiled": ms}}))
 
 
 def monodromy_paths_case(spec: str) -> None:
@@ -864,6 +1136,19 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=384,
                     help="requests of the serving leg (0 skips it)")
     ap.add_argument("--no-cyclic", action="store_true", help="skip the cyclic n-roots legs")
+    ap.add_argument("--monodromy", action="store_true",
+                    help="also run the cyclic n-roots monodromy legs (the paper's one-path runs, "
+                         "loops in flight, the degree by loops): outside the hot-path rows")
+    ap.add_argument("--whole-paths", type=int, default=304,
+                    help="planted dense64 DD paths tracked whole (0 skips the whole-path leg)")
+    ap.add_argument("--whole-paths-single", type=int, default=8,
+                    help="of these, how many the single-path form tracks one by one")
+    ap.add_argument("--whole-paths-qd", type=int, default=3,
+                    help="planted dense64 QD paths tracked whole by the single-path form")
+    ap.add_argument("--sparse-steps", type=int, default=8,
+                    help="predictor-corrector steps of the sparse n = 512 QD path (0 skips)")
+    ap.add_argument("--hard-steps", type=int, default=6,
+                    help="steps of the ill-conditioned precision128 segment (0 skips)")
     ap.add_argument("--only-mgs", default=None, metavar="L,N,n,reps",
                     help="only time least-squares solves of one shape (for kernel profiles)")
     ap.add_argument("--only-monodromy-paths", default=None, metavar="n,L,paths,steps",
@@ -946,6 +1231,10 @@ def main():
         msq, statsq, _ = track_leg(libph, ctx, fq, wq, dev, kq, 1, torch, flush)
         qd = summarize(msq, statsq)
         qd.pop("launches")
+        qd["note"] = ("the first %d steps from the all-ones root: the degree-0 first "
+                      "prediction needs dt ~ 1e-7 for a QD corrector, so these steps are "
+                      "mostly rejections (accepted: %d); whole QD paths are in whole_paths"
+                      % (SEGMENT[4], statsq[-1]["accepted"]))
 
     # many-path form: the same system, distinct total-degree start roots, the
     # same segment per path, one persistent kernel (ph_track_paths)
@@ -988,6 +1277,7 @@ def main():
     cyclic = monodromy = None
     if not args.no_cyclic and rank == 0:
         cyclic = cyclic_leg(libph, synth, ctx, torch, dev, peak)
+    if args.monodromy and rank == 0:
         monodromy = monodromy_leg(libph, synth, ctx, torch, dev, args.seed,
                                   args.monodromy_segment)
         if args.monodromy_loops > 0:
@@ -995,6 +1285,16 @@ def main():
                 libph, synth, ctx, args.seed, args.monodromy_loops, monodromy)
         monodromy["degree"] = monodromy_degree_leg(
             synth, ctx, args.seed, [(16, 32)] + ([(64, 76)] if args.monodromy_degree_64 else []))
+
+    whole = sparse = hard = None
+    if rank == 0 and world == 1:
+        if args.whole_paths > 0 or args.whole_paths_qd > 0:
+            whole = whole_path_leg(libph, synth, ctx, torch, dev, args.seed, args.whole_paths,
+                                   args.whole_paths_single, args.whole_paths_qd)
+        if args.sparse_steps > 0:
+            sparse = sparse512_leg(libph, synth, ctx, torch, dev, args.seed, args.sparse_steps)
+        if args.hard_steps > 0:
+            hard = hard_precision_leg(libph, synth, ctx, torch, dev, args.seed, args.hard_steps)
 
     precision = None
     if args.precision_paths > 0 and rank == 0:
@@ -1054,7 +1354,7 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms_max / len(ms),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic",
+            "dtype": "dd", "data": "synthetic",
             "config": {"workload": wl.name, "n": wl.n, "terms_per_poly": 64, "vars_per_term": 16,
                        "exponents": [1, 2, 3], "homotopy": "total-degree from all-ones, k=1",
                        "seed": args.seed, "precision": "complex double-double",
@@ -1065,7 +1365,8 @@ def main():
             "p50_segment_ms": s["p50_segment_ms"], "p99_segment_ms": s["p99_segment_ms"],
             "path": s["path"], "qd": qd, "batched": batch, "serving": serve,
             "serving_mixed": serve_mixed, "precision": precision, "cyclic": cyclic,
-            "cyclic_monodromy_path": monodromy,
+            "cyclic_monodromy_path": monodromy, "whole_paths": whole,
+            "sparse512_segment": sparse, "precision_ill_conditioned": hard,
             "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": s["launches"], "roofline": roof, "roofline_sparse512_mgs": roof512,

@@ -264,11 +264,19 @@ ph_status ph_track_paths(ph_ctx *ctx, const ph_system *f, const ph_system *g,
  * admits waiting jobs and relaunches the kernel when it has gone idle. */
 typedef struct ph_server ph_server;
 typedef struct {
-  int32_t max_n;        /* largest number of variables of a job                 */
+  int32_t max_n;        /* largest number of variables of a job run by one block */
   int32_t max_blocks;   /* resident blocks, 0 = two per SM                      */
   int64_t pool_bytes;   /* device pool for the jobs' workspaces                 */
   int32_t queue_cap;    /* jobs on the device at once (table slots)             */
-  int32_t reserved;     /* 0                                                    */
+  /* > 0: the large-job route.  A job with more than big_n variables (any
+   * number, not bounded by max_n) is not given to one block, whose O(n^3)
+   * solve would take one SM minutes: it runs alone on the whole GPU through
+   * the single-path tracker (ph_track_path) on a context of the server's own,
+   * in arrival order.  When such a job is next, no further small job is
+   * admitted, the small jobs on the device finish, the large one runs, then
+   * admission resumes.  Its systems must stay loaded until it is done.
+   * 0: every job runs on one block (and n <= max_n). */
+  int32_t big_n;
 } ph_server_config;
 
 ph_status ph_server_create(ph_ctx *ctx, const ph_server_config *cfg, ph_server **out);
@@ -338,6 +346,19 @@ ph_status ph_mgs_set_variant(ph_ctx *ctx, ph_prec prec, int N, int n, int kind, 
 ph_status ph_sum_lanes(ph_ctx *ctx, const ph_system *f, const ph_system *g, int *lanes,
                        double *ms);
 
+/* The summation's lanes per output inside the many-path and serving kernels
+ * (one thread block per path), the paper's threads per sum (Section 3.3):
+ * ph_track_paths times 1, 2, 4, 8, 16 and 32 lanes on its first batch of a
+ * system that fills the GPU (as many paths as SMs or more) -- one corrector
+ * iteration of a full GPU of blocks per choice -- and keeps the fastest on f;
+ * until then, and for the serving loop's jobs of a system never batched, 4.
+ * ph_block_lanes reports the lanes in use and (ms, optional, 6 doubles) the
+ * measured milliseconds per launch of each choice, -1 where not measured;
+ * ph_set_block_lanes pins a choice (0: back to untimed, timed again by the
+ * next batch that fills the GPU). */
+ph_status ph_block_lanes(ph_ctx *ctx, const ph_system *f, int *lanes, double *ms);
+ph_status ph_set_block_lanes(ph_ctx *ctx, const ph_system *f, int lanes);
+
 /* Host-side step-size controller of the path tracker, exported so it can be
  * checked without a GPU: the same code runs inside the device controller.
  * Fig. 3. */
@@ -399,6 +420,30 @@ ph_status ph_fp64_peak(ph_ctx *ctx, double ms_target, double *gops);
 ph_status ph_mgs_solve_static(int device, void *cuda_stream, ph_prec prec, int N, int n,
                               const double *J, const double *rhs, double *dx,
                               double *resid_norm);
+
+/* Failure handling (the paper has no counterpart).
+ *
+ * ph_set_wait_limit: the limit, in milliseconds, of every bounded device-side
+ * wait in this context's kernels (the pivot hand-offs and grid barriers of the
+ * least-squares solves); 2000 by default.  A wait that runs out makes the
+ * call (or the path) end with PH_TIMEOUT and leaves the context usable.
+ *
+ * ph_set_memory_limit: a cap, in bytes, on the device memory that all of this
+ * process's libph objects hold together (0, the default: none); *in_use
+ * (optional) receives what they hold now.  An allocation beyond the cap fails
+ * as on a full device (PH_ENOMEM), so a caller can keep the library within a
+ * share of the GPU; it also lets tests reach every allocation-failure path
+ * without exhausting a device.
+ *
+ * ph_debug_withhold_pivot: test support.  From now on, the least-squares
+ * solves of this context withhold the hand-off of pivot k (the grid kernel
+ * never publishes its flag; the tiled kernel's block 0 never arrives at its
+ * barrier), so the other blocks' bounded waits run out and the call returns
+ * PH_TIMEOUT; k < 0 restores normal operation.  Nothing faults and nothing
+ * waits beyond the wait limit. */
+ph_status ph_set_wait_limit(ph_ctx *ctx, double ms);
+ph_status ph_set_memory_limit(int64_t bytes, int64_t *in_use);
+ph_status ph_debug_withhold_pivot(ph_ctx *ctx, int k);
 
 /* Library version string. */
 const char *ph_version(void);

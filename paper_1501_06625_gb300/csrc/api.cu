@@ -1,5 +1,6 @@
 // api.cu -- context management, error reporting, and the ph_eval_jac /
 // ph_mgs_solve entry points of the C ABI (include/ph.h).
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 
@@ -26,7 +27,54 @@ bool ph_is_device_ptr(const void *p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-extern "C" const char *ph_version(void) { return "libph 0.1 (sm_103a)"; }
+extern "C" const char *ph_version(void) { return "libph 0.2 (sm_103a)"; }
+
+// ---- device memory accounting ---------------------------------------------------
+
+static std::atomic<int64_t> g_dev_used{0};
+static std::atomic<int64_t> g_dev_limit{0};        // 0: no cap
+
+cudaError_t ph_dev_alloc(void **p, size_t bytes) {
+  const int64_t lim = g_dev_limit.load();
+  const int64_t now = g_dev_used.fetch_add((int64_t)bytes) + (int64_t)bytes;
+  if (lim > 0 && now > lim) {
+    g_dev_used.fetch_sub((int64_t)bytes);
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) g_dev_used.fetch_sub((int64_t)bytes);
+  return e;
+}
+
+void ph_dev_free(void *p, size_t bytes) {
+  if (!p) return;
+  cudaFree(p);
+  g_dev_used.fetch_sub((int64_t)bytes);
+}
+
+extern "C" ph_status ph_set_memory_limit(int64_t bytes, int64_t *in_use) {
+  if (bytes < 0) return PH_EINVAL;
+  g_dev_limit.store(bytes);
+  if (in_use) *in_use = g_dev_used.load();
+  return PH_OK;
+}
+
+extern "C" ph_status ph_set_wait_limit(ph_ctx *ctx, double ms) {
+  if (!ctx) return PH_EINVAL;
+  if (!(ms > 0.0) || ms > 600000.0) return ph_fail(ctx, PH_EINVAL, "ph_set_wait_limit: out of range");
+  ctx->wait_ns = (unsigned long long)(ms * 1e6);
+  return PH_OK;
+}
+
+void ph_track_release(ph_ctx *ctx);
+
+extern "C" ph_status ph_debug_withhold_pivot(ph_ctx *ctx, int k) {
+  if (!ctx) return PH_EINVAL;
+  ctx->withhold = k < 0 ? -1 : k;
+  ph_track_release(ctx);                            // captured graphs hold the old value
+  return PH_OK;
+}
 
 extern "C" ph_status ph_init(ph_ctx **out, int device, void *cuda_stream) {
   if (!out) return PH_EINVAL;
@@ -49,8 +97,6 @@ extern "C" ph_status ph_init(ph_ctx **out, int device, void *cuda_stream) {
   return PH_OK;
 }
 
-void ph_track_release(ph_ctx *ctx);
-
 extern "C" ph_status ph_destroy(ph_ctx *c) {
   if (!c) return PH_EINVAL;
   cudaSetDevice(c->device);
@@ -60,7 +106,8 @@ extern "C" ph_status ph_destroy(ph_ctx *c) {
                     &c->out_J, &c->out_dx, &c->slots, &c->ptab, &c->scal, &c->A, &c->R,
                     &c->nrm2, &c->irkk, &c->dxv, &c->state, &c->hist, &c->xw, &c->logbuf,
                     &c->ystage, &c->flags, &c->spow, &c->bws, &c->bq, &c->bx0, &c->bxo,
-                    &c->bstats, &c->blog};
+                    &c->bstats, &c->blog, &c->btune, &c->tuneA, &c->tuneW, &c->tuneN,
+                    &c->tuneF, &c->tuneX, &c->tuneS, &c->mgs_part};
   for (DevBuf *b : bufs) b->release();
   delete c;
   return PH_OK;

@@ -77,6 +77,66 @@ int blocks_per_sm(size_t smem) {
   return nb < 1 ? 1 : (nb > 2 ? 2 : nb);
 }
 
+template <class P>
+cudaError_t launch_any(int L, const BatchArgs &args, int grid, size_t smem, cudaStream_t st) {
+  return L == 1 ? launch_paths<F64>(args, grid, smem, st)
+       : L == 2 ? launch_paths<DD>(args, grid, smem, st) : launch_paths<QD>(args, grid, smem, st);
+}
+
+// The summation's lanes per output inside the per-block kernel (the paper's
+// threads per sum, Section 3.3), chosen by timing: `grid` copies of one start
+// point (a full GPU of blocks, each the same work), one corrector iteration
+// each (a fixed step with one update), for 1, 2, 4, 8, 16 and 32 lanes after
+// one untimed launch; the fastest is kept on the system.
+static cudaError_t tune_block_lanes(ph_ctx *ctx, const ph_system *f, const BatchArgs &base,
+                                   int grid, size_t smem, const double *x0_first) {
+  const int L = f->L;
+  const long pt = 2L * L * f->n;
+  BatchArgs t = base;
+  cudaError_t e = ctx->btune.ensure(sizeof(double) * pt * 2 * grid + sizeof(ph_path_stats) * grid);
+  if (e != cudaSuccess) return e;
+  double *tx0 = ctx->btune.as<double>(), *txo = tx0 + pt * grid;
+  for (int q = 0; q < grid && e == cudaSuccess; ++q)
+    e = cudaMemcpyAsync(tx0 + pt * q, x0_first, sizeof(double) * pt, cudaMemcpyDeviceToDevice,
+                        ctx->stream);
+  t.npaths = grid;
+  t.x0 = tx0;
+  t.x_out = txo;
+  t.stats = (ph_path_stats *)(txo + pt * grid);
+  t.log = nullptr;
+  t.base.log_cap = 0;
+  t.base.p.fixed_steps = 1;
+  t.base.p.max_newton = 1;
+  t.base.p.lin_prec = 0;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  static const int lanes[6] = {1, 2, 4, 8, 16, 32};
+  float best = 1e30f;
+  int choice = kSG;
+  for (int v = -1; v < 6 && e == cudaSuccess; ++v) {
+    t.base.sum_lanes = lanes[v < 0 ? 2 : v];          // v = -1: warm-up
+    e = cudaMemsetAsync(t.next, 0, sizeof(unsigned int), ctx->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
+    if (e == cudaSuccess) e = launch_any<DD>(L, t, grid, smem, ctx->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess && v >= 0) {
+      f->block_ms[v] = ms;
+      if (ms < best) {
+        best = ms;
+        choice = lanes[v];
+      }
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e == cudaSuccess) f->block_lanes = choice;
+  return e;
+}
+
 }  // namespace
 
 // the system part of a job (shared with the serving form)
@@ -97,6 +157,7 @@ void ph_job_fill_system(Job &j, const ph_system *f, const ph_system *g) {
     j.nsg = (long)(g->maxv + 1) * g->Mp;
   }
   j.ldA = ph_lda(f->N);
+  j.sum_lanes = f->block_lanes > 0 ? f->block_lanes : kSG;
   JobLayout o = job_layout(j.L, j.n, j.ldA, j.emax, j.nsf, j.nsg);
   j.o_x = o.o_x; j.o_dx = o.o_dx; j.o_hist = o.o_hist; j.o_ptab = o.o_ptab; j.o_spow = o.o_spow;
   j.o_A = o.o_A; j.o_W = o.o_W; j.o_fslots = o.o_fslots; j.o_gslots = o.o_gslots;
@@ -105,6 +166,26 @@ void ph_job_fill_system(Job &j, const ph_system *f, const ph_system *g) {
 
 long ph_job_ws_doubles(const Job &j) {
   return job_layout(j.L, j.n, j.ldA, j.emax, j.nsf, j.nsg).stride;
+}
+
+extern "C" ph_status ph_block_lanes(ph_ctx *ctx, const ph_system *f, int *lanes, double *ms) {
+  if (!ctx) return PH_EINVAL;
+  if (!f || f->ctx != ctx || !lanes) return ph_fail(ctx, PH_EINVAL, "ph_block_lanes: invalid argument");
+  *lanes = f->block_lanes > 0 ? f->block_lanes : kSG;
+  if (ms)
+    for (int q = 0; q < 6; ++q) ms[q] = f->block_ms[q];
+  return PH_OK;
+}
+
+extern "C" ph_status ph_set_block_lanes(ph_ctx *ctx, const ph_system *f, int lanes) {
+  if (!ctx) return PH_EINVAL;
+  if (!f || f->ctx != ctx || (lanes != 0 && lanes != 1 && lanes != 2 && lanes != 4 &&
+                              lanes != 8 && lanes != 16 && lanes != 32))
+    return ph_fail(ctx, PH_EINVAL, "ph_set_block_lanes: invalid argument");
+  f->block_lanes = lanes;
+  if (lanes == 0)
+    for (int q = 0; q < 6; ++q) f->block_ms[q] = -1.0f;
+  return PH_OK;
 }
 
 extern "C" ph_status ph_track_paths(ph_ctx *ctx, const ph_system *f, const ph_system *g,
@@ -180,9 +261,14 @@ extern "C" ph_status ph_track_paths(ph_ctx *ctx, const ph_system *f, const ph_sy
   a.log = dlog;
   a.next = ctx->bq.as<unsigned int>();
   a.ws = ctx->bws.as<double>();
-  PH_CUDA(ctx, L == 1 ? launch_paths<F64>(a, grid, smem, ctx->stream)
-               : L == 2 ? launch_paths<DD>(a, grid, smem, ctx->stream)
-                      : launch_paths<QD>(a, grid, smem, ctx->stream));
+  // a batch that fills the GPU times the summation's lanes per output once
+  // per system (the first time), before the paths run
+  if (f->block_lanes == 0 && npaths >= ctx->sm_count) {
+    PH_CUDA(ctx, tune_block_lanes(ctx, f, a, grid, smem, dx0));
+    PH_CUDA(ctx, cudaMemsetAsync(ctx->bq.p, 0, sizeof(unsigned int), ctx->stream));
+  }
+  a.base.sum_lanes = f->block_lanes > 0 ? f->block_lanes : kSG;
+  PH_CUDA(ctx, launch_any<DD>(L, a, grid, smem, ctx->stream));
   if (host_out) PH_CUDA(ctx, cudaMemcpyAsync(x_out, dxo, xbytes, cudaMemcpyDeviceToHost, ctx->stream));
   if (stats)
     PH_CUDA(ctx, cudaMemcpyAsync(stats, a.stats, sizeof(ph_path_stats) * (size_t)npaths,

@@ -10,21 +10,27 @@
 
 #include "ph.h"
 
+// Device allocations of the library, counted against the cap set by
+// ph_set_memory_limit (api.cu): beyond it an allocation fails with
+// cudaErrorMemoryAllocation, as on a full device.
+cudaError_t ph_dev_alloc(void **p, size_t bytes);
+void ph_dev_free(void *p, size_t bytes);
+
 // A growable device buffer owned by a context or a system.
 struct DevBuf {
   void *p = nullptr;
   size_t cap = 0;
   cudaError_t ensure(size_t bytes) {
     if (bytes <= cap) return cudaSuccess;
-    if (p) cudaFree(p);
+    if (p) ph_dev_free(p, cap ? cap : 16);
     p = nullptr;
     cap = 0;
-    cudaError_t e = cudaMalloc(&p, bytes ? bytes : 16);
+    cudaError_t e = ph_dev_alloc(&p, bytes ? bytes : 16);
     if (e == cudaSuccess) cap = bytes;
     return e;
   }
   void release() {
-    if (p) cudaFree(p);
+    if (p) ph_dev_free(p, cap ? cap : 16);
     p = nullptr;
     cap = 0;
   }
@@ -83,14 +89,16 @@ struct ph_ctx {
   DevBuf in_x, in_gamma, in_t, in_J, in_rhs;       // staged host inputs
   DevBuf out_h, out_J, out_dx;                      // staged outputs
   DevBuf slots, ptab, scal, A, R, nrm2, irkk, dxv, state, hist, xw, logbuf, ystage, flags, spow;
-  DevBuf bws, bq, bx0, bxo, bstats, blog;           // many-path tracking
+  DevBuf bws, bq, bx0, bxo, bstats, blog, btune;    // many-path tracking
   // the MGS variant chosen for each shape (key (L, N, n)): 0 the grid kernel,
   // C > 0 the cluster kernel with C CTAs; scratch buffers of the choice
   std::map<long long, int> mgs_variant;
   std::map<long long, MgsTimes> mgs_times;
   DevBuf tuneA, tuneW, tuneN, tuneF, tuneX, tuneS, mgs_part;
-  // limit of every bounded device-side wait (ns)
+  // limit of every bounded device-side wait (ns), and the pivot whose
+  // hand-off the solves withhold (test support; -1: none)
   unsigned long long wait_ns = 2000000000ull;
+  int withhold = -1;
 };
 
 // A loaded polynomial system: the instruction layout of Section 3.2 (terms
@@ -118,6 +126,11 @@ struct ph_system {
   // of 1, 2, 4, 8, 16 and 32 lanes
   mutable int sum_lanes = 0;
   mutable float sum_ms[6] = {-1, -1, -1, -1, -1, -1};
+  // the same choice for the summation inside the many-path and serving
+  // kernels (one block per path), timed on a batch of that kernel: 0 until
+  // timed (4 lanes are used), with the times (ms per launch) of 1 .. 32 lanes
+  mutable int block_lanes = 0;
+  mutable float block_ms[6] = {-1, -1, -1, -1, -1, -1};
 };
 
 // ---- helpers (api.cu)
@@ -201,7 +214,7 @@ long ph_mgs_tile_part(int L, int n, int R);
 cudaError_t ph_mgs_tile_launch(int sm_count, cudaStream_t stream, int L, int N, int n, int R,
                                double *A, long ldA, double *W, double *nrm2, double *part,
                                double *dx, PathState *st, const int *skip, double *resid,
-                               unsigned long long limit_ns);
+                               unsigned long long limit_ns, int withhold = -1);
 cudaError_t ph_mgs_cluster_launch(cudaStream_t stream, int C, int L, int N, int n, const double *A,
                                   long ldA, double *W, double *dx, PathState *st, const int *skip,
                                   double *resid, double *nrm_out);   // nrm_out: r_kk^2 (may be null)

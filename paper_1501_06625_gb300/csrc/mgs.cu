@@ -45,7 +45,7 @@ using namespace ph;
 
 namespace {
 
-constexpr unsigned long long kWaitLimitNs = 2000000000ull;
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // default of the context setting
 constexpr int kThreads = 128;
 constexpr int kRowCache = 4;        // pivot rows a lane keeps in registers (N <= 256)
 constexpr int kDowndateBits = 20;   // cancellation beyond which a norm is recomputed
@@ -58,7 +58,7 @@ PHD unsigned long long global_timer_ns() {
 
 // Thread 0 waits until *flag == tag (or the timeout flag is set); the block
 // then proceeds.  Returns false when the wait gave up.
-__device__ bool wait_flag(const int *flag, int tag, PathState *st) {
+__device__ bool wait_flag(const int *flag, int tag, PathState *st, unsigned long long limit_ns) {
   __shared__ int s_ok;
   if (threadIdx.x == 0) {
     volatile const int *f = flag;
@@ -69,7 +69,7 @@ __device__ bool wait_flag(const int *flag, int tag, PathState *st) {
       unsigned spins = 0;
       while (*f != tag) {
         if (*tmo) { ok = 0; break; }
-        if ((++spins & 255u) == 0 && global_timer_ns() - t0 > kWaitLimitNs) {
+        if ((++spins & 255u) == 0 && global_timer_ns() - t0 > limit_ns) {
           atomicExch(&st->timeout, 1);
           ok = 0;
           break;
@@ -158,7 +158,8 @@ __global__ void __launch_bounds__(kThreads) k_mgs(int N, int n, double *__restri
                                                   double *__restrict__ W, double *__restrict__ nrm2,
                                                   double *__restrict__ dx, int *__restrict__ ready,
                                                   PathState *st, const int *__restrict__ skip,
-                                                  double *__restrict__ resid) {
+                                                  double *__restrict__ resid,
+                                                  unsigned long long limit_ns, int withhold) {
   if (skip && *skip) return;
   typedef typename P::real real;
   typedef Part<P> PO;
@@ -183,10 +184,10 @@ __global__ void __launch_bounds__(kThreads) k_mgs(int N, int n, double *__restri
       r_store<P>(nrm2, nc, j, s);
       if (j == 0) r_store<P>(ninv, nc, 0, P::recip(s));
     }
-    if (j == 0) publish(&ready[0], tag);
+    if (j == 0 && withhold != 0) publish(&ready[0], tag);
   }
   for (int k = 0; k < last_own; ++k) {
-    if (!wait_flag(&ready[k], tag, st)) break;
+    if (!wait_flag(&ready[k], tag, st, limit_ns)) break;
     const real r2 = r_load_cg<P>(nrm2, nc, k);
     const real inv2 = r_load_cg<P>(ninv, nc, k);
     const double lead = P::lead(r2);
@@ -254,8 +255,14 @@ __global__ void __launch_bounds__(kThreads) k_mgs(int N, int n, double *__restri
       // chain) warp 0 computes the norm and its inverse while the other warps
       // update the column, warp 1 taking warp 0's rows of the real part too; for
       // other columns every warp updates its own rows and warp 0 then downdates.
+      // Tall columns (N > 256) downdate nothing: a column's norm is needed only
+      // when it becomes the next pivot, and there it is summed afresh from the
+      // updated column (a downdate per column and pivot costs warp 0 more than
+      // one fresh sum per column, and a fresh sum has no cancellation).
       const bool crit = j == k + 1;
-      if (!(crit && w == 0)) {
+      const bool fresh = N > 64 * kRowCache;
+      const bool split = crit && !fresh;
+      if (!(split && w == 0)) {
         // a_j -= alpha a_k:  re: ajr - alr akr + ali aki;  im: aji - alr aki - ali akr
 #pragma unroll
         for (int q = 0; q < kRowCache; ++q) {
@@ -276,7 +283,7 @@ __global__ void __launch_bounds__(kThreads) k_mgs(int N, int n, double *__restri
           else
             store_part<P>(aj, Ap, 1, i, PO::upd(load_part<P>(aj, Ap, 1, i), alr, aki, ali, akr, -1.0));
         }
-        if (crit && w == 1) {                      // warp 0's rows of the real part
+        if (split && w == 1) {                     // warp 0's rows of the real part
           for (int i = lane; i < N; i += 64) {
             real akr = c0_r, aki = c0_i;
             if (i != lane) {
@@ -287,26 +294,37 @@ __global__ void __launch_bounds__(kThreads) k_mgs(int N, int n, double *__restri
           }
         }
       }
-      if (w == 0) {
-        const real s = P::sub(old, P::mul(P::add(P::mul(alr, alr), P::mul(ali, ali)), r2));
-        const bool rec = !(P::lead(s) > ldexp(P::lead(old), -kDowndateBits));
-        if (lane == 0) {
-          sh_rec = rec;
-          if (!rec) {
+      if (fresh) {
+        if (crit) {                                // the same branch in every thread
+          __syncthreads();
+          const real s = col_norm2<P>(aj, Ap, N, part, r0, sh_acc, sh_r);
+          if (tid == 0) {
             r_store<P>(nrm2, nc, j, s);
-            if (crit) r_store<P>(ninv, nc, j, P::recip(s));
+            r_store<P>(ninv, nc, j, P::recip(s));
+          }
+        }
+      } else {
+        if (w == 0) {
+          const real s = P::sub(old, P::mul(P::add(P::mul(alr, alr), P::mul(ali, ali)), r2));
+          const bool rec = !(P::lead(s) > ldexp(P::lead(old), -kDowndateBits));
+          if (lane == 0) {
+            sh_rec = rec;
+            if (!rec) {
+              r_store<P>(nrm2, nc, j, s);
+              if (crit) r_store<P>(ninv, nc, j, P::recip(s));
+            }
+          }
+        }
+        __syncthreads();
+        if (sh_rec) {                              // the same value in every thread
+          const real s = col_norm2<P>(aj, Ap, N, part, r0, sh_acc, sh_r);
+          if (tid == 0) {
+            r_store<P>(nrm2, nc, j, s);
+            if (j == k + 1) r_store<P>(ninv, nc, j, P::recip(s));
           }
         }
       }
-      __syncthreads();
-      if (sh_rec) {                                // the same value in every thread
-        const real s = col_norm2<P>(aj, Ap, N, part, r0, sh_acc, sh_r);
-        if (tid == 0) {
-          r_store<P>(nrm2, nc, j, s);
-          if (j == k + 1) r_store<P>(ninv, nc, j, P::recip(s));
-        }
-      }
-      if (j == k + 1) publish(&ready[j], tag);
+      if (j == k + 1 && j != withhold) publish(&ready[j], tag);
     }
   }
   // completion: block 0 waits for every block, then solves R dx = Q^H rhs
@@ -323,7 +341,7 @@ __global__ void __launch_bounds__(kThreads) k_mgs(int N, int n, double *__restri
     unsigned spins = 0;
     while (*done < (unsigned)G) {
       if (*tmo) break;
-      if ((++spins & 255u) == 0 && global_timer_ns() - t0 > kWaitLimitNs) {
+      if ((++spins & 255u) == 0 && global_timer_ns() - t0 > limit_ns) {
         atomicExch(&st->timeout, 1);
         break;
       }
@@ -367,7 +385,8 @@ __global__ void __launch_bounds__(kThreads) k_mgs(int N, int n, double *__restri
 template <class P>
 cudaError_t launch_p(int sm_count, cudaStream_t stream, int N, int n, double *A, long ldA,
                      double *W, double *nrm2, double *dx, int *ready, PathState *st,
-                     const int *skip, double *resid) {
+                     const int *skip, double *resid, unsigned long long limit_ns = kWaitLimitNs,
+                     int withhold = -1) {
   const size_t smem = sizeof(double) * 2 * P::L * (size_t)n;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_mgs<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -377,7 +396,8 @@ cudaError_t launch_p(int sm_count, cudaStream_t stream, int N, int n, double *A,
   int grid = n + 1 < sm_count ? n + 1 : sm_count;
   if (grid < 1) grid = 1;
   // cooperative launch: the driver guarantees that all blocks are resident
-  void *args[] = {&N, &n, &A, &ldA, &W, &nrm2, &dx, &ready, &st, (void *)&skip, &resid};
+  void *args[] = {&N, &n, &A, &ldA, &W, &nrm2, &dx, &ready, &st, (void *)&skip, &resid,
+                  &limit_ns, &withhold};
   return cudaLaunchCooperativeKernel((const void *)k_mgs<P>, dim3(grid), dim3(kThreads), args,
                                      smem, stream);
 }
@@ -458,11 +478,16 @@ static cudaError_t mgs_launch_code(ph_ctx *ctx, int code, cudaStream_t s, int L,
     return ph_mgs_cluster_launch(s, size, L, N, n, A, ldA, W, dx, st, skip, resid, nrm2);
   if (kind == PH_MGS_TILED)
     return ph_mgs_tile_launch(ctx->sm_count, s, L, N, n, size, A, ldA, W, nrm2,
-                              ctx->mgs_part.as<double>(), dx, st, skip, resid, ctx->wait_ns);
+                              ctx->mgs_part.as<double>(), dx, st, skip, resid, ctx->wait_ns,
+                              ctx->withhold);
   if (L == 1)
-    return launch_p<F64>(ctx->sm_count, s, N, n, A, ldA, W, nrm2, dx, flags, st, skip, resid);
-  if (L == 2) return launch_p<DD>(ctx->sm_count, s, N, n, A, ldA, W, nrm2, dx, flags, st, skip, resid);
-  return launch_p<QD>(ctx->sm_count, s, N, n, A, ldA, W, nrm2, dx, flags, st, skip, resid);
+    return launch_p<F64>(ctx->sm_count, s, N, n, A, ldA, W, nrm2, dx, flags, st, skip, resid,
+                         ctx->wait_ns, ctx->withhold);
+  if (L == 2)
+    return launch_p<DD>(ctx->sm_count, s, N, n, A, ldA, W, nrm2, dx, flags, st, skip, resid,
+                        ctx->wait_ns, ctx->withhold);
+  return launch_p<QD>(ctx->sm_count, s, N, n, A, ldA, W, nrm2, dx, flags, st, skip, resid,
+                      ctx->wait_ns, ctx->withhold);
 }
 
 // Times the variants of a shape once per context on a scratch matrix and

@@ -93,12 +93,13 @@ __device__ typename P::real bcast_real(const typename P::real &a, int src) {
 
 // Grid barrier: block arrivals counted in st->bar_count; waits for `target`.
 // Returns false when the wait gave up (timeout flag set).
-__device__ bool tile_barrier(PathState *st, unsigned target, unsigned long long limit_ns) {
+__device__ bool tile_barrier(PathState *st, unsigned target, unsigned long long limit_ns,
+                             bool arrive = true) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
-    atomicAdd(&st->bar_count, 1u);
+    if (arrive) atomicAdd(&st->bar_count, 1u);
     volatile unsigned *cnt = &st->bar_count;
     volatile int *tmo = &st->timeout;
     int ok = 1;
@@ -132,7 +133,7 @@ __global__ void __launch_bounds__(kTT, 1)
 k_mgs_tile(int N, int n, int R, double *__restrict__ A, long ldA,
            double *__restrict__ W, double *__restrict__ nrm2, double *__restrict__ part,
            double *__restrict__ dx, PathState *st, const int *__restrict__ skip,
-           double *__restrict__ resid, unsigned long long limit_ns) {
+           double *__restrict__ resid, unsigned long long limit_ns, int withhold) {
   if (skip && *skip) return;
   typedef typename P::real real;
   typedef Part<P> PO;
@@ -165,7 +166,8 @@ k_mgs_tile(int N, int n, int R, double *__restrict__ A, long ldA,
     const double *Ppar = part + (long)(k & 1) * PP;       // partials against pivot k
     double *Pnext = part + (long)((k + 1) & 1) * PP;      // partials against pivot k+1
     if (k >= 0) {
-      if (!tile_barrier(st, (unsigned)G * (unsigned)(k + 1), limit_ns)) return;
+      if (!tile_barrier(st, (unsigned)G * (unsigned)(k + 1), limit_ns, !(b == 0 && k == withhold)))
+        return;
       if (bad) continue;
       if (tid == 0) sh_bad = 0;
       // 2. ||a_k||^2 (warp 0) and a_k^H a_{k+1} (warp 1), summed over the R row blocks
@@ -399,7 +401,8 @@ size_t tile_smem(int N, int n, int R) {
 template <class P>
 cudaError_t launch_tile(int G, int R, cudaStream_t stream, int N, int n, double *A, long ldA,
                         double *W, double *nrm2, double *part, double *dx, PathState *st,
-                        const int *skip, double *resid, unsigned long long limit_ns) {
+                        const int *skip, double *resid, unsigned long long limit_ns,
+                        int withhold) {
   const size_t smem = tile_smem<P>(N, n, R);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_mgs_tile<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -407,7 +410,7 @@ cudaError_t launch_tile(int G, int R, cudaStream_t stream, int N, int n, double 
     if (e != cudaSuccess) return e;
   }
   void *args[] = {&N, &n, &R, &A, &ldA, &W, &nrm2, &part, &dx, &st, (void *)&skip,
-                  &resid, &limit_ns};
+                  &resid, &limit_ns, &withhold};
   return cudaLaunchCooperativeKernel((const void *)k_mgs_tile<P>, dim3(G), dim3(kTT), args, smem,
                                      stream);
 }
@@ -431,12 +434,15 @@ long ph_mgs_tile_part(int L, int n, int R) { return 2L * 2 * L * (long)R * (n + 
 cudaError_t ph_mgs_tile_launch(int sm_count, cudaStream_t stream, int L, int N, int n, int R,
                                double *A, long ldA, double *W, double *nrm2, double *part,
                                double *dx, PathState *st, const int *skip, double *resid,
-                               unsigned long long limit_ns) {
+                               unsigned long long limit_ns, int withhold) {
   const int G = ph_mgs_tile_grid(sm_count, L, N, n, R);
   if (G < 1) return cudaErrorInvalidValue;
   if (L == 1)
-    return launch_tile<F64>(G, R, stream, N, n, A, ldA, W, nrm2, part, dx, st, skip, resid, limit_ns);
+    return launch_tile<F64>(G, R, stream, N, n, A, ldA, W, nrm2, part, dx, st, skip, resid, limit_ns,
+                            withhold);
   if (L == 2)
-    return launch_tile<DD>(G, R, stream, N, n, A, ldA, W, nrm2, part, dx, st, skip, resid, limit_ns);
-  return launch_tile<QD>(G, R, stream, N, n, A, ldA, W, nrm2, part, dx, st, skip, resid, limit_ns);
+    return launch_tile<DD>(G, R, stream, N, n, A, ldA, W, nrm2, part, dx, st, skip, resid, limit_ns,
+                           withhold);
+  return launch_tile<QD>(G, R, stream, N, n, A, ldA, W, nrm2, part, dx, st, skip, resid, limit_ns,
+                         withhold);
 }

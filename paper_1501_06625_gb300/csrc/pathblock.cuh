@@ -20,7 +20,7 @@ namespace ph {
 constexpr int kBT = 256;          // threads per block: 8 warps, 2 per SM sub-partition
 constexpr int kNW = kBT / 32;
 constexpr int kHistB = 16;        // accepted points kept for the predictor
-constexpr int kSG = 4;            // lanes per output in the summation
+constexpr int kSG = 4;            // lanes per output in the summation, until tuned
 
 struct Job {
   int L, N, n, Mf, Mpf, maxvf, Mg, Mpg, maxvg, emax, nout;
@@ -36,6 +36,7 @@ struct Job {
   ph_path_stats *stats;           // one record (may be null)
   ph_step_record *log;            // log_cap records (may be null)
   int log_cap;
+  int sum_lanes;                  // lanes per output of the summation: 1, 2, 4, ..., 32
   double *ws;                     // this job's workspace
   long o_x, o_dx, o_hist, o_ptab, o_spow, o_A, o_W, o_fslots, o_gslots, o_scal, o_t, o_g, o_h;
   long ldA, nsf, nsg;
@@ -86,6 +87,37 @@ __device__ typename P::real warp_sum_part(typename Part<P>::acc a) {
 #pragma unroll
   for (int m = 16; m > 0; m >>= 1) a = Part<P>::combine(a, Part<P>::shfl(a, m));
   return Part<P>::value(a);
+}
+
+// The outputs [o0, o1) of the homotopy's values and Jacobian summed by the
+// block with G lanes per output (the paper's threads per sum, Section 3.3);
+// put(o, value) runs on each output's first lane.
+template <class P, int G, class Put>
+__device__ void block_sum_g(const Job &a, int o0, int o1, const double *fslots,
+                            const double *gslots, const double *spow, const double *scal,
+                            Put put) {
+  const int tid = threadIdx.x;
+  for (int ob = o0; ob < o1; ob += kBT / G) {
+    const int o = ob + tid / G, lane = tid % G;
+    const bool act = o < o1;
+    cx<P> val = sum_output<P, G>(act, o, lane, a.N, a.n, a.optrf, a.oslotf, fslots, a.nsf,
+                                 a.optrg, a.oslotg, gslots, a.nsg, spow, scal, 1,
+                                 a.p.fixed_rows ? a.zrows_g : nullptr);
+    if (act && lane == 0) put(o, val);
+  }
+}
+
+template <class P, class Put>
+__device__ void block_sum(const Job &a, int o0, int o1, const double *fslots,
+                          const double *gslots, const double *spow, const double *scal, Put put) {
+  switch (a.sum_lanes) {
+    case 1: block_sum_g<P, 1>(a, o0, o1, fslots, gslots, spow, scal, put); break;
+    case 2: block_sum_g<P, 2>(a, o0, o1, fslots, gslots, spow, scal, put); break;
+    case 8: block_sum_g<P, 8>(a, o0, o1, fslots, gslots, spow, scal, put); break;
+    case 16: block_sum_g<P, 16>(a, o0, o1, fslots, gslots, spow, scal, put); break;
+    case 32: block_sum_g<P, 32>(a, o0, o1, fslots, gslots, spow, scal, put); break;
+    default: block_sum_g<P, 4>(a, o0, o1, fslots, gslots, spow, scal, put); break;
+  }
 }
 
 // MGS of [J | -h] (A) and back substitution.  Returns PH_OK or PH_NONFINITE;
@@ -216,17 +248,10 @@ __device__ int lowprec_solve(const Job &a, const double *x, const double *tl, co
   for (int s = tid; s < a.Mg; s += kBT)
     ad_term<LP>(s, a.Mpg, a.nvg, a.vidxg, a.vexpg, a.coeff_g, ptab, n, a.maxvg, gslots, a.nsg);
   __syncthreads();
-  for (int o0 = 0; o0 < nN; o0 += kBT / kSG) {
-    const int o = o0 + tid / kSG, lane = tid % kSG;
-    const bool act = o < nN;
-    cx<LP> val = sum_output<LP, kSG>(act, o, lane, N, n, a.optrf, a.oslotf, fslots, a.nsf,
-                                     a.optrg, a.oslotg, gslots, a.nsg, spow, scal, 1,
-                                     a.p.fixed_rows ? a.zrows_g : nullptr);
-    if (act && lane == 0) {
-      const int j = o / N, i = o - j * N;
-      c_store<LP>(A + (long)j * a.ldA, Ap, i, val);
-    }
-  }
+  block_sum<LP>(a, 0, nN, fslots, gslots, spow, scal, [&](int o, const cx<LP> &val) {
+    const int j = o / N, i = o - j * N;
+    c_store<LP>(A + (long)j * a.ldA, Ap, i, val);
+  });
   __syncthreads();
   const int ms = block_mgs<LP>(N, n, a.ldA, A, W, dx, s_nrm, s_y, s_dxmax);
   if (tid == 0) {
@@ -399,24 +424,17 @@ __device__ void track_job(const Job &a, double *smem) {
           for (int s = tid; s < a.Mg; s += kBT)
             ad_term<P>(s, a.Mpg, a.nvg, a.vidxg, a.vexpg, a.coeff_g, ptab, n, a.maxvg, gslots, a.nsg);
           __syncthreads();
-          for (int o0 = 0; o0 < a.nout; o0 += kBT / kSG) {
-            const int o = o0 + tid / kSG, lane = tid % kSG;
-            const bool act = o < a.nout;
-            cx<P> val = sum_output<P, kSG>(act, o, lane, N, n, a.optrf, a.oslotf, fslots, a.nsf,
-                                           a.optrg, a.oslotg, gslots, a.nsg, spow, scal, 1,
-                                     a.p.fixed_rows ? a.zrows_g : nullptr);
-            if (act && lane == 0) {
-              if (o < n * N) {
-                const int j = o / N, i = o - j * N;
-                c_store<P>(A + (long)j * a.ldA, Ap, i, val);
-              } else {
-                const int i = o - n * N;
-                c_store<P>(A + (long)n * a.ldA, Ap, i, c_neg<P>(val));
-                double mg = c_mag_lead<P>(val);
-                if (!(mg <= mymax)) mymax = mg;
-              }
+          block_sum<P>(a, 0, a.nout, fslots, gslots, spow, scal, [&](int o, const cx<P> &val) {
+            if (o < n * N) {
+              const int j = o / N, i = o - j * N;
+              c_store<P>(A + (long)j * a.ldA, Ap, i, val);
+            } else {
+              const int i = o - n * N;
+              c_store<P>(A + (long)n * a.ldA, Ap, i, c_neg<P>(val));
+              double mg = c_mag_lead<P>(val);
+              if (!(mg <= mymax)) mymax = mg;
             }
-          }
+          });
         } else {
           // the residual alone in working precision; the leading limbs of -h to hl
           for (int s = tid; s < a.Mf; s += kBT)
@@ -426,19 +444,14 @@ __device__ void track_job(const Job &a, double *smem) {
             val_term<P>(s, a.Mpg, a.nvg, a.vidxg, a.vexpg, a.coeff_g, ptab, n, a.emax, a.maxvg,
                         gslots, a.nsg);
           __syncthreads();
-          for (int o0 = 0; o0 < N; o0 += kBT / kSG) {
-            const int i = o0 + tid / kSG, lane = tid % kSG;
-            const bool act = i < N;
-            cx<P> val = sum_output<P, kSG>(act, n * N + i, lane, N, n, a.optrf, a.oslotf, fslots,
-                                           a.nsf, a.optrg, a.oslotg, gslots, a.nsg, spow, scal, 1,
-                                     a.p.fixed_rows ? a.zrows_g : nullptr);
-            if (act && lane == 0) {
-              hl[i] = -P::lead(val.re);
-              hl[a.ldA + i] = -P::lead(val.im);
-              double mg = c_mag_lead<P>(val);
-              if (!(mg <= mymax)) mymax = mg;
-            }
-          }
+          block_sum<P>(a, n * N, n * N + N, fslots, gslots, spow, scal,
+                       [&](int o, const cx<P> &val) {
+            const int i = o - n * N;
+            hl[i] = -P::lead(val.re);
+            hl[a.ldA + i] = -P::lead(val.im);
+            double mg = c_mag_lead<P>(val);
+            if (!(mg <= mymax)) mymax = mg;
+          });
         }
         atomicMax(&s_resbits, (unsigned long long)__double_as_longlong(mymax));
         __syncthreads();

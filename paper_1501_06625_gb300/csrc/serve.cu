@@ -45,6 +45,10 @@
 using namespace ph;
 
 long ph_lda(int N);
+ph_status ph_track_path_exec(ph_ctx *ctx, const ph_system *f, const ph_system *g,
+                             const double *gamma, const double *x0,
+                             const ph_track_params *params, double *x_out,
+                             ph_path_stats *stats, ph_step_record *log, int log_cap);
 void ph_job_fill_system(Job &j, const ph_system *f, const ph_system *g);
 long ph_job_ws_doubles(const Job &j);
 
@@ -227,6 +231,10 @@ struct JobRec {
   clk::time_point t_submit, t_done;
   std::vector<double> x_out;
   ph_path_stats stats;
+  // the large-job route: the homotopy, run by the single-path tracker
+  bool big = false;
+  const ph_system *f = nullptr, *g = nullptr;
+  ph_track_params p;
 };
 
 }  // namespace
@@ -259,6 +267,10 @@ struct ph_server {
   std::vector<int64_t> slot_job;   // slot -> job id
   unsigned long long published = 0;
   long long launches = 0;
+  // the large-job route: a context and stream of the server's own
+  ph_ctx *big_ctx = nullptr;
+  cudaStream_t big_stream = nullptr;
+  long long big_done = 0;
 };
 
 static void server_loop(ph_server *s);
@@ -266,6 +278,7 @@ static void server_loop(ph_server *s);
 static void admit_locked(ph_server *s) {
   while (!s->waiting.empty() && !s->free_slots.empty()) {
     JobRec &r = s->jobs[s->waiting.front()];
+    if (r.big) break;                             // the GPU is drained for it first
     size_t off;
     if (!s->palloc.alloc(r.bytes, &off)) break;   // the oldest waiting job does not fit yet
     const int64_t id = s->waiting.front();
@@ -327,11 +340,42 @@ static void reap_locked(ph_server *s) {
   }
 }
 
+// The large job at the head of the arrival order, once no small job is on the
+// device and the persistent kernel has closed: tracked by the single-path
+// tracker on the whole GPU (the lock is released meanwhile).
+static bool run_big_locked(ph_server *s, std::unique_lock<std::mutex> &lk) {
+  if (s->waiting.empty()) return false;
+  const int64_t id = s->waiting.front();
+  JobRec &r = s->jobs[id];
+  if (!r.big) return false;
+  for (int64_t sj : s->slot_job)
+    if (sj != 0) return false;
+  if (s->launched && cudaStreamQuery(s->stream) == cudaErrorNotReady) return false;
+  cudaGetLastError();
+  s->waiting.pop_front();
+  r.state = 1;
+  std::vector<double> xo(r.x0.size());
+  ph_path_stats st;
+  memset(&st, 0, sizeof st);
+  lk.unlock();
+  ph_status status = ph_track_path_exec(s->big_ctx, r.f, r.g, r.gamma.data(), r.x0.data(), &r.p,
+                                        xo.data(), &st, nullptr, 0);
+  lk.lock();
+  if (status != PH_OK && st.status == PH_OK) st.status = status;
+  r.x_out = std::move(xo);
+  r.stats = st;
+  r.t_done = clk::now();
+  r.state = 2;
+  s->big_done += 1;
+  return true;
+}
+
 static void server_loop(ph_server *s) {
   cudaSetDevice(s->ctx->device);
   std::unique_lock<std::mutex> lk(s->mu);
   while (!s->stop) {
     reap_locked(s);
+    if (run_big_locked(s, lk)) continue;
     admit_locked(s);
     // a kernel is needed while a published job is unclaimed
     bool pending = false;
@@ -387,6 +431,11 @@ extern "C" ph_status ph_server_create(ph_ctx *ctx, const ph_server_config *cfg, 
   if (e == cudaSuccess) e = s->pool.ensure((size_t)cfg->pool_bytes);
   if (e == cudaSuccess) e = s->ctl.ensure(sizeof(Ctl));
   if (e == cudaSuccess) e = cudaMemset(s->ctl.p, 0, sizeof(Ctl));
+  if (e == cudaSuccess && cfg->big_n > 0) {
+    e = cudaStreamCreateWithFlags(&s->big_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess && ph_init(&s->big_ctx, ctx->device, s->big_stream) != PH_OK)
+      e = cudaErrorInitializationError;
+  }
   if (e != cudaSuccess) {
     ph_status st = ph_cuda_fail(ctx, e, "ph_server_create");
     ph_server_destroy(s);
@@ -411,7 +460,11 @@ extern "C" ph_status ph_server_submit(ph_server *s, const ph_system *f, const ph
     return ph_fail(ctx, PH_EINVAL, "ph_server_submit: invalid argument");
   if (g && (g->ctx != ctx || g->L != f->L || g->N != f->N || g->n != f->n))
     return ph_fail(ctx, PH_EINVAL, "ph_server_submit: g does not match f");
-  if (f->n > s->cfg.max_n) return ph_fail(ctx, PH_EINVAL, "ph_server_submit: more variables than max_n");
+  const bool big = s->cfg.big_n > 0 && f->n > s->cfg.big_n;
+  if (!big && f->n > s->cfg.max_n)
+    return ph_fail(ctx, PH_EINVAL, "ph_server_submit: more variables than max_n");
+  if (big && params->lin_prec != 0 && params->lin_prec != 1)
+    return ph_fail(ctx, PH_EINVAL, "ph_server_submit: a large job takes lin_prec 0 or 1");
   const ph_track_params &p = *params;
   if (p.max_newton < 1 || p.max_newton > 64 || p.pred_order < 0 || p.pred_order > 8 ||
       p.relax_k < 1 || p.relax_k > 64 || p.max_steps < 0 || p.lin_prec < 0 || p.lin_prec > 3 ||
@@ -429,7 +482,11 @@ extern "C" ph_status ph_server_submit(ph_server *s, const ph_system *f, const ph
   ph_job_fill_system(r.job, f, g);
   r.job.p = p;
   r.bytes = sizeof(double) * (size_t)ph_job_ws_doubles(r.job);
-  if (r.bytes > (size_t)s->cfg.pool_bytes)
+  r.big = big;
+  r.f = f;
+  r.g = g;
+  r.p = p;
+  if (!big && r.bytes > (size_t)s->cfg.pool_bytes)
     return ph_fail(ctx, PH_ENOMEM, "ph_server_submit: the job's workspace exceeds the pool");
   const int L = f->L;
   r.x0.resize((size_t)2 * L * f->n);
@@ -534,6 +591,8 @@ extern "C" ph_status ph_server_destroy(ph_server *s) {
     cudaStreamSynchronize(s->stream);
     cudaStreamDestroy(s->stream);
   }
+  if (s->big_ctx) ph_destroy(s->big_ctx);
+  if (s->big_stream) cudaStreamDestroy(s->big_stream);
   if (s->slots) cudaFreeHost(s->slots);
   if (s->queue) cudaFreeHost(s->queue);
   if (s->q) cudaFreeHost(s->q);

@@ -536,13 +536,17 @@ static ph_status build_graph(ph_ctx *ctx, TrackCache *c, const ph_system *f, con
   return PH_OK;
 }
 
-extern "C" ph_status ph_track_path(ph_ctx *ctx, const ph_system *f, const ph_system *g,
-                                   const double *gamma, const double *x0,
-                                   const ph_track_params *params, double *x_out,
-                                   ph_path_stats *stats, ph_step_record *log, int log_cap) {
+// ph_track_path on an executing context `ctx` that may differ from the
+// context the systems were loaded in, as long as both are on the same device
+// (the serving loop runs its large jobs on a context of its own).
+ph_status ph_track_path_exec(ph_ctx *ctx, const ph_system *f, const ph_system *g,
+                             const double *gamma, const double *x0,
+                             const ph_track_params *params, double *x_out,
+                             ph_path_stats *stats, ph_step_record *log, int log_cap) {
   if (!ctx) return PH_EINVAL;
-  if (!f || f->ctx != ctx) return ph_fail(ctx, PH_EINVAL, "ph_track_path: f missing or from another context");
-  if (g && (g->ctx != ctx || g->L != f->L || g->N != f->N || g->n != f->n))
+  if (!f || !f->ctx || f->ctx->device != ctx->device)
+    return ph_fail(ctx, PH_EINVAL, "ph_track_path: f missing or from another device");
+  if (g && (g->ctx != f->ctx || g->L != f->L || g->N != f->N || g->n != f->n))
     return ph_fail(ctx, PH_EINVAL, "ph_track_path: g does not match f");
   if (!gamma || !x0 || !params || !x_out) return ph_fail(ctx, PH_EINVAL, "ph_track_path: NULL argument");
   const ph_track_params p = *params;
@@ -677,6 +681,16 @@ extern "C" ph_status ph_track_path(ph_ctx *ctx, const ph_system *f, const ph_sys
   }
   if (status == PH_TIMEOUT) return ph_fail(ctx, PH_TIMEOUT, "ph_track_path: a grid barrier timed out");
   return status;
+}
+
+extern "C" ph_status ph_track_path(ph_ctx *ctx, const ph_system *f, const ph_system *g,
+                                   const double *gamma, const double *x0,
+                                   const ph_track_params *params, double *x_out,
+                                   ph_path_stats *stats, ph_step_record *log, int log_cap) {
+  if (!ctx) return PH_EINVAL;
+  if (!f || f->ctx != ctx) return ph_fail(ctx, PH_EINVAL, "ph_track_path: f missing or from another context");
+  if (g && g->ctx != ctx) return ph_fail(ctx, PH_EINVAL, "ph_track_path: g does not match f");
+  return ph_track_path_exec(ctx, f, g, gamma, x0, params, x_out, stats, log, log_cap);
 }
 
 // ---- measurement support ----------------------------------------------------------

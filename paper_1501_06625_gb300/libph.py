@@ -50,7 +50,7 @@ class StepRecord(C.Structure):
 
 class ServerConfig(C.Structure):
     _fields_ = [("max_n", C.c_int32), ("max_blocks", C.c_int32), ("pool_bytes", C.c_int64),
-                ("queue_cap", C.c_int32), ("reserved", C.c_int32)]
+                ("queue_cap", C.c_int32), ("big_n", C.c_int32)]
 
 
 class CtrlState(C.Structure):
@@ -64,7 +64,8 @@ EXPORTS = ["ph_init", "ph_destroy", "ph_last_error", "ph_system_load", "ph_syste
            "ph_mgs_solve_static", "ph_track_paths", "ph_server_create", "ph_server_submit",
            "ph_server_poll", "ph_server_wait", "ph_server_info", "ph_server_destroy",
            "ph_server_job_bytes", "ph_mgs_variant", "ph_sum_lanes", "ph_ctrl_linear_contraction",
-           "ph_mgs_set_variant"]
+           "ph_mgs_set_variant", "ph_set_wait_limit", "ph_set_memory_limit",
+           "ph_debug_withhold_pivot", "ph_block_lanes", "ph_set_block_lanes"]
 
 
 class PhError(RuntimeError):
@@ -106,6 +107,11 @@ def lib():
             L.ph_ctrl_linear_contraction.restype = C.c_int
             L.ph_version.restype = C.c_char_p
             L.ph_profile_newton.argtypes = [vp, vp, vp, vp, C.c_int, vp, vp, C.c_int, dp]
+            L.ph_set_wait_limit.argtypes = [vp, C.c_double]
+            L.ph_block_lanes.argtypes = [vp, vp, C.POINTER(C.c_int), dp]
+            L.ph_set_block_lanes.argtypes = [vp, vp, C.c_int]
+            L.ph_set_memory_limit.argtypes = [C.c_int64, C.POINTER(C.c_int64)]
+            L.ph_debug_withhold_pivot.argtypes = [vp, C.c_int]
             L.ph_mgs_set_variant.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]
             L.ph_mgs_variant.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int),
                                          C.POINTER(C.c_int), dp]
@@ -256,8 +262,8 @@ def ph_track_paths(ctx, f, g, gamma, x0, params: dict, x_out, log_cap: int = 0):
 
 
 def ph_server_create(ctx, max_n: int, pool_bytes: int, queue_cap: int = 1024,
-                     max_blocks: int = 0):
-    cfg = ServerConfig(max_n, max_blocks, pool_bytes, queue_cap, 0)
+                     max_blocks: int = 0, big_n: int = 0):
+    cfg = ServerConfig(max_n, max_blocks, pool_bytes, queue_cap, big_n)
     h = C.c_void_p()
     _check(ctx, lib().ph_server_create(ctx, C.byref(cfg), C.byref(h)))
     return h
@@ -349,6 +355,35 @@ def ph_mgs_variant(ctx, prec: int, N: int, n: int):
 def ph_mgs_set_variant(ctx, prec: int, N: int, n: int, kind: int, size: int = 0):
     """Pins the solve variant of a shape (kind -1: back to the timed choice)."""
     return _check(ctx, lib().ph_mgs_set_variant(ctx, prec, N, n, kind, size))
+
+
+def ph_block_lanes(ctx, f):
+    """(lanes per output of the per-block summation, ms of 1..32 lanes or -1)."""
+    lanes = C.c_int(0)
+    ms = (C.c_double * 6)()
+    _check(ctx, lib().ph_block_lanes(ctx, f, C.byref(lanes), ms))
+    return lanes.value, list(ms)
+
+
+def ph_set_block_lanes(ctx, f, lanes: int):
+    return _check(ctx, lib().ph_set_block_lanes(ctx, f, lanes))
+
+
+def ph_set_wait_limit(ctx, ms: float):
+    return _check(ctx, lib().ph_set_wait_limit(ctx, ms))
+
+
+def ph_set_memory_limit(nbytes: int) -> int:
+    """Caps the library's device memory (0: no cap); returns the bytes held now."""
+    used = C.c_int64(0)
+    st = lib().ph_set_memory_limit(nbytes, C.byref(used))
+    if st != PH_OK:
+        raise PhError(st, "ph_set_memory_limit failed")
+    return used.value
+
+
+def ph_debug_withhold_pivot(ctx, k: int):
+    return _check(ctx, lib().ph_debug_withhold_pivot(ctx, k))
 
 
 def ph_sum_lanes(ctx, f, g=None):

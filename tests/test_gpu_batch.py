@@ -116,3 +116,41 @@ def test_batch_work_queue_and_nonfinite(ctx):
     single = np.zeros_like(x0[400])
     libph.ph_track_path(ctx.h, f, None, wl.gamma_soa(), x0[400], params, single)
     assert cabs_diff(xo[400], single).max() <= TOL_END[L]
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16, 32])
+def test_each_summation_lane_count_matches_the_oracle(ctx, lanes):
+    """The per-block summation with 1 .. 32 lanes per output (pinned): the
+    fixed schedule of the dense8 system ends where the oracle's does."""
+    wl = synth.dense8(1, "dd")
+    L = wl.L
+    f = ctx.load(wl.f, L)
+    libph.ph_set_block_lanes(ctx.h, f, lanes)
+    assert libph.ph_block_lanes(ctx.h, f)[0] == lanes
+    x0 = start_points(wl.f, L, 2)
+    xo = np.zeros_like(x0)
+    stats, _ = libph.ph_track_paths(ctx.h, f, None, wl.gamma_soa(), x0, wl.params, xo)
+    so, xr, _, _ = oracle.track(oracle.System(wl.f, L), x0[0], wl.gamma_soa(), wl.params)
+    assert stats[0]["status"] == libph.PH_OK and so == oracle.OK
+    assert cabs_diff(xo[0], xr).max() <= TOL_END[L] * max(1.0, np.abs(lead_complex(xr)).max())
+    ctx.free(f)
+
+
+def test_summation_lanes_are_timed_on_a_full_batch(ctx):
+    """A batch with at least as many paths as SMs times every lane count once
+    and keeps the fastest; a smaller batch leaves the choice alone."""
+    wl = synth.dense8(3, "dd")
+    L = wl.L
+    f = ctx.load(wl.f, L)
+    params = dict(wl.params, fixed_steps=2)
+    x0 = start_points(wl.f, L, 4)
+    libph.ph_track_paths(ctx.h, f, None, wl.gamma_soa(), x0, params, np.zeros_like(x0))
+    lanes, ms = libph.ph_block_lanes(ctx.h, f)
+    assert lanes == 4 and all(m == -1 for m in ms)
+    x0 = start_points(wl.f, L, 304)
+    libph.ph_track_paths(ctx.h, f, None, wl.gamma_soa(), x0, params, np.zeros_like(x0))
+    lanes, ms = libph.ph_block_lanes(ctx.h, f)
+    assert all(m > 0 for m in ms)
+    assert ms[[1, 2, 4, 8, 16, 32].index(lanes)] == min(ms)
+    print(f"dense8 DD per-block summation: {lanes} lanes; ms by lanes {ms}")
+    ctx.free(f)

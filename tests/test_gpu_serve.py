@@ -129,3 +129,37 @@ def test_rejects_oversized_job(ctx):
         assert ei.value.status == libph.PH_EINVAL
     finally:
         libph.ph_server_destroy(srv)
+
+
+def test_large_job_route_alone_and_in_the_mix(ctx):
+    """A job above big_n (here a sparse n = 280 quad-double system, which one
+    block would take minutes per solve for) runs alone on the whole GPU by the
+    single-path tracker: the same bits alone and submitted in the middle of a
+    stream of small jobs, which all finish; and the same end point as
+    ph_track_path on the caller's context within the end-point tolerance (the
+    two contexts may time their way to different solver variants)."""
+    srv = libph.ph_server_create(ctx.h, max_n=32, pool_bytes=1 << 30, queue_cap=128, big_n=64)
+    try:
+        big = make_job(ctx, 21, 280, "qd", dense=False, steps=3)
+        xa, sa, _ = run_alone(ctx, srv, big)
+        assert sa["steps"] == 3 and sa["status"] in (libph.PH_OK, libph.PH_MAXSTEPS)
+        mix = [make_job(ctx, 500 + i, 8 + (i * 5) % 24, "qd" if i % 4 == 0 else "dd",
+                        dense=(i % 2 == 0), steps=10) for i in range(24)]
+        ids = []
+        for i, jb in enumerate(mix):
+            ids.append(libph.ph_server_submit(ctx.h, srv, jb["f"], None, jb["gam"], jb["x0"],
+                                              jb["params"]))
+            if i == 11:
+                pb = libph.ph_server_submit(ctx.h, srv, big["f"], None, big["gam"], big["x0"],
+                                            big["params"])
+        for jid, jb in zip(ids, mix):
+            st, _ = libph.ph_server_wait(ctx.h, srv, jid, 300000, np.zeros_like(jb["x0"]))
+            assert st["steps"] >= 1
+        xb = np.zeros_like(big["x0"])
+        sb, _ = libph.ph_server_wait(ctx.h, srv, pb, 300000, xb)
+        assert np.array_equal(xb, xa) and sb["steps"] == sa["steps"]
+        xr = np.zeros_like(big["x0"])
+        libph.ph_track_path(ctx.h, big["f"], None, big["gam"], big["x0"], big["params"], xr)
+        assert cabs_diff(xr, xa).max() <= TOL_END[4] * max(1.0, np.abs(lead_complex(xa)).max())
+    finally:
+        libph.ph_server_destroy(srv)
