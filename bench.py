@@ -815,24 +815,33 @@ def whole_path_leg(libph, synth, ctx, torch, dev, seed, npaths_dd, nsingle, qd_p
             loaded.append((wl, xs, f, G))
         base = dict(synth.default_params(L), max_steps=4000, tol_path=1e-8,
                     max_newton=3 if L == 2 else 5)
-        # backward paths: start roots (untimed)
+        # backward paths: start roots (untimed); many DD paths through the
+        # serving loop, a few QD paths one by one on the whole GPU
         t0 = time.perf_counter()
-        srv = libph.ph_server_create(ctx.h, max_n=64, pool_bytes=8 << 30, queue_cap=1024)
         starts = []
-        try:
-            ids = []
+
+        def start_of(wl, xl):
+            return _soa(synth.nearest_start_root(wl.f, xl[0, 0] + 1j * xl[0, 1]), L)
+
+        if count > 16:
+            srv = libph.ph_server_create(ctx.h, max_n=64, pool_bytes=8 << 30, queue_cap=1024)
+            try:
+                ids = []
+                for wl, xs, f, G in loaded:
+                    gb = _soa([1.0 / wl.gamma], L).reshape(L, 2)
+                    ids.append(libph.ph_server_submit(ctx.h, srv, G, f, gb, _soa(xs, L), base))
+                for (wl, xs, f, G), jid in zip(loaded, ids):
+                    xl = np.zeros((L, 2, 64))
+                    st, _ = libph.ph_server_wait(ctx.h, srv, jid, 600000, x_out=xl)
+                    starts.append(start_of(wl, xl) if st["status"] == libph.PH_OK else None)
+            finally:
+                libph.ph_server_destroy(srv)
+        else:
             for wl, xs, f, G in loaded:
-                gi = 1.0 / wl.gamma
-                gb = _soa([gi], L).reshape(L, 2)
-                ids.append(libph.ph_server_submit(ctx.h, srv, G, f, gb, _soa(xs, L), base))
-            for (wl, xs, f, G), jid in zip(loaded, ids):
+                gb = _soa([1.0 / wl.gamma], L).reshape(L, 2)
                 xl = np.zeros((L, 2, 64))
-                st, _ = libph.ph_server_wait(ctx.h, srv, jid, 600000, x_out=xl)
-                ok = st["status"] == libph.PH_OK
-                starts.append(_soa(synth.nearest_start_root(wl.f, xl[0, 0] + 1j * xl[0, 1]), L)
-                              if ok else None)
-        finally:
-            libph.ph_server_destroy(srv)
+                st, _, _ = libph.ph_track_path(ctx.h, G, f, gb, _soa(xs, L), base, xl)
+                starts.append(start_of(wl, xl) if st == libph.PH_OK else None)
         prep_s = time.perf_counter() - t0
         idx = [i for i, s0 in enumerate(starts) if s0 is not None]
         row = {"systems": count, "start_roots_found": len(idx), "generation_s": gen_s,
@@ -911,16 +920,17 @@ def whole_path_leg(libph, synth, ctx, torch, dev, seed, npaths_dd, nsingle, qd_p
 
 def sparse512_leg(libph, synth, ctx, torch, dev, seed, steps):
     """The very sparse n = 512 system in QD, total-degree homotopy
-    from the all-ones root, adaptive steps: the first `steps` predictor-corrector
-    steps through ph_track_path (the MGS solve of the 512 x 512 Jacobian
-    dominates), CUDA events, and one corrector iteration's kernels."""
+    from the all-ones root, adaptive steps (5 Newton iterations, path
+    tolerance 1e-8, QD at t = 1): the first `steps` predictor-corrector steps
+    through ph_track_path (the MGS solve of the 512 x 512 Jacobian dominates),
+    CUDA events."""
     stream = torch.cuda.current_stream(dev)
     wl = synth.sparse512(seed, "qd")
     f = ctx.load(wl.f, wl.L)
     x0 = torch.tensor(wl.x0_soa(), device=dev)
     gam = torch.tensor(wl.gamma_soa(), device=dev)
     xo = torch.empty_like(x0)
-    params = dict(wl.params, max_steps=steps - 1)
+    params = dict(wl.params, max_steps=steps - 1, max_newton=5, tol_path=1e-8)
     libph.ph_track_path(ctx.h, f, None, gam, x0, dict(params, max_steps=0), xo)   # graph, tuning
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -940,11 +950,13 @@ def sparse512_leg(libph, synth, ctx, torch, dev, seed, steps):
                             "ms_grid_cluster_tiled": vms}}
 
 
-def hard_precision_leg(libph, synth, ctx, torch, dev, seed, steps):
+def hard_precision_leg(libph, synth, ctx, torch, dev, seed, steps, decades=8.0, max_dt=1e-6):
     """The planted n = 128 workload where it is hard: precision128's shape with the coefficient
-    moduli spread over 12 decades between the equations (each polynomial's
-    terms share a modulus 10^{12 u_i}), so the Jacobian's rows differ in scale
-    by up to 1e12 (condition number about 2e13 at the planted root, in numpy).
+    moduli spread over `decades` decades between the equations (each
+    polynomial's terms share a modulus 10^{decades u_i}), so the Jacobian's
+    rows differ in scale by up to 10^decades (condition number about 2.5e9 at
+    the planted root for 8 decades, 1.9e13 for 12, in numpy; with 12 no step
+    of either form converges from x*).
     The path is tracked backwards from x* (start system f, target the
     total-degree system, gamma' = 1/gamma), where the Jacobian is the
     ill-conditioned J_f: the first `steps` steps, single path, plain (lin_prec
@@ -954,7 +966,7 @@ def hard_precision_leg(libph, synth, ctx, torch, dev, seed, steps):
     stream = torch.cuda.current_stream(dev)
     out = {}
     for prec in ("dd", "qd"):
-        wl, xs = synth.precision128_equations(seed, prec)
+        wl, xs = synth.precision128_equations(seed, prec, decades)
         L = wl.L
         f = ctx.load(wl.f, L)
         G = ctx.load(synth.total_degree_start(wl.f), L)
@@ -962,10 +974,12 @@ def hard_precision_leg(libph, synth, ctx, torch, dev, seed, steps):
         gb = torch.tensor(_soa([gi], L).reshape(L, 2), device=dev)
         x0 = torch.tensor(_soa(xs, L), device=dev)
         mn = 5 if L == 2 else 6
-        row = {"steps": steps, "max_newton": mn, "max_dt": 1e-3}
+        row = {"steps": steps, "max_newton": mn, "max_dt": max_dt, "decades": decades,
+               "cond_at_planted_root_numpy": {8.0: 2.5e9, 12.0: 1.9e13}.get(decades)}
         ref = None
         for lin in (0, 1):
-            params = dict(wl.params, max_steps=steps - 1, max_dt=1e-3, max_newton=mn, lin_prec=lin)
+            params = dict(wl.params, max_steps=steps - 1, max_dt=max_dt, max_newton=mn,
+                          lin_prec=lin)
             xo = torch.empty_like(x0)
             libph.ph_track_path(ctx.h, G, f, gb, x0, dict(params, max_steps=0), xo)
             e0 = torch.cuda.Event(enable_timing=True)
@@ -992,7 +1006,8 @@ def hard_precision_leg(libph, synth, ctx, torch, dev, seed, steps):
             row[f"single_lin{lin}"] = r
         bx = torch.tensor(np.repeat(_soa(xs, L)[None], 152, axis=0), device=dev)
         for lin in (0, 1, 3):
-            params = dict(wl.params, max_steps=steps - 1, max_dt=1e-3, max_newton=mn, lin_prec=lin)
+            params = dict(wl.params, max_steps=steps - 1, max_dt=max_dt, max_newton=mn,
+                          lin_prec=lin)
             bo = torch.empty_like(bx)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -1145,9 +1160,9 @@ def main():
                     help="of these, how many the single-path form tracks one by one")
     ap.add_argument("--whole-paths-qd", type=int, default=3,
                     help="planted dense64 QD paths tracked whole by the single-path form")
-    ap.add_argument("--sparse-steps", type=int, default=8,
+    ap.add_argument("--sparse-steps", type=int, default=16,
                     help="predictor-corrector steps of the sparse n = 512 QD path (0 skips)")
-    ap.add_argument("--hard-steps", type=int, default=6,
+    ap.add_argument("--hard-steps", type=int, default=30,
                     help="steps of the ill-conditioned precision128 segment (0 skips)")
     ap.add_argument("--only-mgs", default=None, metavar="L,N,n,reps",
                     help="only time least-squares solves of one shape (for kernel profiles)")
@@ -1194,6 +1209,7 @@ def main():
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     build.build()
+    legs = {}                                      # wall seconds of each leg
     stream = torch.cuda.current_stream(dev)
     ctx = libph.Context(local, stream=stream)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -1270,13 +1286,17 @@ def main():
 
     serve = serve_mixed = None
     if args.serve_requests > 0 and rank == 0:
+        _t0 = time.perf_counter()
         serve = serve_leg(libph, synth, ctx, args.serve_requests, args.seed)
         serve_mixed = serve_leg(libph, synth, ctx, args.serve_requests, args.seed, lin=3,
                                 seq_rate=serve["sequential_single_path"]["paths_per_s"])
+        legs['serving'] = time.perf_counter() - _t0
 
     cyclic = monodromy = None
     if not args.no_cyclic and rank == 0:
+        _t0 = time.perf_counter()
         cyclic = cyclic_leg(libph, synth, ctx, torch, dev, peak)
+        legs['cyclic'] = time.perf_counter() - _t0
     if args.monodromy and rank == 0:
         monodromy = monodromy_leg(libph, synth, ctx, torch, dev, args.seed,
                                   args.monodromy_segment)
@@ -1289,18 +1309,26 @@ def main():
     whole = sparse = hard = None
     if rank == 0 and world == 1:
         if args.whole_paths > 0 or args.whole_paths_qd > 0:
+            _t0 = time.perf_counter()
             whole = whole_path_leg(libph, synth, ctx, torch, dev, args.seed, args.whole_paths,
                                    args.whole_paths_single, args.whole_paths_qd)
+            legs['whole_paths'] = time.perf_counter() - _t0
         if args.sparse_steps > 0:
+            _t0 = time.perf_counter()
             sparse = sparse512_leg(libph, synth, ctx, torch, dev, args.seed, args.sparse_steps)
+            legs['sparse512'] = time.perf_counter() - _t0
         if args.hard_steps > 0:
+            _t0 = time.perf_counter()
             hard = hard_precision_leg(libph, synth, ctx, torch, dev, args.seed, args.hard_steps)
+            legs['precision_ill_conditioned'] = time.perf_counter() - _t0
 
     precision = None
     if args.precision_paths > 0 and rank == 0:
+        _t0 = time.perf_counter()
         precision = precision_leg(libph, synth, ctx, torch, dev, flush, args.seed,
                                   args.precision_paths)
         precision.update(precision_path_leg(libph, synth, ctx, torch, dev, flush, args.seed))
+        legs['precision'] = time.perf_counter() - _t0
 
     # end to end through the same call with host buffers
     e2e_v, h2d, d2h = e2e_leg(libph, ctx, f, wl, max(2, args.steps // 2), torch)
@@ -1371,7 +1399,7 @@ def main():
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": s["launches"], "roofline": roof, "roofline_sparse512_mgs": roof512,
             "cpu_baseline": cpu,
-            "clocks": clk, "wall_s_timed": wall,
+            "clocks": clk, "wall_s_timed": wall, "leg_seconds": legs,
         }
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -442,6 +442,14 @@ ph_status ph_mgs_solve_static(int device, void *cuda_stream, ph_prec prec, int N
  * PH_TIMEOUT; k < 0 restores normal operation.  Nothing faults and nothing
  * waits beyond the wait limit. */
 ph_status ph_set_wait_limit(ph_ctx *ctx, double ms);
+
+/* Test support for the solvers' reductions: the exact sum over one warp of 32
+ * double-double (limbs 2) or quad-double (limbs 4) values in[32][limbs] (host
+ * array), rounded back to limbs doubles in out[limbs] (host array): the
+ * fixed-point integer reduction the MGS kernels use for their dot products
+ * and norms (each input truncated below 2^-116 (DD) / 2^-244 (QD) of the
+ * largest; the total correctly rounded limb by limb). */
+ph_status ph_debug_warp_sum(int device, int limbs, const double *in, double *out);
 ph_status ph_set_memory_limit(int64_t bytes, int64_t *in_use);
 ph_status ph_debug_withhold_pivot(ph_ctx *ctx, int k);
 

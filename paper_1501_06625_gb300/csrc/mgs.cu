@@ -37,6 +37,9 @@
 // Every wait is bounded (2 s of %globaltimer); a wait that runs out sets
 // PathState::timeout and the blocks return, so the host gets PH_TIMEOUT and the
 // context stays usable.
+#include <type_traits>
+
+#include "exsum.cuh"
 #include "internal.h"
 #include "mp.cuh"
 #include "pathdev.cuh"
@@ -96,8 +99,16 @@ __device__ void publish(int *flag, int tag) {
 template <class P>
 __device__ typename P::real part_total(typename Part<P>::acc a, typename Part<P>::acc *sh) {
   typedef Part<P> PO;
+  if constexpr (std::is_same<P, DD>::value) {      // an exact integer sum over the warp
+    const dd v = warp_exact_sum(PO::value(a));
+    a.s = v.h;
+    a.c = v.l;
+  } else if constexpr (std::is_same<P, QD>::value) {
+    a.v = warp_exact_sum(a.v);
+  } else {
 #pragma unroll
-  for (int m = 16; m > 0; m >>= 1) a = PO::combine(a, PO::shfl(a, m));
+    for (int m = 16; m > 0; m >>= 1) a = PO::combine(a, PO::shfl(a, m));
+  }
   const int w = threadIdx.x >> 5;
   if ((threadIdx.x & 31) == 0) sh[w] = a;
   __syncthreads();
@@ -642,5 +653,36 @@ extern "C" ph_status ph_mgs_set_variant(ph_ctx *ctx, ph_prec prec, int N, int n,
   }
   // a captured path graph holds the previous choice: rebuild it on next use
   ph_track_release(ctx);
+  return PH_OK;
+}
+
+namespace {
+template <class P>
+__global__ void k_warp_sum(const double *in, double *out) {
+  typename P::real v;
+#pragma unroll
+  for (int l = 0; l < P::L; ++l) P::set_limb(v, l, in[threadIdx.x * P::L + l]);
+  v = warp_exact_sum(v);
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int l = 0; l < P::L; ++l) out[l] = P::limb(v, l);
+}
+}  // namespace
+
+extern "C" ph_status ph_debug_warp_sum(int device, int limbs, const double *in, double *out) {
+  if ((limbs != 2 && limbs != 4) || !in || !out) return PH_EINVAL;
+  if (cudaSetDevice(device) != cudaSuccess) { cudaGetLastError(); return PH_ECUDA; }
+  double *d = nullptr;
+  const size_t nin = 32 * (size_t)limbs;
+  if (cudaMalloc(&d, sizeof(double) * (nin + 4)) != cudaSuccess) { cudaGetLastError(); return PH_ENOMEM; }
+  cudaError_t e = cudaMemcpy(d, in, sizeof(double) * nin, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    if (limbs == 2) k_warp_sum<DD><<<1, 32>>>(d, d + nin);
+    else k_warp_sum<QD><<<1, 32>>>(d, d + nin);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(out, d + nin, sizeof(double) * limbs, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) { cudaGetLastError(); return PH_ECUDA; }
   return PH_OK;
 }

@@ -10,7 +10,10 @@
 // dealt round-robin to the 8 warps, the pivot norms in shared memory, and a
 // block barrier per column step.
 #pragma once
+#include <type_traits>
+
 #include "ctrl.h"
+#include "exsum.cuh"
 #include "internal.h"
 #include "mp.cuh"
 #include "pathdev.cuh"
@@ -82,11 +85,19 @@ PHD void rp_store(double *v, long plane, int part, long i, const typename P::rea
   r_store<P>(v + part * plane, 2 * plane, i, z);
 }
 
+// the sum over the warp: exact integer sums for double-double and
+// quad-double (exsum.cuh), a shuffle tree for one-limb types
 template <class P>
 __device__ typename P::real warp_sum_part(typename Part<P>::acc a) {
+  if constexpr (std::is_same<P, DD>::value) {
+    return warp_exact_sum(Part<DD>::value(a));
+  } else if constexpr (std::is_same<P, QD>::value) {
+    return warp_exact_sum(a.v);
+  } else {
 #pragma unroll
-  for (int m = 16; m > 0; m >>= 1) a = Part<P>::combine(a, Part<P>::shfl(a, m));
-  return Part<P>::value(a);
+    for (int m = 16; m > 0; m >>= 1) a = Part<P>::combine(a, Part<P>::shfl(a, m));
+    return Part<P>::value(a);
+  }
 }
 
 // The outputs [o0, o1) of the homotopy's values and Jacobian summed by the

@@ -65,7 +65,8 @@ EXPORTS = ["ph_init", "ph_destroy", "ph_last_error", "ph_system_load", "ph_syste
            "ph_server_poll", "ph_server_wait", "ph_server_info", "ph_server_destroy",
            "ph_server_job_bytes", "ph_mgs_variant", "ph_sum_lanes", "ph_ctrl_linear_contraction",
            "ph_mgs_set_variant", "ph_set_wait_limit", "ph_set_memory_limit",
-           "ph_debug_withhold_pivot", "ph_block_lanes", "ph_set_block_lanes"]
+           "ph_debug_withhold_pivot", "ph_block_lanes", "ph_set_block_lanes",
+           "ph_debug_warp_sum"]
 
 
 class PhError(RuntimeError):
@@ -108,6 +109,7 @@ def lib():
             L.ph_version.restype = C.c_char_p
             L.ph_profile_newton.argtypes = [vp, vp, vp, vp, C.c_int, vp, vp, C.c_int, dp]
             L.ph_set_wait_limit.argtypes = [vp, C.c_double]
+            L.ph_debug_warp_sum.argtypes = [C.c_int, C.c_int, dp, dp]
             L.ph_block_lanes.argtypes = [vp, vp, C.POINTER(C.c_int), dp]
             L.ph_set_block_lanes.argtypes = [vp, vp, C.c_int]
             L.ph_set_memory_limit.argtypes = [C.c_int64, C.POINTER(C.c_int64)]
@@ -367,6 +369,18 @@ def ph_block_lanes(ctx, f):
 
 def ph_set_block_lanes(ctx, f, lanes: int):
     return _check(ctx, lib().ph_set_block_lanes(ctx, f, lanes))
+
+
+def ph_debug_warp_sum(device: int, values):
+    """The exact warp sum of 32 multi-limb values [32][limbs] (test support)."""
+    v = np.ascontiguousarray(values, dtype=np.float64)
+    limbs = v.shape[1]
+    out = np.zeros(limbs)
+    st = lib().ph_debug_warp_sum(device, limbs, v.ctypes.data_as(C.POINTER(C.c_double)),
+                                 out.ctypes.data_as(C.POINTER(C.c_double)))
+    if st != PH_OK:
+        raise PhError(st, "ph_debug_warp_sum failed")
+    return out
 
 
 def ph_set_wait_limit(ctx, ms: float):
