@@ -1217,6 +1217,9 @@ def main():
     wl = synth.dense64(args.seed + rank, args.prec)
     f = ctx.load(wl.f, wl.L)
     peak = libph.ph_fp64_peak(ctx.h, 50.0)            # G lane-ops/s, measured now
+    rates = libph.ph_unit_rates(ctx.h)
+    unit_rates = {"fp64_fma_pipe_g_per_s": rates[0], "fp64_fma_tensor_core_g_per_s": rates[1],
+                  "int32_mad_g_per_s": rates[2]}
 
     # timed region: barrier + synchronize on both sides, max over ranks
     track_leg(libph, ctx, f, wl, dev, 0, args.warmup, torch, flush)
@@ -1399,7 +1402,7 @@ def main():
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": s["launches"], "roofline": roof, "roofline_sparse512_mgs": roof512,
             "cpu_baseline": cpu,
-            "clocks": clk, "wall_s_timed": wall, "leg_seconds": legs,
+            "clocks": clk, "wall_s_timed": wall, "leg_seconds": legs, "unit_rates": unit_rates,
         }
         print(json.dumps(line), flush=True)
     ctx.close()

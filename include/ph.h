@@ -395,6 +395,15 @@ ph_status ph_profile_newton(ph_ctx *ctx, const ph_system *f, const ph_system *g,
                             int reps, double *ms_out);
 ph_status ph_fp64_peak(ph_ctx *ctx, double ms_target, double *gops);
 
+/* The execution-unit rates the kernels' design rests on, measured on the
+ * context's device in G operations per second: rates[0] FP64 fused
+ * multiply-adds on the FP64 pipe (as ph_fp64_peak), rates[1] FP64 fused
+ * multiply-adds on the tensor cores (mma.sync m8n8k4 .f64: 256 per warp
+ * instruction), rates[2] 32-bit integer multiply-adds.  The tensor-core rate
+ * below the FP64 pipe's is why no MGS update runs on the tensor cores; the
+ * integer rate is what the exact integer reductions of the solvers use. */
+ph_status ph_unit_rates(ph_ctx *ctx, double *rates);
+
 /* A least-squares solve like ph_mgs_solve for callers that must not allocate
  * device memory: processes whose device memory belongs to another allocator
  * (a framework's caching allocator or a fixed arena, where one more

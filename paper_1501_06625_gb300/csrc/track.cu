@@ -813,3 +813,75 @@ extern "C" ph_status ph_fp64_peak(ph_ctx *ctx, double ms_target, double *gops) {
   *gops = (double)blocks * threads * iters * 8.0 / (ms * 1e-3) / 1e9;
   return PH_OK;
 }
+
+// ---- the unit rates that shape the design ------------------------------------------
+
+namespace {
+// four independent FP64 tensor-core MMAs (m8n8k4, 256 FMAs each per warp) per iteration
+__global__ void k_dmma_rate(double *out, int iters) {
+  const double a = 1.0 + threadIdx.x * 1e-9, b = 1.0 - threadIdx.x * 1e-9;
+  double c0[2] = {0, 0}, c1[2] = {0, 0}, c2[2] = {0, 0}, c3[2] = {0, 0};
+  for (int i = 0; i < iters; ++i) {
+    asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
+                 : "+d"(c0[0]), "+d"(c0[1]) : "d"(a), "d"(b));
+    asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
+                 : "+d"(c1[0]), "+d"(c1[1]) : "d"(a), "d"(b));
+    asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
+                 : "+d"(c2[0]), "+d"(c2[1]) : "d"(a), "d"(b));
+    asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
+                 : "+d"(c3[0]), "+d"(c3[1]) : "d"(a), "d"(b));
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = c0[0] + c0[1] + c1[0] + c1[1] + c2[0] + c2[1] +
+                                               c3[0] + c3[1];
+}
+
+// eight independent 32-bit integer multiply-adds per iteration
+__global__ void k_imad_rate(double *out, int iters) {
+  unsigned a = 3u + threadIdx.x, b = 7u ^ threadIdx.x;
+  unsigned c[8] = {0, 1, 2, 3, 4, 5, 6, 7};
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) c[q] = c[q] * a + b;
+  }
+  unsigned s = 0;
+  for (int q = 0; q < 8; ++q) s += c[q];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = (double)s;
+}
+}  // namespace
+
+extern "C" ph_status ph_unit_rates(ph_ctx *ctx, double *rates) {
+  if (!ctx || !rates) return PH_EINVAL;
+  cudaSetDevice(ctx->device);
+  double dfma = 0.0;
+  ph_status s = ph_fp64_peak(ctx, 20.0, &dfma);
+  if (s != PH_OK) return s;
+  const int blocks = ctx->sm_count * 4, threads = 128;
+  PH_CUDA(ctx, ctx->ystage.ensure(sizeof(double) * blocks * 256));
+  double *out = ctx->ystage.as<double>();
+  cudaEvent_t e0, e1;
+  PH_CUDA(ctx, cudaEventCreate(&e0));
+  PH_CUDA(ctx, cudaEventCreate(&e1));
+  float ms_mma = 0.f, ms_imad = 0.f;
+  const int it_mma = 4096, it_imad = 8192;
+  k_dmma_rate<<<blocks, threads, 0, ctx->stream>>>(out, 16);
+  cudaEventRecord(e0, ctx->stream);
+  k_dmma_rate<<<blocks, threads, 0, ctx->stream>>>(out, it_mma);
+  cudaEventRecord(e1, ctx->stream);
+  cudaError_t e = cudaEventSynchronize(e1);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms_mma, e0, e1);
+  if (e == cudaSuccess) {
+    k_imad_rate<<<blocks, 256, 0, ctx->stream>>>(out, 16);
+    cudaEventRecord(e0, ctx->stream);
+    k_imad_rate<<<blocks, 256, 0, ctx->stream>>>(out, it_imad);
+    cudaEventRecord(e1, ctx->stream);
+    e = cudaEventSynchronize(e1);
+  }
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms_imad, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return ph_cuda_fail(ctx, e, "ph_unit_rates");
+  rates[0] = dfma;
+  rates[1] = (double)blocks * (threads / 32) * it_mma * 4 * 256 / (ms_mma * 1e-3) / 1e9;
+  rates[2] = (double)blocks * 256 * it_imad * 8 / (ms_imad * 1e-3) / 1e9;
+  return PH_OK;
+}

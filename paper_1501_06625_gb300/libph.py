@@ -66,7 +66,7 @@ EXPORTS = ["ph_init", "ph_destroy", "ph_last_error", "ph_system_load", "ph_syste
            "ph_server_job_bytes", "ph_mgs_variant", "ph_sum_lanes", "ph_ctrl_linear_contraction",
            "ph_mgs_set_variant", "ph_set_wait_limit", "ph_set_memory_limit",
            "ph_debug_withhold_pivot", "ph_block_lanes", "ph_set_block_lanes",
-           "ph_debug_warp_sum"]
+           "ph_debug_warp_sum", "ph_unit_rates"]
 
 
 class PhError(RuntimeError):
@@ -110,6 +110,7 @@ def lib():
             L.ph_profile_newton.argtypes = [vp, vp, vp, vp, C.c_int, vp, vp, C.c_int, dp]
             L.ph_set_wait_limit.argtypes = [vp, C.c_double]
             L.ph_debug_warp_sum.argtypes = [C.c_int, C.c_int, dp, dp]
+            L.ph_unit_rates.argtypes = [vp, dp]
             L.ph_block_lanes.argtypes = [vp, vp, C.POINTER(C.c_int), dp]
             L.ph_set_block_lanes.argtypes = [vp, vp, C.c_int]
             L.ph_set_memory_limit.argtypes = [C.c_int64, C.POINTER(C.c_int64)]
@@ -369,6 +370,13 @@ def ph_block_lanes(ctx, f):
 
 def ph_set_block_lanes(ctx, f, lanes: int):
     return _check(ctx, lib().ph_set_block_lanes(ctx, f, lanes))
+
+
+def ph_unit_rates(ctx):
+    """G ops/s of FP64 FMA (pipe), FP64 FMA (tensor cores), 32-bit integer multiply-add."""
+    r = (C.c_double * 3)()
+    _check(ctx, lib().ph_unit_rates(ctx, r))
+    return list(r)
 
 
 def ph_debug_warp_sum(device: int, values):
