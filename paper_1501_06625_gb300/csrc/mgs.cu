@@ -49,8 +49,7 @@ using namespace ph;
 namespace {
 
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // default of the context setting
-constexpr int kThreads = 128;
-constexpr int kRowCache = 4;        // pivot rows a lane keeps in registers (N <= 256)
+constexpr int kRowCache = 4;        // pivot rows a lane keeps in registers (N <= 128 WP)
 constexpr int kDowndateBits = 20;   // cancellation beyond which a norm is recomputed
 
 PHD unsigned long long global_timer_ns() {
@@ -94,9 +93,9 @@ __device__ void publish(int *flag, int tag) {
   }
 }
 
-// Sum of the block's four warps by part: warps {0,1} -> part 0, {2,3} -> part 1.
-// Returns this warp's part total (normalised) to every lane.
-template <class P>
+// Sum over the block's warps of one part: warps [0, WP) carry part 0, [WP, 2 WP)
+// part 1.  Returns this warp's part total (normalised) to every lane.
+template <class P, int WP>
 __device__ typename P::real part_total(typename Part<P>::acc a, typename Part<P>::acc *sh) {
   typedef Part<P> PO;
   if constexpr (std::is_same<P, DD>::value) {      // an exact integer sum over the warp
@@ -109,22 +108,24 @@ __device__ typename P::real part_total(typename Part<P>::acc a, typename Part<P>
 #pragma unroll
     for (int m = 16; m > 0; m >>= 1) a = PO::combine(a, PO::shfl(a, m));
   }
-  const int w = threadIdx.x >> 5;
+  const int w = threadIdx.x >> 5, w0 = w - w % WP;
   if ((threadIdx.x & 31) == 0) sh[w] = a;
   __syncthreads();
-  typename PO::acc t = PO::combine(sh[w & 2], sh[(w & 2) + 1]);
+  typename PO::acc t = sh[w0];
+#pragma unroll
+  for (int q = 1; q < WP; ++q) t = PO::combine(t, sh[w0 + q]);
   __syncthreads();
   return PO::value(t);
 }
 
 // Exchange a part value between the two halves of the block: warps of part q
 // receive the value the warps of part 1-q computed.
-template <class P>
+template <class P, int WP>
 __device__ typename P::real swap_parts(const typename P::real &mine, typename P::real *sh) {
   const int w = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0 && (w & 1) == 0) sh[w >> 1] = mine;
+  if ((threadIdx.x & 31) == 0 && w % WP == 0) sh[w / WP] = mine;
   __syncthreads();
-  typename P::real other = sh[1 - (w >> 1)];
+  typename P::real other = sh[1 - w / WP];
   __syncthreads();
   return other;
 }
@@ -152,20 +153,20 @@ PHD void store_part(double *col, long Ap, int part, long i, const typename P::re
 }
 
 // ||a_j||^2 of a column (after its last update by this block)
-template <class P>
+template <class P, int WP>
 __device__ typename P::real col_norm2(const double *col, long Ap, int N, int part, int r0,
                                       typename Part<P>::acc *sh, typename P::real *shr) {
   typename Part<P>::acc a = Part<P>::zero();
-  for (int i = r0; i < N; i += 64) Part<P>::sq(a, load_part<P>(col, Ap, part, i));
-  typename P::real mine = part_total<P>(a, sh);
-  typename P::real other = swap_parts<P>(mine, shr);
+  for (int i = r0; i < N; i += 32 * WP) Part<P>::sq(a, load_part<P>(col, Ap, part, i));
+  typename P::real mine = part_total<P, WP>(a, sh);
+  typename P::real other = swap_parts<P, WP>(mine, shr);
   return P::add(mine, other);
 }
 
 // W: alpha_kj at W[(2l+c) Wp + j nc + k] (column j of the alphas);
 // nrm2: [L][nc] ||a_j||^2, then [L][nc] 1/||a_j||^2; ready: [nc] pivot flags.
-template <class P>
-__global__ void __launch_bounds__(kThreads) k_mgs(int N, int n, double *__restrict__ A, long ldA,
+template <class P, int WP>
+__global__ void __launch_bounds__(64 * WP) k_mgs(int N, int n, double *__restrict__ A, long ldA,
                                                   double *__restrict__ W, double *__restrict__ nrm2,
                                                   double *__restrict__ dx, int *__restrict__ ready,
                                                   PathState *st, const int *__restrict__ skip,
@@ -174,7 +175,7 @@ __global__ void __launch_bounds__(kThreads) k_mgs(int N, int n, double *__restri
   if (skip && *skip) return;
   typedef typename P::real real;
   typedef Part<P> PO;
-  __shared__ typename PO::acc sh_acc[4];
+  __shared__ typename PO::acc sh_acc[2 * WP];
   __shared__ real sh_r[2];
   __shared__ int sh_rec;
   extern __shared__ double s_y[];                // back substitution: [L][2][n]
@@ -183,14 +184,15 @@ __global__ void __launch_bounds__(kThreads) k_mgs(int N, int n, double *__restri
   double *ninv = nrm2 + (long)P::L * nc;
   const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
   const int w = tid >> 5, lane = tid & 31;
-  const int part = w >> 1;                       // 0 = real, 1 = imaginary
-  const int r0 = (w & 1) * 32 + lane;            // rows r0, r0 + 64, ...
+  const int part = w / WP;                       // 0 = real, 1 = imaginary
+  constexpr int RS = 32 * WP;                    // row stride of a lane
+  const int r0 = (w % WP) * 32 + lane;           // rows r0, r0 + RS, ...
   const int tag = st->mgs_epoch + 1;
   const int last_own = b + ((n - b) / G) * G;    // largest column this block owns
 
   // the norms of this block's columns; column 0 first, published at once
   for (int j = b; j <= n; j += G) {
-    real s = col_norm2<P>(A + (long)j * ldA, Ap, N, part, r0, sh_acc, sh_r);
+    real s = col_norm2<P, WP>(A + (long)j * ldA, Ap, N, part, r0, sh_acc, sh_r);
     if (tid == 0) {
       r_store<P>(nrm2, nc, j, s);
       if (j == 0) r_store<P>(ninv, nc, 0, P::recip(s));
@@ -212,7 +214,7 @@ __global__ void __launch_bounds__(kThreads) k_mgs(int N, int n, double *__restri
     real ck_r[kRowCache], ck_i[kRowCache];
 #pragma unroll
     for (int q = 0; q < kRowCache; ++q) {
-      const int i = r0 + 64 * q;
+      const int i = r0 + RS * q;
       if (i < N) {
         ck_r[q] = load_part_cg<P>(ak, Ap, 0, i);
         ck_i[q] = load_part_cg<P>(ak, Ap, 1, i);
@@ -234,22 +236,22 @@ __global__ void __launch_bounds__(kThreads) k_mgs(int N, int n, double *__restri
       typename PO::acc a = PO::zero();
 #pragma unroll
       for (int q = 0; q < kRowCache; ++q) {
-        const int i = r0 + 64 * q;
+        const int i = r0 + RS * q;
         if (i < N) {
           real ajr = load_part<P>(aj, Ap, 0, i), aji = load_part<P>(aj, Ap, 1, i);
           if (part == 0) PO::dot2(a, ck_r[q], ajr, ck_i[q], aji, 1.0);
           else PO::dot2(a, ck_r[q], aji, ck_i[q], ajr, -1.0);
         }
       }
-      for (int i = r0 + 64 * kRowCache; i < N; i += 64) {
+      for (int i = r0 + RS * kRowCache; i < N; i += RS) {
         real akr = load_part_cg<P>(ak, Ap, 0, i), aki = load_part_cg<P>(ak, Ap, 1, i);
         real ajr = load_part<P>(aj, Ap, 0, i), aji = load_part<P>(aj, Ap, 1, i);
         if (part == 0) PO::dot2(a, akr, ajr, aki, aji, 1.0);
         else PO::dot2(a, akr, aji, aki, ajr, -1.0);
       }
-      real d = part_total<P>(a, sh_acc);
+      real d = part_total<P, WP>(a, sh_acc);
       real al = P::mul(d, inv2);                  // this part of alpha_kj
-      real al_o = swap_parts<P>(al, sh_r);        // the other part
+      real al_o = swap_parts<P, WP>(al, sh_r);        // the other part
       const real alr = part == 0 ? al : al_o, ali = part == 0 ? al_o : al;
       if (tid == 0) {
 #pragma unroll
@@ -272,12 +274,12 @@ __global__ void __launch_bounds__(kThreads) k_mgs(int N, int n, double *__restri
       // one fresh sum per column, and a fresh sum has no cancellation).
       const bool crit = j == k + 1;
       const bool fresh = N > 64 * kRowCache;
-      const bool split = crit && !fresh;
+      const bool split = crit && !fresh && WP == 2;
       if (!(split && w == 0)) {
         // a_j -= alpha a_k:  re: ajr - alr akr + ali aki;  im: aji - alr aki - ali akr
 #pragma unroll
         for (int q = 0; q < kRowCache; ++q) {
-          const int i = r0 + 64 * q;
+          const int i = r0 + RS * q;
           if (i < N) {
             if (part == 0)
               store_part<P>(aj, Ap, 0, i,
@@ -287,7 +289,7 @@ __global__ void __launch_bounds__(kThreads) k_mgs(int N, int n, double *__restri
                             PO::upd(load_part<P>(aj, Ap, 1, i), alr, ck_i[q], ali, ck_r[q], -1.0));
           }
         }
-        for (int i = r0 + 64 * kRowCache; i < N; i += 64) {
+        for (int i = r0 + RS * kRowCache; i < N; i += RS) {
           real akr = load_part_cg<P>(ak, Ap, 0, i), aki = load_part_cg<P>(ak, Ap, 1, i);
           if (part == 0)
             store_part<P>(aj, Ap, 0, i, PO::upd(load_part<P>(aj, Ap, 0, i), alr, akr, ali, aki, 1.0));
@@ -308,7 +310,7 @@ __global__ void __launch_bounds__(kThreads) k_mgs(int N, int n, double *__restri
       if (fresh) {
         if (crit) {                                // the same branch in every thread
           __syncthreads();
-          const real s = col_norm2<P>(aj, Ap, N, part, r0, sh_acc, sh_r);
+          const real s = col_norm2<P, WP>(aj, Ap, N, part, r0, sh_acc, sh_r);
           if (tid == 0) {
             r_store<P>(nrm2, nc, j, s);
             r_store<P>(ninv, nc, j, P::recip(s));
@@ -328,7 +330,7 @@ __global__ void __launch_bounds__(kThreads) k_mgs(int N, int n, double *__restri
         }
         __syncthreads();
         if (sh_rec) {                              // the same value in every thread
-          const real s = col_norm2<P>(aj, Ap, N, part, r0, sh_acc, sh_r);
+          const real s = col_norm2<P, WP>(aj, Ap, N, part, r0, sh_acc, sh_r);
           if (tid == 0) {
             r_store<P>(nrm2, nc, j, s);
             if (j == k + 1) r_store<P>(ninv, nc, j, P::recip(s));
@@ -370,13 +372,13 @@ __global__ void __launch_bounds__(kThreads) k_mgs(int N, int n, double *__restri
   if (tid == 0 && resid) *resid = __dsqrt_rn(P::lead(r_load_cg<P>(nrm2, nc, n)));
   // back substitution on y = alpha_{., n}:  dx_k = y_k;  y_i -= alpha_ik dx_k (i < k)
   const double *yc = W + (long)n * nc;
-  for (int i = tid; i < n; i += kThreads) c_store<P>(s_y, n, i, c_load_cg<P>(yc, Wp, i));
+  for (int i = tid; i < n; i += 64 * WP) c_store<P>(s_y, n, i, c_load_cg<P>(yc, Wp, i));
   __syncthreads();
   for (int k = n - 1; k >= 1; --k) {
     const real xr = load_part<P>(s_y, n, 0, k), xi = load_part<P>(s_y, n, 1, k);
     const double *Wk = W + (long)k * nc;
     // warps of part 0 update the real parts of rows i < k, part 1 the imaginary
-    for (int i = (w & 1) * 32 + lane; i < k; i += 64) {
+    for (int i = r0; i < k; i += RS) {
       real wr = load_part_cg<P>(Wk, Wp, 0, i), wi = load_part_cg<P>(Wk, Wp, 1, i);
       if (part == 0) store_part<P>(s_y, n, 0, i, PO::upd(load_part<P>(s_y, n, 0, i), wr, xr, wi, xi, 1.0));
       else store_part<P>(s_y, n, 1, i, PO::upd(load_part<P>(s_y, n, 1, i), wr, xi, wi, xr, -1.0));
@@ -384,7 +386,7 @@ __global__ void __launch_bounds__(kThreads) k_mgs(int N, int n, double *__restri
     __syncthreads();
   }
   double m = 0.0;
-  for (int i = tid; i < n; i += kThreads) {
+  for (int i = tid; i < n; i += 64 * WP) {
     cx<P> v = c_load<P>(s_y, n, i);
     c_store<P>(dx, n, i, v);
     double a = c_mag_lead<P>(v);
@@ -393,15 +395,14 @@ __global__ void __launch_bounds__(kThreads) k_mgs(int N, int n, double *__restri
   atomicMax(&st->dx_bits, (unsigned long long)__double_as_longlong(m));
 }
 
-template <class P>
-cudaError_t launch_p(int sm_count, cudaStream_t stream, int N, int n, double *A, long ldA,
-                     double *W, double *nrm2, double *dx, int *ready, PathState *st,
-                     const int *skip, double *resid, unsigned long long limit_ns = kWaitLimitNs,
-                     int withhold = -1) {
+template <class P, int WP>
+cudaError_t launch_wp(int sm_count, cudaStream_t stream, int N, int n, double *A, long ldA,
+                      double *W, double *nrm2, double *dx, int *ready, PathState *st,
+                      const int *skip, double *resid, unsigned long long limit_ns, int withhold) {
   const size_t smem = sizeof(double) * 2 * P::L * (size_t)n;
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_mgs<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_mgs<P, WP>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
   int grid = n + 1 < sm_count ? n + 1 : sm_count;
@@ -409,8 +410,23 @@ cudaError_t launch_p(int sm_count, cudaStream_t stream, int N, int n, double *A,
   // cooperative launch: the driver guarantees that all blocks are resident
   void *args[] = {&N, &n, &A, &ldA, &W, &nrm2, &dx, &ready, &st, (void *)&skip, &resid,
                   &limit_ns, &withhold};
-  return cudaLaunchCooperativeKernel((const void *)k_mgs<P>, dim3(grid), dim3(kThreads), args,
+  return cudaLaunchCooperativeKernel((const void *)k_mgs<P, WP>, dim3(grid), dim3(64 * WP), args,
                                      smem, stream);
+}
+
+// Two warps per part (128 threads) up to 256 rows; tall matrices take four
+// (256 threads): the same FP64 work per SM, half the chain of instructions
+// per warp on the pivot's critical path.
+template <class P>
+cudaError_t launch_p(int sm_count, cudaStream_t stream, int N, int n, double *A, long ldA,
+                     double *W, double *nrm2, double *dx, int *ready, PathState *st,
+                     const int *skip, double *resid, unsigned long long limit_ns = kWaitLimitNs,
+                     int withhold = -1) {
+  if (N > 64 * kRowCache)
+    return launch_wp<P, 4>(sm_count, stream, N, n, A, ldA, W, nrm2, dx, ready, st, skip, resid,
+                           limit_ns, withhold);
+  return launch_wp<P, 2>(sm_count, stream, N, n, A, ldA, W, nrm2, dx, ready, st, skip, resid,
+                         limit_ns, withhold);
 }
 
 }  // namespace

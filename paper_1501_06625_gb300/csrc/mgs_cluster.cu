@@ -26,6 +26,10 @@
 // named barriers, so no barrier can wait forever.
 #include <cooperative_groups.h>
 
+#include <type_traits>
+
+#include "exsum.cuh"
+
 #include "internal.h"
 #include "mp.cuh"
 #include "pathdev.cuh"
@@ -58,24 +62,35 @@ __device__ __forceinline__ void pair_sync(int pair) {
   asm volatile("bar.sync %0, 64;" ::"r"(pair + 1) : "memory");
 }
 
+// the sum over the warp: exact integer sums for double-double and
+// quad-double (exsum.cuh), a shuffle tree for one-limb types
 template <class P>
 __device__ typename P::real warp_total(typename Part<P>::acc a) {
+  if constexpr (std::is_same<P, DD>::value || std::is_same<P, QD>::value) {
+    return warp_exact_sum(Part<P>::value(a));
+  } else {
 #pragma unroll
-  for (int m = 16; m > 0; m >>= 1) a = Part<P>::combine(a, Part<P>::shfl(a, m));
-  return Part<P>::value(a);
+    for (int m = 16; m > 0; m >>= 1) a = Part<P>::combine(a, Part<P>::shfl(a, m));
+    return Part<P>::value(a);
+  }
 }
 
-// two sums at once (independent chains, interleaved)
+// two sums at once (independent chains, interleaved for one-limb types)
 template <class P>
 __device__ void warp_total2(typename Part<P>::acc a, typename Part<P>::acc b,
                             typename P::real &ra, typename P::real &rb) {
+  if constexpr (std::is_same<P, DD>::value || std::is_same<P, QD>::value) {
+    ra = warp_exact_sum(Part<P>::value(a));
+    rb = warp_exact_sum(Part<P>::value(b));
+  } else {
 #pragma unroll
-  for (int m = 16; m > 0; m >>= 1) {
-    a = Part<P>::combine(a, Part<P>::shfl(a, m));
-    b = Part<P>::combine(b, Part<P>::shfl(b, m));
+    for (int m = 16; m > 0; m >>= 1) {
+      a = Part<P>::combine(a, Part<P>::shfl(a, m));
+      b = Part<P>::combine(b, Part<P>::shfl(b, m));
+    }
+    ra = Part<P>::value(a);
+    rb = Part<P>::value(b);
   }
-  ra = Part<P>::value(a);
-  rb = Part<P>::value(b);
 }
 
 // element (limb l, part c, row i) of a column block [2L][N]

@@ -1,18 +1,20 @@
 """Parity of the least-squares solve (ph_mgs_solve: modified Gram-Schmidt on
 [J | rhs] and back substitution; Introduction, and Section 2 for N >= n)
 against the oracle's textbook MGS, for each solver variant pinned through
-ph_mgs_set_variant, at sizes where every row loop of the kernels runs:
+ph_mgs_set_variant, at sizes where every branch of the kernels runs:
 
-* n = N = 288 (DD) and 260 (QD): beyond the 256 rows the grid kernel keeps in
-  registers, by the grid and the tiled kernel.  The oracle takes minutes there, so its solutions are stored
-  (tests/golden/make_mgs_golden.py writes them from the oracle alone) and the
-  inputs are regenerated from the seed;
+* n = N = 288 (DD) and 260 (QD): tall enough that the grid kernel works with
+  four warps per part and sums each pivot's norm afresh; by the grid, cluster
+  (where it fits) and tiled kernels.  The oracle takes minutes there, so its
+  solutions are stored (tests/golden/make_mgs_golden.py writes them from the
+  oracle alone) and the inputs are regenerated from the seed;
 * tall systems with N > 256 > n, and small square and tall shapes, by the
   grid, the cluster and the tiled kernel (one and several row blocks), in D,
   DD and QD, against the oracle live;
 * n = 1024, against an exact solution: integer-valued inputs scaled by
   powers of two, whose right-hand side is computed exactly, so the solve must
-  reproduce the planted dyadic solution to working precision.
+  reproduce the planted dyadic solution to working precision; by the grid
+  kernel (past the 512 rows it keeps in registers) and, in QD, the tiled one.
 
 The bound is the first-order forward error of a backward-stable least-squares
 solve, 2 n u (kappa + kappa^2 rho) (gpu_common.mgs_tol); each case also
@@ -154,14 +156,21 @@ def test_exact_solution_at_n_1024(ctx, L):
     J[0, 0], J[0, 1] = A.T.real, A.T.imag
     rhs = soa_from_complex(b, L)
     dx = np.zeros((L, 2, n))
-    if L == 4:                                        # spare the QD timing of every variant
-        libph.ph_mgs_set_variant(ctx.h, L, n, n, libph.MGS_TILED, 8)
-    libph.ph_mgs_solve(ctx.h, L, n, n, J, rhs, dx)
+    # the grid kernel (its loop over rows beyond the ones kept in registers
+    # runs past 512 rows), and in QD also the tiled one
+    variants = [(libph.MGS_GRID, 0)] + ([(libph.MGS_TILED, 8)] if L == 4 else [])
+    for kind, size in variants:
+        libph.ph_mgs_set_variant(ctx.h, L, n, n, kind, size)
+        libph.ph_mgs_solve(ctx.h, L, n, n, J, rhs, dx)
+        _check_exact(L, n, dx, xs, A, f"{libph.MGS_KINDS[kind]} {size}")
+
+
+def _check_exact(L, n, dx, xs, A, label):
     d = dx.copy()
     d[0] -= np.stack([xs.real, xs.imag])              # exact: x* is a double
     err = np.hypot(*d.sum(0)).max() / np.abs(xs).max()
     kappa = np.linalg.cond(A)
     bound = 2 * n * U[L] * kappa
-    print(f"L{L} n=1024 exact: error {err:.2e} ({err / (n * U[L] * kappa):.2e} n u kappa), "
-          f"kappa {kappa:.2f}")
+    print(f"L{L} n=1024 exact, {label}: error {err:.2e} ({err / (n * U[L] * kappa):.2e} "
+          f"n u kappa), kappa {kappa:.2f}")
     assert err <= bound, (err, bound)
