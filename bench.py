@@ -962,7 +962,7 @@ def hard_precision_leg(libph, synth, ctx, torch, dev, seed, steps, decades=8.0, 
     ill-conditioned J_f: the first `steps` steps, single path, plain (lin_prec
     0) against the precision form (lin_prec 1: Newton systems in double), the
     same tolerances; then copies of the path at once through ph_track_paths
-    (152 in DD, 32 in QD) with lin_prec 0, 1 and 3 for the FP32/FP64 split.""" 
+    (152 in DD, 32 in QD) with lin_prec 0, 1 and 3 for the FP32/FP64 split."""
     stream = torch.cuda.current_stream(dev)
     out = {}
     for prec in ("dd", "qd"):
