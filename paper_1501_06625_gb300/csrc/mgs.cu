@@ -414,17 +414,15 @@ cudaError_t launch_wp(int sm_count, cudaStream_t stream, int N, int n, double *A
                                      smem, stream);
 }
 
-// Two warps per part (128 threads) up to 256 rows; tall matrices take four
-// (256 threads): the same FP64 work per SM, half the chain of instructions
-// per warp on the pivot's critical path.
+// Two warps per part (128 threads).  (Four warps per part halve the chain of
+// instructions per warp on a pivot's critical path, but measured slower on
+// tall QD matrices -- 259 against 235 ms at 512 x 513 -- where each column's
+// reductions then combine four warps instead of two.)
 template <class P>
 cudaError_t launch_p(int sm_count, cudaStream_t stream, int N, int n, double *A, long ldA,
                      double *W, double *nrm2, double *dx, int *ready, PathState *st,
                      const int *skip, double *resid, unsigned long long limit_ns = kWaitLimitNs,
                      int withhold = -1) {
-  if (N > 64 * kRowCache)
-    return launch_wp<P, 4>(sm_count, stream, N, n, A, ldA, W, nrm2, dx, ready, st, skip, resid,
-                           limit_ns, withhold);
   return launch_wp<P, 2>(sm_count, stream, N, n, A, ldA, W, nrm2, dx, ready, st, skip, resid,
                          limit_ns, withhold);
 }

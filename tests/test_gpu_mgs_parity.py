@@ -3,9 +3,9 @@
 against the oracle's textbook MGS, for each solver variant pinned through
 ph_mgs_set_variant, at sizes where every branch of the kernels runs:
 
-* n = N = 288 (DD) and 260 (QD): tall enough that the grid kernel works with
-  four warps per part and sums each pivot's norm afresh; by the grid, cluster
-  (where it fits) and tiled kernels.  The oracle takes minutes there, so its
+* n = N = 288 (DD) and 260 (QD): beyond the 256 rows the grid kernel keeps in
+  registers, where it also sums each pivot's norm afresh instead of
+  downdating; by the grid, cluster (where it fits) and tiled kernels.  The oracle takes minutes there, so its
   solutions are stored (tests/golden/make_mgs_golden.py writes them from the
   oracle alone) and the inputs are regenerated from the seed;
 * tall systems with N > 256 > n, and small square and tall shapes, by the
@@ -14,7 +14,7 @@ ph_mgs_set_variant, at sizes where every branch of the kernels runs:
 * n = 1024, against an exact solution: integer-valued inputs scaled by
   powers of two, whose right-hand side is computed exactly, so the solve must
   reproduce the planted dyadic solution to working precision; by the grid
-  kernel (past the 512 rows it keeps in registers) and, in QD, the tiled one.
+  kernel and, in QD, the tiled one.
 
 The bound is the first-order forward error of a backward-stable least-squares
 solve, 2 n u (kappa + kappa^2 rho) (gpu_common.mgs_tol); each case also
@@ -156,8 +156,7 @@ def test_exact_solution_at_n_1024(ctx, L):
     J[0, 0], J[0, 1] = A.T.real, A.T.imag
     rhs = soa_from_complex(b, L)
     dx = np.zeros((L, 2, n))
-    # the grid kernel (its loop over rows beyond the ones kept in registers
-    # runs past 512 rows), and in QD also the tiled one
+    # the grid kernel, and in QD also the tiled one
     variants = [(libph.MGS_GRID, 0)] + ([(libph.MGS_TILED, 8)] if L == 4 else [])
     for kind, size in variants:
         libph.ph_mgs_set_variant(ctx.h, L, n, n, kind, size)
