@@ -244,7 +244,7 @@ CONTROL = {"control": 0}       # 1: host-side step control (for profiling runs)
 # DRAM bytes (read + write) of one k_mgs<DD> launch on the dense64 DD system,
 # from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # current kernel: the 64 x 65 matrix and the projection coefficients, read once.
-MGS_DENSE64_DD_TRAFFIC = 269568
+MGS_DENSE64_DD_TRAFFIC = 284160
 
 
 def seg_params(wl):
@@ -1279,7 +1279,14 @@ def main():
         bit = sum(x["newton_iters"] for x in bstats)
         bops = bit * (ad_ops(wl.f, wl.L) + sum_ops(wl.f, wl.L) + mgs_ops(wl.f.N, wl.n, wl.L))
         bach = bops / (bms * 1e-3) / 1e9
+        lanes, lane_ms = libph.ph_block_lanes(ctx.h, f)
+        tuned = {"lanes_per_output": lanes,
+                 "ms_per_iteration_launch_by_lanes": dict(zip(["1", "2", "4", "8", "16", "32"],
+                                                              lane_ms))}
+        if lane_ms[2] > 0 and min(lane_ms) > 0:
+            tuned["gain_vs_4_lanes"] = lane_ms[2] / min(lane_ms)
         batch = {"paths": args.batch_paths, "steps_per_path": bparams["max_steps"] + 1, "ms": bms,
+                 "summation_tuning": tuned,
                  "corrector_steps_per_s": bit / (bms * 1e-3),
                  "pc_steps_per_s": sum(x["steps"] for x in bstats) / (bms * 1e-3),
                  "segments_per_s": args.batch_paths / (bms * 1e-3),
