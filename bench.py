@@ -1032,6 +1032,66 @@ def hard_precision_leg(libph, synth, ctx, torch, dev, seed, steps, decades=8.0, 
     return out
 
 
+def large_job_leg(libph, synth, ctx, seed, nsmall=64):
+    """The serving loop's large-job route (ph_server_config.big_n = 64): a
+    stream of small requests (n log-uniform in [16, 64], dense or sparse,
+    DD/QD 70/30, 20-step segments) alone, then the same stream with two large
+    jobs submitted in its middle -- a dense n = 128 DD system (128 terms per
+    polynomial over 16 variables, 5-step segment) and the sparse n = 320 QD
+    system (3-step segment) -- which run alone on the whole GPU by the
+    single-path tracker while small-job admission pauses.  Reports each large
+    job's latency and the small jobs' p50/p99 without and with them."""
+    rng = np.random.default_rng(seed + 2000)
+    small = []
+    for i in range(nsmall):
+        srng = synth.Rng(seed * 104729 + i)
+        n = int(round(np.exp(srng.uniform() * (np.log(64) - np.log(16)) + np.log(16))))
+        dense = i % 2 == 0
+        L = 2 if rng.random() < 0.7 else 4
+        spec = (synth.dense_system(srng, n, n, min(16, n), (1, 2, 3)) if dense
+                else synth.sparse_system(srng, n))
+        g = srng.unit_complex()
+        small.append((ctx.load(spec, L), _soa([g], L).reshape(L, 2), _soa(np.ones(n), L),
+                      synth.default_params(L, max_steps=19)))
+    big = []
+    for (n, L, dense, steps) in ((128, 2, True, 5), (320, 4, False, 3)):
+        srng = synth.Rng(seed * 7 + n)
+        spec = (synth.dense_system(srng, n, n, 16, (1, 2, 3)) if dense
+                else synth.sparse_system(srng, n))
+        g = srng.unit_complex()
+        big.append((ctx.load(spec, L), _soa([g], L).reshape(L, 2), _soa(np.ones(n), L),
+                     synth.default_params(L, max_steps=steps - 1, max_newton=3 if L == 2 else 5,
+                                          tol_path=1e-8), n, L))
+    out = {}
+    srv = libph.ph_server_create(ctx.h, max_n=64, pool_bytes=4 << 30, queue_cap=512, big_n=64)
+    try:
+        for label, with_big in (("small_alone", False), ("with_two_large_jobs", True)):
+            ids, bids = [], []
+            t0 = time.perf_counter()
+            for i, (f, gam, x0, p) in enumerate(small):
+                ids.append(libph.ph_server_submit(ctx.h, srv, f, None, gam, x0, p))
+                if with_big and i in (nsmall // 4, nsmall // 2):
+                    bf, bg, bx, bp, _, _ = big[len(bids)]
+                    bids.append(libph.ph_server_submit(ctx.h, srv, bf, None, bg, bx, bp))
+            lats = [libph.ph_server_wait(ctx.h, srv, jid, 900000)[1] for jid in ids]
+            row = {"small_jobs": len(ids), "wall_s": time.perf_counter() - t0,
+                   "small_p50_ms": float(np.percentile(lats, 50)),
+                   "small_p99_ms": float(np.percentile(lats, 99))}
+            for (bf, bg, bx, bp, n, L), jid in zip(big, bids):
+                st, lat = libph.ph_server_wait(ctx.h, srv, jid, 900000)
+                row[f"large_n{n}_{'dd' if L == 2 else 'qd'}"] = {
+                    "latency_ms": lat, "status": libph.STATUS_NAMES[st["status"]],
+                    "steps": st["steps"], "newton_iters": st["newton_iters"]}
+            out[label] = row
+    finally:
+        libph.ph_server_destroy(srv)
+    for f, _, _, _ in small:
+        ctx.free(f)
+    for bf, _, _, _, _, _ in big:
+        ctx.free(bf)
+    return out
+
+
 def combine_ranks(dist, torch, tot_ms: float, iters: int, device):
     """Whole-job figures of a replicas run: the slowest rank's timed ms and the
     corrector steps of all ranks (each rank tracks its own path; the only
@@ -1164,6 +1224,8 @@ def main():
                     help="planted dense64 QD paths tracked whole by the single-path form")
     ap.add_argument("--sparse-steps", type=int, default=16,
                     help="predictor-corrector steps of the sparse n = 512 QD path (0 skips)")
+    ap.add_argument("--large-jobs", type=int, default=1,
+                    help="1: the serving loop's large-job route leg (0 skips it)")
     ap.add_argument("--hard-steps", type=int, default=30,
                     help="steps of the ill-conditioned precision128 segment (0 skips)")
     ap.add_argument("--only-mgs", default=None, metavar="L,N,n,reps",
@@ -1318,7 +1380,7 @@ def main():
         monodromy["degree"] = monodromy_degree_leg(
             synth, ctx, args.seed, [(16, 32)] + ([(64, 76)] if args.monodromy_degree_64 else []))
 
-    whole = sparse = hard = None
+    whole = sparse = hard = large = None
     if rank == 0 and world == 1:
         if args.whole_paths > 0 or args.whole_paths_qd > 0:
             _t0 = time.perf_counter()
@@ -1329,6 +1391,10 @@ def main():
             _t0 = time.perf_counter()
             sparse = sparse512_leg(libph, synth, ctx, torch, dev, args.seed, args.sparse_steps)
             legs['sparse512'] = time.perf_counter() - _t0
+        if args.large_jobs:
+            _t0 = time.perf_counter()
+            large = large_job_leg(libph, synth, ctx, args.seed)
+            legs['serving_large_jobs'] = time.perf_counter() - _t0
         if args.hard_steps > 0:
             _t0 = time.perf_counter()
             hard = hard_precision_leg(libph, synth, ctx, torch, dev, args.seed, args.hard_steps)
@@ -1407,6 +1473,7 @@ def main():
             "serving_mixed": serve_mixed, "precision": precision, "cyclic": cyclic,
             "cyclic_monodromy_path": monodromy, "whole_paths": whole,
             "sparse512_segment": sparse, "precision_ill_conditioned": hard,
+            "serving_large_jobs": large,
             "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": s["launches"], "roofline": roof, "roofline_sparse512_mgs": roof512,
