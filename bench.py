@@ -1210,7 +1210,7 @@ def main():
                     help="steps per path of the many-path leg (default: the segment)")
     ap.add_argument("--precision-paths", type=int, default=152,
                     help="paths of the precision-form leg (0 skips it)")
-    ap.add_argument("--serve-requests", type=int, default=256,
+    ap.add_argument("--serve-requests", type=int, default=384,
                     help="requests of the serving leg (0 skips it)")
     ap.add_argument("--no-cyclic", action="store_true", help="skip the cyclic n-roots legs")
     ap.add_argument("--monodromy", action="store_true",
