@@ -58,18 +58,25 @@ PHD unsigned long long global_timer_ns() {
   return t;
 }
 
+__device__ __forceinline__ int ld_acquire(const int *p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 // Thread 0 waits until *flag == tag (or the timeout flag is set); the block
-// then proceeds.  Returns false when the wait gave up.
+// then proceeds.  The flag is read with acquire semantics, so every read the
+// block makes after the barrier sees what the publisher wrote before its
+// release.  Returns false when the wait gave up.
 __device__ bool wait_flag(const int *flag, int tag, PathState *st, unsigned long long limit_ns) {
   __shared__ int s_ok;
   if (threadIdx.x == 0) {
-    volatile const int *f = flag;
     volatile int *tmo = &st->timeout;
     int ok = 1;
-    if (*f != tag) {
+    if (ld_acquire(flag) != tag) {
       unsigned long long t0 = global_timer_ns();
       unsigned spins = 0;
-      while (*f != tag) {
+      while (ld_acquire(flag) != tag) {
         if (*tmo) { ok = 0; break; }
         if ((++spins & 255u) == 0 && global_timer_ns() - t0 > limit_ns) {
           atomicExch(&st->timeout, 1);
@@ -78,19 +85,19 @@ __device__ bool wait_flag(const int *flag, int tag, PathState *st, unsigned long
         }
       }
     }
-    __threadfence();
     s_ok = ok;
   }
   __syncthreads();
   return s_ok != 0;
 }
 
+// After a block barrier, thread 0 stores the flag with release semantics:
+// everything the block wrote before the barrier is visible to a block that
+// reads the flag with acquire semantics.
 __device__ void publish(int *flag, int tag) {
   __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    *(volatile int *)flag = tag;
-  }
+  if (threadIdx.x == 0)
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" : : "l"(flag), "r"(tag) : "memory");
 }
 
 // Sum over the block's warps of one part: warps [0, WP) carry part 0, [WP, 2 WP)
@@ -201,16 +208,12 @@ __global__ void __launch_bounds__(64 * WP) k_mgs(int N, int n, double *__restric
   }
   for (int k = 0; k < last_own; ++k) {
     if (!wait_flag(&ready[k], tag, st, limit_ns)) break;
+    // the pivot's norm, its inverse and this lane's first kRowCache rows of
+    // the pivot column (kept in registers for every column's dot product and
+    // update), all requested before any of them is used
+    const double *ak = A + (long)k * ldA;
     const real r2 = r_load_cg<P>(nrm2, nc, k);
     const real inv2 = r_load_cg<P>(ninv, nc, k);
-    const double lead = P::lead(r2);
-    if (!(lead > 0.0) || !isfinite(lead) || !isfinite(P::lead(inv2))) {
-      if (tid == 0) atomicExch(&st->mgs_status, PH_NONFINITE);   // the same value in every block
-      break;
-    }
-    const double *ak = A + (long)k * ldA;
-    // this lane's first kRowCache rows of the pivot column, loaded once per
-    // pivot and kept in registers for every column's dot product and update
     real ck_r[kRowCache], ck_i[kRowCache];
 #pragma unroll
     for (int q = 0; q < kRowCache; ++q) {
@@ -226,6 +229,11 @@ __global__ void __launch_bounds__(64 * WP) k_mgs(int N, int n, double *__restric
     if (w == 1 && lane < N) {
       c0_r = load_part_cg<P>(ak, Ap, 0, lane);
       c0_i = load_part_cg<P>(ak, Ap, 1, lane);
+    }
+    const double lead = P::lead(r2);
+    if (!(lead > 0.0) || !isfinite(lead) || !isfinite(P::lead(inv2))) {
+      if (tid == 0) atomicExch(&st->mgs_status, PH_NONFINITE);   // the same value in every block
+      break;
     }
     for (int j = k + 1 + (((b - (k + 1)) % G) + G) % G; j <= n; j += G) {
       double *aj = A + (long)j * ldA;

@@ -104,7 +104,7 @@ struct DD {
   // 1/b: the double reciprocal y0 and one Newton correction y0 + y0 (1 - b y0);
   // 1 - b.h y0 is exact in one FMA for a correctly rounded y0.  ~16 ops.
   PHD static real recip(real b) {
-    double y0 = 1.0 / b.h;
+    double y0 = __drcp_rn(b.h);                   // correctly rounded, as 1.0 / b.h
     double e = ffma(-b.h, y0, 1.0);
     e = ffma(-b.l, y0, e);
     double s, t;
@@ -240,7 +240,7 @@ struct QD {
   // 1/b: a double-double reciprocal, then one Newton step y + y (1 - b y) in
   // quad-double (106 -> 212 bits).
   PHD static real recip(real b) {
-    double y0 = 1.0 / b.x[0];
+    double y0 = __drcp_rn(b.x[0]);                // correctly rounded, as 1.0 / b.x[0]
     double e = ffma(-b.x[0], y0, 1.0);
     e = ffma(-b.x[1], y0, e);
     double s, t;
