@@ -169,6 +169,85 @@ __device__ __forceinline__ double fix_round_off(Fix<W> &acc, int base) {
   return neg ? -d : d;
 }
 
+// The double m 2^E for a significand with its top bit at bit 52 (or m = 2^53
+// after rounding up, handled by the caller); zero below the normal range,
+// infinity above it.
+__device__ __forceinline__ double fix_make_double(unsigned long long m, int E) {
+  const int ex = E + 52;                           // unbiased exponent
+  if (ex > 1023) return __longlong_as_double(0x7ff0000000000000ll);
+  if (ex < -1022) return 0.0;
+  return __longlong_as_double(
+      (long long)(((unsigned long long)(ex + 1023) << 52) | (m & 0xfffffffffffffull)));
+}
+
+// A non-zero 128-bit magnitude (h, l) shifted left by lz = its leading zeros
+// (n1, n0), the 53 leading bits m, whether round-to-nearest-even rounds m up,
+// and the 11 bits of n1 below m.
+__device__ __forceinline__ void fix_norm128(unsigned long long h, unsigned long long l, int &lz,
+                                            unsigned long long &m, bool &up,
+                                            unsigned long long &r, unsigned long long &n0) {
+  lz = h ? __clzll((long long)h) : 64 + __clzll((long long)l);
+  unsigned long long n1;
+  if (lz >= 64) {
+    n1 = l << (lz - 64);
+    n0 = 0ull;
+  } else if (lz == 0) {
+    n1 = h;
+    n0 = l;
+  } else {
+    n1 = (h << lz) | (l >> (64 - lz));
+    n0 = l << lz;
+  }
+  m = n1 >> 11;
+  r = n1 & 0x7ffull;
+  up = (r & 0x400ull) && ((r & 0x3ffull) || n0 || (m & 1ull));
+}
+
+// Two limbs from a two-word accumulator (last bit 2^base) in straight-line
+// code: v0 the double nearest to it, v1 the double nearest to what remains
+// (the same values as two fix_round_off<2> calls).
+__device__ __forceinline__ void fix_round2(const Fix<2> &acc, int base, double &v0, double &v1) {
+  unsigned long long h = acc.w[1], l = acc.w[0];
+  const bool neg = (long long)h < 0;
+  if (neg) {                                       // magnitude of the two's complement value
+    l = ~l + 1ull;
+    h = ~h + (l == 0ull ? 1ull : 0ull);
+  }
+  v0 = v1 = 0.0;
+  if ((h | l) == 0ull) return;
+  int lz;
+  unsigned long long m, r, n0;
+  bool up;
+  fix_norm128(h, l, lz, m, up, r, n0);
+  const int e = 127 - lz - 52 + base;              // weight of m's last bit
+  const unsigned long long mu = m + (up ? 1ull : 0ull);
+  v0 = (mu >> 53) ? fix_make_double(1ull << 52, e + 1) : fix_make_double(mu, e);
+  // what remains, in the normalised frame: (r - 2^11 up) 2^64 + n0, signed
+  long long R1 = (long long)r - (up ? 0x800ll : 0ll);
+  unsigned long long R0 = n0;
+  const bool rneg = R1 < 0;
+  if (rneg) {
+    R0 = ~R0 + 1ull;
+    R1 = ~R1 + (R0 == 0ull ? 1ll : 0ll);
+  }
+  if ((R1 | (long long)R0) != 0) {
+    int lz2;
+    unsigned long long m2, r2, n02;
+    bool up2;
+    fix_norm128((unsigned long long)R1, R0, lz2, m2, up2, r2, n02);
+    // bit 127 of the normalised frame weighs 2^(127 - lz + base); the
+    // remainder's frame is that one shifted by 64 + lz bits
+    const int e2 = 127 - lz2 - 52 + base - lz;
+    const unsigned long long mu2 = m2 + (up2 ? 1ull : 0ull);
+    v1 = (mu2 >> 53) ? fix_make_double(1ull << 52, e2 + 1) : fix_make_double(mu2, e2);
+    if (rneg) v1 = -v1;
+  }
+  if (neg) {
+    v0 = -v0;
+    v1 = -v1;
+  }
+}
+
 template <int W, int L>
 __device__ __forceinline__ void warp_exact_sum_limbs(double (&v)[L]) {
   // largest exponent of the leading limbs; any non-finite input poisons all
@@ -206,8 +285,12 @@ __device__ __forceinline__ void warp_exact_sum_limbs(double (&v)[L]) {
     for (int q = 0; q < W; ++q) o.w[q] = __shfl_xor_sync(0xffffffffu, acc.w[q], off);
     acc = fix_add<W>(acc, o);
   }
+  if constexpr (W == 2 && L == 2) {
+    fix_round2(acc, base, v[0], v[1]);
+  } else {
 #pragma unroll
-  for (int l = 0; l < L; ++l) v[l] = fix_round_off<W>(acc, base);
+    for (int l = 0; l < L; ++l) v[l] = fix_round_off<W>(acc, base);
+  }
 }
 
 // The exact warp sum of a DD (W = 2) or QD (W = 4) value, rounded to L limbs.
