@@ -65,6 +65,13 @@ OPS = {
 }
 
 
+# The many-path kernel's DD MGS runs its dot products and updates in fixed
+# point (exact products and cross terms in FP64, the sums in integer units):
+# 8 FP64 instructions per part of a dot-product term and 8 per part of an
+# update, 2 x (8 + 8) per (row, pivot, later column).
+MGS_UNIT_FIXED_DD = 32
+
+
 def ad_ops(spec, L: int) -> int:
     """FP64 operations of the monomial AD kernel for one evaluation."""
     o = OPS[L]
@@ -87,12 +94,14 @@ def sum_ops(spec, L: int) -> int:
     return contrib * o["cadd"]
 
 
-def mgs_ops(N: int, n: int, L: int) -> int:
+def mgs_ops(N: int, n: int, L: int, unit=None) -> int:
     """Per solve: the dot-product term and the update of every (row, pivot,
-    later column) of [J | rhs], the column norms, the back substitution."""
+    later column) of [J | rhs], the column norms, the back substitution.
+    `unit` overrides the FP64 operations per (row, pivot, later column)."""
     o = OPS[L]
     pairs = n * (n + 1) // 2                          # (k, j) with k < j <= n
-    return pairs * N * o["mgs_unit"] + (n + 1) * N * o["mgs_sq"] + (n * (n - 1) // 2) * o["mgs_back"]
+    u = o["mgs_unit"] if unit is None else unit
+    return pairs * N * u + (n + 1) * N * o["mgs_sq"] + (n * (n - 1) // 2) * o["mgs_back"]
 
 
 # ---- clocks during the timed region
@@ -1339,7 +1348,12 @@ def main():
         e1.synchronize()
         bms = e0.elapsed_time(e1)
         bit = sum(x["newton_iters"] for x in bstats)
-        bops = bit * (ad_ops(wl.f, wl.L) + sum_ops(wl.f, wl.L) + mgs_ops(wl.f.N, wl.n, wl.L))
+        # FP64 instructions the kernel issues (DD: the fixed-point MGS tally),
+        # and the same work counted in the FP64 forms of the single-path kernels
+        fx_unit = MGS_UNIT_FIXED_DD if wl.L == 2 else None
+        bops = bit * (ad_ops(wl.f, wl.L) + sum_ops(wl.f, wl.L) +
+                      mgs_ops(wl.f.N, wl.n, wl.L, unit=fx_unit))
+        bops_form = bit * (ad_ops(wl.f, wl.L) + sum_ops(wl.f, wl.L) + mgs_ops(wl.f.N, wl.n, wl.L))
         bach = bops / (bms * 1e-3) / 1e9
         lanes, lane_ms = libph.ph_block_lanes(ctx.h, f)
         tuned = {"lanes_per_output": lanes,
@@ -1356,7 +1370,9 @@ def main():
                  "gpu_launches": 1,
                  "roofline": {"bound": "alu", "kernel": "k_paths (whole step, many paths)",
                               "achieved": bach, "peak": peak, "unit": "G FP64-ops/s",
-                              "frac": bach / peak}}
+                              "frac": bach / peak,
+                              "ops": "FP64 instructions issued (DD MGS sums in integer units)",
+                              "fp64_form_equivalent_frac": bops_form / (bms * 1e-3) / 1e9 / peak}}
 
     serve = serve_mixed = None
     if args.serve_requests > 0 and rank == 0:

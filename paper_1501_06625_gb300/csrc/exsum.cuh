@@ -306,4 +306,103 @@ __device__ __forceinline__ qd warp_exact_sum(const qd &a) {
   return {{v[0], v[1], v[2], v[3]}};
 }
 
+// ------------------------------------------------ double-double in fixed point
+// Throughput forms of the DD dot-product and update steps, for kernels with
+// enough warps to hide integer latency (measured on this GPU at 16 warps per
+// SM: a DD update a - x y + u v costs 27 FP64 instructions in the FP64 form
+// and 8 here, and runs 2.1x as fast; with one warp its latency is higher, so
+// latency-bound kernels keep the FP64 form).  Each product of leading limbs is
+// split exactly (two_prod), the cross products of a leading and a trailing
+// limb are summed in double, and all terms are added exactly as 128-bit
+// two's-complement integers with a common last-bit weight 2^base; the total is
+// rounded back to two limbs (fix_round2).
+
+typedef unsigned __int128 fx128;
+
+// Biased exponent field of a double: 0 for zero and subnormals, 2047 for inf
+// and NaN; a double with field f is below 2^(f - 1022) in magnitude.
+__device__ __forceinline__ unsigned dbl_ef(double d) {
+  return (unsigned)((unsigned long long)__double_as_longlong(d) >> 52) & 0x7ffu;
+}
+
+// Last-bit weight of a 128-bit accumulator for terms below 2^(key - 1022) in
+// magnitude whose sum is below 2^lg times that bound (sign bit kept free).
+__device__ __forceinline__ int fx_base(int key, int lg) { return key - 1022 + lg + 1 - 128; }
+
+// d as a signed 128-bit integer in units of 2^base, truncated toward zero
+// (subnormals count as zero)
+__device__ __forceinline__ fx128 fx_place(double d, int base) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const int ef = (int)((b >> 52) & 0x7ff);
+  const unsigned long long m = ef ? ((b & 0xfffffffffffffull) | (1ull << 52)) : 0ull;
+  const int s = ef - 1075 - base;
+  fx128 v;
+  if (s >= 0) v = s < 128 ? ((fx128)m << s) : (fx128)0;
+  else v = s > -64 ? (fx128)(m >> (-s)) : (fx128)0;
+  return (b >> 63) ? (fx128)0 - v : v;
+}
+
+__device__ __forceinline__ dd fx_round_dd(fx128 acc, int base) {
+  Fix<2> f;
+  f.w[0] = (unsigned long long)acc;
+  f.w[1] = (unsigned long long)(acc >> 64);
+  dd r;
+  fix_round2(f, base, r.h, r.l);
+  return r;
+}
+
+__device__ __forceinline__ fx128 fx_shfl_xor(fx128 a, int m) {
+  const unsigned long long lo = __shfl_xor_sync(0xffffffffu, (unsigned long long)a, m);
+  const unsigned long long hi = __shfl_xor_sync(0xffffffffu, (unsigned long long)(a >> 64), m);
+  return ((fx128)hi << 64) | lo;
+}
+
+// sum over the warp (every lane gets it)
+__device__ __forceinline__ fx128 fx_warp_sum(fx128 a) {
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) a += fx_shfl_xor(a, m);
+  return a;
+}
+
+// acc += x1 y1 + sg x2 y2 (sg = +-1) in units of 2^base: the exact leading
+// products and the four cross products (8 FP64 instructions)
+__device__ __forceinline__ void fx_dot2(fx128 &acc, const dd &x1, const dd &y1, const dd &x2,
+                                        const dd &y2, double sg, int base) {
+  const double x2h = sg * x2.h, x2l = sg * x2.l;
+  double p1, e1, p2, e2;
+  two_prod(x1.h, y1.h, p1, e1);
+  two_prod(x2h, y2.h, p2, e2);
+  double c = ph::fmul(x1.h, y1.l);
+  c = ph::ffma(x1.l, y1.h, c);
+  c = ph::ffma(x2h, y2.l, c);
+  c = ph::ffma(x2l, y2.h, c);
+  acc += fx_place(p1, base) + fx_place(e1, base) + fx_place(p2, base) + fx_place(e2, base) +
+         fx_place(c, base);
+}
+
+// a - ar b + sg ai c (one part of a complex update), exactly summed and
+// rounded to two limbs: the same value as Part<DD>::upd up to its rounding
+// (this one is the nearer to the exact result)
+__device__ __forceinline__ dd fx_upd(const dd &a, const dd &ar, const dd &b, const dd &ai,
+                                     const dd &c, double sg) {
+  const double aih = sg * ai.h, ail = sg * ai.l;
+  double p1, e1, p2, e2;
+  two_prod(ar.h, b.h, p1, e1);
+  two_prod(aih, c.h, p2, e2);
+  double x = ph::fmul(ar.h, b.l);
+  x = ph::ffma(ar.l, b.h, x);
+  double y = ph::fmul(aih, c.l);
+  y = ph::ffma(ail, c.h, y);
+  // terms added: a.h, a.l, p2, e2, y; subtracted (in the integers): p1, e1, x
+  const unsigned key = max(max(max(dbl_ef(a.h), dbl_ef(a.l)), max(dbl_ef(p1), dbl_ef(e1))),
+                           max(max(dbl_ef(p2), dbl_ef(e2)), max(dbl_ef(x), dbl_ef(y))));
+  if (key == 0u) return {0.0, 0.0};
+  if (key == 0x7ffu) return {a.h - p1 + p2, 0.0};         // inf or NaN, as the FP64 form
+  const int base = fx_base((int)key, 2);                   // a.h, p1, p2: the sum is below 4x
+  const fx128 acc = fx_place(a.h, base) + fx_place(a.l, base) + fx_place(p2, base) +
+                    fx_place(e2, base) + fx_place(y, base) -
+                    (fx_place(p1, base) + fx_place(e1, base) + fx_place(x, base));
+  return fx_round_dd(acc, base);
+}
+
 }  // namespace ph

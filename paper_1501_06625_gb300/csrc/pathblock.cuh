@@ -71,8 +71,12 @@ inline JobLayout job_layout(int L, int n, long ldA, int emax, long nsf, long nsg
   return o;
 }
 
-// dynamic shared memory of a block for jobs of up to n variables (doubles)
-inline size_t job_smem_bytes(int L, int n) { return sizeof(double) * (2L * L * n + (long)L * (n + 1)); }
+// dynamic shared memory of a block for jobs of up to n variables: the back
+// substitution's y [2L][n], the pivot norms [L][n+1], and the columns'
+// exponent bounds of the DD fixed-point MGS [n+1] (unsigned)
+inline size_t job_smem_bytes(int L, int n) {
+  return sizeof(double) * (2L * L * n + (long)L * (n + 1) + (n + 2) / 2);
+}
 
 // one part (0 = real, 1 = imaginary) of element i of a complex array laid out
 // [limb][re|im][...] with `plane` doubles between planes
@@ -131,18 +135,48 @@ __device__ void block_sum(const Job &a, int o0, int o1, const double *fslots,
   }
 }
 
+// Largest exponent field of the leading limbs of column j's rows i = lane,
+// lane + 32, ... (both parts), over the warp: every entry is below
+// 2^(field - 1022) in magnitude.
+__device__ __forceinline__ unsigned dd_col_exp(const double *aj, long Ap, int N, int lane) {
+  unsigned m = 0;
+  for (int i = lane; i < N; i += 32)
+    m = max(m, max(dbl_ef(rp_load<DD>(aj, Ap, 0, i).h), dbl_ef(rp_load<DD>(aj, Ap, 1, i).h)));
+  return __reduce_max_sync(0xffffffffu, m);
+}
+
 // MGS of [J | -h] (A) and back substitution.  Returns PH_OK or PH_NONFINITE;
 // on success dx and max |dx_i| (in *s_dxmax).
+//
+// In double-double the dot products and updates run in fixed point
+// (exsum.cuh: 16 FP64 instructions per row where the FP64 forms take 48 for a
+// complex dot product, 16 for 54 for an update).  A dot product's terms are
+// bounded by the product of its columns' largest entries, so each column's
+// largest exponent field is kept in shared memory (s_nrm + L (n+1)) and
+// refreshed when the column is updated; the accumulator's scale follows from
+// the two bounds, with no pass over the rows first.  The truncation error is
+// below 2^-118 of the bound per term, under 2^-107 ||a_k|| ||a_j|| in all for
+// the column heights this kernel takes, below the FP64 form's.
 template <class P>
 __device__ int block_mgs(int N, int n, long ldA, double *A, double *W, double *dx, double *s_nrm,
                          double *s_y, double *s_dxmax) {
   typedef typename P::real real;
   typedef Part<P> PO;
+  constexpr bool kDD = std::is_same<P, DD>::value;
   __shared__ int s_bad;
   const int nc = n + 1;
   const long Ap = (long)nc * ldA, Wp = (long)nc * nc;
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  unsigned *s_cexp = (unsigned *)(s_nrm + (long)P::L * nc);
+  // headroom of a dot product's accumulator: 2N leading products and small terms
+  const int lgN = 32 - __clz(2 * N + 1);
   if (tid == 0) s_bad = 0;
+  if constexpr (kDD) {
+    for (int j = w; j <= n; j += kNW) {           // a column's bound is kept by its warp
+      const unsigned m = dd_col_exp(A + (long)j * ldA, Ap, N, lane);
+      if (lane == 0) s_cexp[j] = m;
+    }
+  }
   if (w == 0) {                                    // ||a_0||^2
     typename PO::acc ar = PO::zero(), ai = PO::zero();
     for (int i = lane; i < N; i += 32) {
@@ -164,30 +198,66 @@ __device__ int block_mgs(int N, int n, long ldA, double *A, double *W, double *d
     const double *ak = A + (long)k * ldA;
     for (int j = k + 1 + (((w - (k + 1)) % kNW) + kNW) % kNW; j <= n; j += kNW) {
       double *aj = A + (long)j * ldA;
-      typename PO::acc dr = PO::zero(), di = PO::zero();
-      for (int i = lane; i < N; i += 32) {
-        real akr = rp_load<P>(ak, Ap, 0, i), aki = rp_load<P>(ak, Ap, 1, i);
-        real ajr = rp_load<P>(aj, Ap, 0, i), aji = rp_load<P>(aj, Ap, 1, i);
-        PO::dot2(dr, akr, ajr, aki, aji, 1.0);
-        PO::dot2(di, akr, aji, aki, ajr, -1.0);
+      real dsr, dsi;                               // a_k^H a_j
+      if constexpr (kDD) {
+        const int ek = (int)s_cexp[k], ej = (int)s_cexp[j];
+        const int kb = ek + ej - 1022;             // the products are below 2^(kb - 1022)
+        if (ek == 0 || ej == 0) {
+          dsr = dsi = DD::zero();
+        } else if (ek == 0x7ff || ej == 0x7ff || kb > 2046) {
+          dsr = dsi = DD::from(__longlong_as_double(0x7ff8000000000000ll));
+        } else {
+          const int base = fx_base(kb, lgN);
+          fx128 accr = 0, acci = 0;
+          for (int i = lane; i < N; i += 32) {
+            const dd akr = rp_load<P>(ak, Ap, 0, i), aki = rp_load<P>(ak, Ap, 1, i);
+            const dd ajr = rp_load<P>(aj, Ap, 0, i), aji = rp_load<P>(aj, Ap, 1, i);
+            fx_dot2(accr, akr, ajr, aki, aji, 1.0, base);
+            fx_dot2(acci, akr, aji, aki, ajr, -1.0, base);
+          }
+          dsr = fx_round_dd(fx_warp_sum(accr), base);
+          dsi = fx_round_dd(fx_warp_sum(acci), base);
+        }
+      } else {
+        typename PO::acc dr = PO::zero(), di = PO::zero();
+        for (int i = lane; i < N; i += 32) {
+          real akr = rp_load<P>(ak, Ap, 0, i), aki = rp_load<P>(ak, Ap, 1, i);
+          real ajr = rp_load<P>(aj, Ap, 0, i), aji = rp_load<P>(aj, Ap, 1, i);
+          PO::dot2(dr, akr, ajr, aki, aji, 1.0);
+          PO::dot2(di, akr, aji, aki, ajr, -1.0);
+        }
+        dsr = warp_sum_part<P>(dr);
+        dsi = warp_sum_part<P>(di);
       }
-      const real alr = P::mul(warp_sum_part<P>(dr), inv2);
-      const real ali = P::mul(warp_sum_part<P>(di), inv2);
+      const real alr = P::mul(dsr, inv2);
+      const real ali = P::mul(dsi, inv2);
       if (lane == 0) {
         rp_store<P>(W + (long)j * nc, Wp, 0, k, alr);
         rp_store<P>(W + (long)j * nc, Wp, 1, k, ali);
       }
       typename PO::acc nr = PO::zero(), ni = PO::zero();
+      unsigned emax = 0;                           // the updated column's bound (DD)
       for (int i = lane; i < N; i += 32) {
         real akr = rp_load<P>(ak, Ap, 0, i), aki = rp_load<P>(ak, Ap, 1, i);
-        real ajr = PO::upd(rp_load<P>(aj, Ap, 0, i), alr, akr, ali, aki, 1.0);
-        real aji = PO::upd(rp_load<P>(aj, Ap, 1, i), alr, aki, ali, akr, -1.0);
+        real ajr, aji;
+        if constexpr (kDD) {
+          ajr = fx_upd(rp_load<P>(aj, Ap, 0, i), alr, akr, ali, aki, 1.0);
+          aji = fx_upd(rp_load<P>(aj, Ap, 1, i), alr, aki, ali, akr, -1.0);
+          emax = max(emax, max(dbl_ef(ajr.h), dbl_ef(aji.h)));
+        } else {
+          ajr = PO::upd(rp_load<P>(aj, Ap, 0, i), alr, akr, ali, aki, 1.0);
+          aji = PO::upd(rp_load<P>(aj, Ap, 1, i), alr, aki, ali, akr, -1.0);
+        }
         rp_store<P>(aj, Ap, 0, i, ajr);
         rp_store<P>(aj, Ap, 1, i, aji);
         if (j == k + 1) {
           PO::sq(nr, ajr);
           PO::sq(ni, aji);
         }
+      }
+      if constexpr (kDD) {
+        emax = __reduce_max_sync(0xffffffffu, emax);
+        if (lane == 0) s_cexp[j] = emax;
       }
       if (j == k + 1) {
         real s = P::add(warp_sum_part<P>(nr), warp_sum_part<P>(ni));
