@@ -248,6 +248,63 @@ __device__ __forceinline__ void fix_round2(const Fix<2> &acc, int base, double &
   }
 }
 
+// leading zeros of a 256-bit magnitude (256 for zero)
+__device__ __forceinline__ int fix_clz4(const Fix<4> &a) {
+  return a.w[3] ? __clzll((long long)a.w[3])
+       : a.w[2] ? 64 + __clzll((long long)a.w[2])
+       : a.w[1] ? 128 + __clzll((long long)a.w[1])
+       : a.w[0] ? 192 + __clzll((long long)a.w[0]) : 256;
+}
+
+// a 2^s for 0 <= s < 256 (bits above 255 dropped), by selects
+__device__ __forceinline__ Fix<4> fix_shl4(const Fix<4> &a, int s) {
+  const int ws = s >> 6, bs = s & 63;
+  Fix<4> r;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    // words q - ws and q - ws - 1 of a (zero below word 0)
+    unsigned long long hi = 0ull, lo = 0ull;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (q - k >= 0 && ws == k) hi = a.w[q - k];
+      if (q - k - 1 >= 0 && ws == k) lo = a.w[q - k - 1];
+    }
+    r.w[q] = bs ? (hi << bs) | (lo >> (64 - bs)) : hi;
+  }
+  return r;
+}
+
+// Four limbs from a four-word accumulator (last bit 2^base) in straight-line
+// code: each limb the double nearest to what the previous limbs leave (the
+// same values as four fix_round_off<4> calls).  Each step normalises the
+// remainder so that its top bit is bit 255, takes the 53 bits below it,
+// rounds to nearest even on the 203 bits under them, and keeps the signed
+// remainder in the same frame.
+__device__ __forceinline__ void fix_round4(const Fix<4> &acc, int base, double (&v)[4]) {
+  Fix<4> a = acc;
+#pragma unroll
+  for (int l = 0; l < 4; ++l) v[l] = 0.0;
+#pragma unroll
+  for (int l = 0; l < 4; ++l) {
+    const bool neg = (long long)a.w[3] < 0;
+    const Fix<4> mag = neg ? fix_neg<4>(a) : a;
+    const int lz = fix_clz4(mag);
+    if (lz == 256) break;
+    Fix<4> n = fix_shl4(mag, lz);
+    const unsigned long long m = n.w[3] >> 11, r = n.w[3] & 0x7ffull;
+    const bool sticky = (r & 0x3ffull) || n.w[2] || n.w[1] || n.w[0];
+    const bool up = (r & 0x400ull) && (sticky || (m & 1ull));
+    const int e = base - lz + 203;                 // weight of m's last bit
+    const unsigned long long mu = m + (up ? 1ull : 0ull);
+    const double d = (mu >> 53) ? fix_make_double(1ull << 52, e + 1) : fix_make_double(mu, e);
+    v[l] = neg ? -d : d;
+    // what remains: the 11 bits below m, less 2^11 if m was rounded up
+    n.w[3] = (unsigned long long)((long long)r - (up ? 0x800ll : 0ll));
+    a = neg ? fix_neg<4>(n) : n;
+    base -= lz;
+  }
+}
+
 template <int W, int L>
 __device__ __forceinline__ void warp_exact_sum_limbs(double (&v)[L]) {
   // largest exponent of the leading limbs; any non-finite input poisons all
@@ -287,6 +344,8 @@ __device__ __forceinline__ void warp_exact_sum_limbs(double (&v)[L]) {
   }
   if constexpr (W == 2 && L == 2) {
     fix_round2(acc, base, v[0], v[1]);
+  } else if constexpr (W == 4 && L == 4) {
+    fix_round4(acc, base, v);
   } else {
 #pragma unroll
     for (int l = 0; l < L; ++l) v[l] = fix_round_off<W>(acc, base);

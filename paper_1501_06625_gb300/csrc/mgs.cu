@@ -43,6 +43,7 @@
 #include "internal.h"
 #include "mp.cuh"
 #include "pathdev.cuh"
+#include "qfx.cuh"
 
 using namespace ph;
 
@@ -51,6 +52,9 @@ namespace {
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // default of the context setting
 constexpr int kRowCache = 4;        // pivot rows a lane keeps in registers (N <= 128 WP)
 constexpr int kDowndateBits = 20;   // cancellation beyond which a norm is recomputed
+// Headroom (log2) of the QD fixed-point dot product over the bound ||a_k|| ||a_j||:
+// one bit for rounding, the rest keeps every product's shift non-negative.
+constexpr int kQfDotLg = 6;
 
 PHD unsigned long long global_timer_ns() {
   unsigned long long t;
@@ -185,6 +189,9 @@ __global__ void __launch_bounds__(64 * WP) k_mgs(int N, int n, double *__restric
   __shared__ typename PO::acc sh_acc[2 * WP];
   __shared__ real sh_r[2];
   __shared__ int sh_rec;
+  __shared__ Q256 sh_q[2 * WP];                  // QD dot products: each warp's fixed-point sum
+  __shared__ int sh_qb[2 * WP];                  // and whether it met a non-finite value
+  constexpr bool kQD = std::is_same<P, QD>::value;
   extern __shared__ double s_y[];                // back substitution: [L][2][n]
   const int nc = n + 1;
   const long Ap = (long)nc * ldA, Wp = (long)nc * nc;
@@ -241,26 +248,96 @@ __global__ void __launch_bounds__(64 * WP) k_mgs(int N, int n, double *__restric
       // below (thread 0 overwrites it after them)
       const real old = r_load<P>(nrm2, nc, j);
       // this warp's part of a_k^H a_j:  re = akr ajr + aki aji,  im = akr aji - aki ajr
-      typename PO::acc a = PO::zero();
+      real d, d_other = P::zero();                 // this part's sum; the other part's (QD)
+      if constexpr (kQD) {
+        // QD: every product in 256-bit fixed point (qfx.cuh), summed exactly
+        // over the block.  ||a_k|| ||a_j|| bounds the sum of the products'
+        // magnitudes (Cauchy-Schwarz), so it sets the accumulator's scale.
+        // ||a_j||^2 is this column's current norm (downdated) or, for tall
+        // columns, its first one, which only decreases under projection.
+        const int er = (int)dbl_ef(P::lead(r2)), eo = (int)dbl_ef(P::lead(old));
+        Q256 acc = q_zero();
+        bool bad = eo == 0x7ff;
+        const bool zero = eo == 0;
+        const int kb = (er + eo + 1) / 2 + 1;        // ||a_k|| ||a_j|| < 2^(kb - 1022)
+        const int base = kb - 1022 + kQfDotLg + 1 - 255;
+        if (!zero && !bad) {
 #pragma unroll
-      for (int q = 0; q < kRowCache; ++q) {
-        const int i = r0 + RS * q;
-        if (i < N) {
-          real ajr = load_part<P>(aj, Ap, 0, i), aji = load_part<P>(aj, Ap, 1, i);
-          if (part == 0) PO::dot2(a, ck_r[q], ajr, ck_i[q], aji, 1.0);
-          else PO::dot2(a, ck_r[q], aji, ck_i[q], ajr, -1.0);
+          for (int q = 0; q < kRowCache; ++q) {
+            const int i = r0 + RS * q;
+            if (i < N) {
+              const real ajr = load_part<P>(aj, Ap, 0, i), aji = load_part<P>(aj, Ap, 1, i);
+              if (part == 0) qf_dot2(acc, ck_r[q], ajr, ck_i[q], aji, 1.0, base, &bad);
+              else qf_dot2(acc, ck_r[q], aji, ck_i[q], ajr, -1.0, base, &bad);
+            }
+          }
+          for (int i = r0 + RS * kRowCache; i < N; i += RS) {
+            const real akr = load_part_cg<P>(ak, Ap, 0, i), aki = load_part_cg<P>(ak, Ap, 1, i);
+            const real ajr = load_part<P>(aj, Ap, 0, i), aji = load_part<P>(aj, Ap, 1, i);
+            if (part == 0) qf_dot2(acc, akr, ajr, aki, aji, 1.0, base, &bad);
+            else qf_dot2(acc, akr, aji, aki, ajr, -1.0, base, &bad);
+          }
+#pragma unroll
+          for (int m = 16; m > 0; m >>= 1) acc = fix_add<4>(acc, q_shfl_xor(acc, m));
         }
+        const bool wbad = __any_sync(0xffffffffu, bad);
+        if (lane == 0) {
+          sh_q[w] = acc;
+          sh_qb[w] = wbad;
+        }
+        __syncthreads();
+        Q256 sp[2] = {sh_q[0], sh_q[WP]};
+        int anybad = 0;
+#pragma unroll
+        for (int q = 0; q < 2 * WP; ++q) anybad |= sh_qb[q];
+#pragma unroll
+        for (int q = 1; q < WP; ++q) {
+          sp[0] = fix_add<4>(sp[0], sh_q[q]);
+          sp[1] = fix_add<4>(sp[1], sh_q[WP + q]);
+        }
+        real v[2];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          if (anybad) v[r] = P::from(__longlong_as_double(0x7ff8000000000000ll));
+          else if (zero) v[r] = P::zero();
+          else fix_round4(sp[r], base, v[r].x);
+        }
+        d = v[part];
+        d_other = v[1 - part];
+      } else {
+        typename PO::acc a = PO::zero();
+#pragma unroll
+        for (int q = 0; q < kRowCache; ++q) {
+          const int i = r0 + RS * q;
+          if (i < N) {
+            real ajr = load_part<P>(aj, Ap, 0, i), aji = load_part<P>(aj, Ap, 1, i);
+            if (part == 0) PO::dot2(a, ck_r[q], ajr, ck_i[q], aji, 1.0);
+            else PO::dot2(a, ck_r[q], aji, ck_i[q], ajr, -1.0);
+          }
+        }
+        for (int i = r0 + RS * kRowCache; i < N; i += RS) {
+          real akr = load_part_cg<P>(ak, Ap, 0, i), aki = load_part_cg<P>(ak, Ap, 1, i);
+          real ajr = load_part<P>(aj, Ap, 0, i), aji = load_part<P>(aj, Ap, 1, i);
+          if (part == 0) PO::dot2(a, akr, ajr, aki, aji, 1.0);
+          else PO::dot2(a, akr, aji, aki, ajr, -1.0);
+        }
+        d = part_total<P, WP>(a, sh_acc);
       }
-      for (int i = r0 + RS * kRowCache; i < N; i += RS) {
-        real akr = load_part_cg<P>(ak, Ap, 0, i), aki = load_part_cg<P>(ak, Ap, 1, i);
-        real ajr = load_part<P>(aj, Ap, 0, i), aji = load_part<P>(aj, Ap, 1, i);
-        if (part == 0) PO::dot2(a, akr, ajr, aki, aji, 1.0);
-        else PO::dot2(a, akr, aji, aki, ajr, -1.0);
-      }
-      real d = part_total<P, WP>(a, sh_acc);
       real al = P::mul(d, inv2);                  // this part of alpha_kj
       real al_o = swap_parts<P, WP>(al, sh_r);        // the other part
       const real alr = part == 0 ? al : al_o, ali = part == 0 ? al_o : al;
+      // the update a - alr b + sg ali c of one part: QD in fixed point, with
+      // alpha converted once per column
+      QF qalr, qali;
+      bool abad = false;
+      if constexpr (kQD) {
+        qalr = qf_from(alr, &abad);
+        qali = qf_from(ali, &abad);
+      }
+      auto upd = [&](const real &x, const real &bb, const real &cc, double sg) -> real {
+        if constexpr (kQD) return qf_upd2(x, qalr, bb, qali, cc, sg, abad);
+        else return PO::upd(x, alr, bb, ali, cc, sg);
+      };
       if (tid == 0) {
 #pragma unroll
         for (int l = 0; l < P::L; ++l) {
@@ -291,18 +368,18 @@ __global__ void __launch_bounds__(64 * WP) k_mgs(int N, int n, double *__restric
           if (i < N) {
             if (part == 0)
               store_part<P>(aj, Ap, 0, i,
-                            PO::upd(load_part<P>(aj, Ap, 0, i), alr, ck_r[q], ali, ck_i[q], 1.0));
+                            upd(load_part<P>(aj, Ap, 0, i), ck_r[q], ck_i[q], 1.0));
             else
               store_part<P>(aj, Ap, 1, i,
-                            PO::upd(load_part<P>(aj, Ap, 1, i), alr, ck_i[q], ali, ck_r[q], -1.0));
+                            upd(load_part<P>(aj, Ap, 1, i), ck_i[q], ck_r[q], -1.0));
           }
         }
         for (int i = r0 + RS * kRowCache; i < N; i += RS) {
           real akr = load_part_cg<P>(ak, Ap, 0, i), aki = load_part_cg<P>(ak, Ap, 1, i);
           if (part == 0)
-            store_part<P>(aj, Ap, 0, i, PO::upd(load_part<P>(aj, Ap, 0, i), alr, akr, ali, aki, 1.0));
+            store_part<P>(aj, Ap, 0, i, upd(load_part<P>(aj, Ap, 0, i), akr, aki, 1.0));
           else
-            store_part<P>(aj, Ap, 1, i, PO::upd(load_part<P>(aj, Ap, 1, i), alr, aki, ali, akr, -1.0));
+            store_part<P>(aj, Ap, 1, i, upd(load_part<P>(aj, Ap, 1, i), aki, akr, -1.0));
         }
         if (split && w == 1) {                     // warp 0's rows of the real part
           for (int i = lane; i < N; i += 64) {
@@ -311,7 +388,7 @@ __global__ void __launch_bounds__(64 * WP) k_mgs(int N, int n, double *__restric
               akr = load_part_cg<P>(ak, Ap, 0, i);
               aki = load_part_cg<P>(ak, Ap, 1, i);
             }
-            store_part<P>(aj, Ap, 0, i, PO::upd(load_part<P>(aj, Ap, 0, i), alr, akr, ali, aki, 1.0));
+            store_part<P>(aj, Ap, 0, i, upd(load_part<P>(aj, Ap, 0, i), akr, aki, 1.0));
           }
         }
       }
@@ -326,7 +403,19 @@ __global__ void __launch_bounds__(64 * WP) k_mgs(int N, int n, double *__restric
         }
       } else {
         if (w == 0) {
-          const real s = P::sub(old, P::mul(P::add(P::mul(alr, alr), P::mul(ali, ali)), r2));
+          real s;
+          if constexpr (kQD) {
+            // ||a_j||^2 - |alpha|^2 ||a_k||^2 = ||a_j||^2 - Re(d conj(alpha)), d
+            // = a_k^H a_j (warp 0 carries the real part), in fixed point
+            bool b2 = abad;
+            const QF A = qf_from(old, &b2);
+            const QF p1 = qf_mul(qf_from(d, &b2), qalr);
+            const QF p2 = qf_mul(qf_from(d_other, &b2), qali);
+            const QF t[3] = {A, qf_neg(p1), qf_neg(p2)};
+            s = b2 ? P::from(__longlong_as_double(0x7ff8000000000000ll)) : qf_sum_to_qd<3>(t);
+          } else {
+            s = P::sub(old, P::mul(P::add(P::mul(alr, alr), P::mul(ali, ali)), r2));
+          }
           const bool rec = !(P::lead(s) > ldexp(P::lead(old), -kDowndateBits));
           if (lane == 0) {
             sh_rec = rec;

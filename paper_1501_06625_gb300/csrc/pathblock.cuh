@@ -17,6 +17,7 @@
 #include "internal.h"
 #include "mp.cuh"
 #include "pathdev.cuh"
+#include "qfx.cuh"
 
 namespace ph {
 
@@ -138,10 +139,12 @@ __device__ void block_sum(const Job &a, int o0, int o1, const double *fslots,
 // Largest exponent field of the leading limbs of column j's rows i = lane,
 // lane + 32, ... (both parts), over the warp: every entry is below
 // 2^(field - 1022) in magnitude.
-__device__ __forceinline__ unsigned dd_col_exp(const double *aj, long Ap, int N, int lane) {
+template <class P>
+__device__ __forceinline__ unsigned col_exp(const double *aj, long Ap, int N, int lane) {
   unsigned m = 0;
   for (int i = lane; i < N; i += 32)
-    m = max(m, max(dbl_ef(rp_load<DD>(aj, Ap, 0, i).h), dbl_ef(rp_load<DD>(aj, Ap, 1, i).h)));
+    m = max(m, max(dbl_ef(P::lead(rp_load<P>(aj, Ap, 0, i))),
+                   dbl_ef(P::lead(rp_load<P>(aj, Ap, 1, i)))));
   return __reduce_max_sync(0xffffffffu, m);
 }
 
@@ -163,6 +166,8 @@ __device__ int block_mgs(int N, int n, long ldA, double *A, double *W, double *d
   typedef typename P::real real;
   typedef Part<P> PO;
   constexpr bool kDD = std::is_same<P, DD>::value;
+  constexpr bool kQD = std::is_same<P, QD>::value;
+  constexpr bool kFix = kDD || kQD;
   __shared__ int s_bad;
   const int nc = n + 1;
   const long Ap = (long)nc * ldA, Wp = (long)nc * nc;
@@ -171,9 +176,9 @@ __device__ int block_mgs(int N, int n, long ldA, double *A, double *W, double *d
   // headroom of a dot product's accumulator: 2N leading products and small terms
   const int lgN = 32 - __clz(2 * N + 1);
   if (tid == 0) s_bad = 0;
-  if constexpr (kDD) {
+  if constexpr (kFix) {
     for (int j = w; j <= n; j += kNW) {           // a column's bound is kept by its warp
-      const unsigned m = dd_col_exp(A + (long)j * ldA, Ap, N, lane);
+      const unsigned m = col_exp<P>(A + (long)j * ldA, Ap, N, lane);
       if (lane == 0) s_cexp[j] = m;
     }
   }
@@ -218,6 +223,36 @@ __device__ int block_mgs(int N, int n, long ldA, double *A, double *W, double *d
           dsr = fx_round_dd(fx_warp_sum(accr), base);
           dsi = fx_round_dd(fx_warp_sum(acci), base);
         }
+      } else if constexpr (kQD) {
+        const int ek = (int)s_cexp[k], ej = (int)s_cexp[j];
+        const int kb = ek + ej - 1022;             // the products are below 2^(kb - 1022)
+        if (ek == 0 || ej == 0) {
+          dsr = dsi = QD::zero();
+        } else if (ek == 0x7ff || ej == 0x7ff || kb > 2046) {
+          dsr = dsi = QD::from(__longlong_as_double(0x7ff8000000000000ll));
+        } else {
+          // the sum of 2N products below 2^lg times the bound; three more bits
+          // keep every product's shift to the accumulator non-negative
+          const int lg = lgN + 3;
+          const int base = kb - 1022 + lg + 1 - 255;
+          Q256 accr = q_zero(), acci = q_zero();
+          bool bad = false;
+          for (int i = lane; i < N; i += 32) {
+            const qd akr = rp_load<P>(ak, Ap, 0, i), aki = rp_load<P>(ak, Ap, 1, i);
+            const qd ajr = rp_load<P>(aj, Ap, 0, i), aji = rp_load<P>(aj, Ap, 1, i);
+            qf_dot2(accr, akr, ajr, aki, aji, 1.0, base, &bad);
+            qf_dot2(acci, akr, aji, aki, ajr, -1.0, base, &bad);
+          }
+#pragma unroll
+          for (int m = 16; m > 0; m >>= 1) {
+            accr = fix_add<4>(accr, q_shfl_xor(accr, m));
+            acci = fix_add<4>(acci, q_shfl_xor(acci, m));
+          }
+          fix_round4(accr, base, dsr.x);
+          fix_round4(acci, base, dsi.x);
+          if (__any_sync(0xffffffffu, bad))
+            dsr = dsi = QD::from(__longlong_as_double(0x7ff8000000000000ll));
+        }
       } else {
         typename PO::acc dr = PO::zero(), di = PO::zero();
         for (int i = lane; i < N; i += 32) {
@@ -236,7 +271,13 @@ __device__ int block_mgs(int N, int n, long ldA, double *A, double *W, double *d
         rp_store<P>(W + (long)j * nc, Wp, 1, k, ali);
       }
       typename PO::acc nr = PO::zero(), ni = PO::zero();
-      unsigned emax = 0;                           // the updated column's bound (DD)
+      unsigned emax = 0;                           // the updated column's bound (DD, QD)
+      QF qalr, qali;                               // alpha in fixed point (QD)
+      bool abad = false;
+      if constexpr (kQD) {
+        qalr = qf_from(alr, &abad);
+        qali = qf_from(ali, &abad);
+      }
       for (int i = lane; i < N; i += 32) {
         real akr = rp_load<P>(ak, Ap, 0, i), aki = rp_load<P>(ak, Ap, 1, i);
         real ajr, aji;
@@ -244,6 +285,10 @@ __device__ int block_mgs(int N, int n, long ldA, double *A, double *W, double *d
           ajr = fx_upd(rp_load<P>(aj, Ap, 0, i), alr, akr, ali, aki, 1.0);
           aji = fx_upd(rp_load<P>(aj, Ap, 1, i), alr, aki, ali, akr, -1.0);
           emax = max(emax, max(dbl_ef(ajr.h), dbl_ef(aji.h)));
+        } else if constexpr (kQD) {
+          ajr = qf_upd2(rp_load<P>(aj, Ap, 0, i), qalr, akr, qali, aki, 1.0, abad);
+          aji = qf_upd2(rp_load<P>(aj, Ap, 1, i), qalr, aki, qali, akr, -1.0, abad);
+          emax = max(emax, max(dbl_ef(ajr.x[0]), dbl_ef(aji.x[0])));
         } else {
           ajr = PO::upd(rp_load<P>(aj, Ap, 0, i), alr, akr, ali, aki, 1.0);
           aji = PO::upd(rp_load<P>(aj, Ap, 1, i), alr, aki, ali, akr, -1.0);
@@ -255,7 +300,7 @@ __device__ int block_mgs(int N, int n, long ldA, double *A, double *W, double *d
           PO::sq(ni, aji);
         }
       }
-      if constexpr (kDD) {
+      if constexpr (kFix) {
         emax = __reduce_max_sync(0xffffffffu, emax);
         if (lane == 0) s_cexp[j] = emax;
       }

@@ -153,8 +153,7 @@ __device__ __forceinline__ qd qf_sum_to_qd(const QF (&v)[T]) {
     acc = fix_add<4>(acc, q_sar(v[i].m, base - v[i].e));
   }
   qd r;
-#pragma unroll
-  for (int l = 0; l < 4; ++l) r.x[l] = fix_round_off<4>(acc, base);
+  fix_round4(acc, base, r.x);
   return r;
 }
 
@@ -167,6 +166,39 @@ __device__ __forceinline__ qd qf_upd(const qd &a, const qd &ar, const qd &b, con
   QF p2 = qf_mul(qf_from(ai, &bad), qf_from(c, &bad));
   if (sg < 0) p2 = qf_neg(p2);
   if (bad) return {{a.x[0] - ar.x[0] * b.x[0] + sg * ai.x[0] * c.x[0], 0.0, 0.0, 0.0}};
+  const QF t[3] = {A, qf_neg(p1), p2};
+  return qf_sum_to_qd<3>(t);
+}
+
+// acc += x1 y1 + sg x2 y2 for QD values, the products in 256-bit fixed point
+// aligned to the accumulator's last-bit weight 2^base (every product's
+// magnitude is below 2^(base + 252 - lg) by the caller's bound)
+__device__ __forceinline__ void qf_dot2(Q256 &acc, const qd &x1, const qd &y1, const qd &x2,
+                                       const qd &y2, double sg, int base, bool *bad) {
+  const QF p1 = qf_mul(qf_from(x1, bad), qf_from(y1, bad));
+  QF p2 = qf_mul(qf_from(x2, bad), qf_from(y2, bad));
+  if (sg < 0) p2 = qf_neg(p2);
+  if (p1.e != kQFZeroE) acc = fix_add<4>(acc, q_sar(p1.m, base - p1.e));
+  if (p2.e != kQFZeroE) acc = fix_add<4>(acc, q_sar(p2.m, base - p2.e));
+}
+
+__device__ __forceinline__ Q256 q_shfl_xor(const Q256 &a, int m) {
+  Q256 r;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) r.w[q] = __shfl_xor_sync(0xffffffffu, a.w[q], m);
+  return r;
+}
+
+// a - ar b + sg ai c with ar, ai already in fixed point (abad: either was not
+// finite); a non-finite input gives NaN
+__device__ __forceinline__ qd qf_upd2(const qd &a, const QF &ar, const qd &b, const QF &ai,
+                                      const qd &c, double sg, bool abad) {
+  bool bad = abad;
+  const QF A = qf_from(a, &bad);
+  const QF p1 = qf_mul(ar, qf_from(b, &bad));
+  QF p2 = qf_mul(ai, qf_from(c, &bad));
+  if (sg < 0) p2 = qf_neg(p2);
+  if (bad) return {{__longlong_as_double(0x7ff8000000000000ll), 0.0, 0.0, 0.0}};
   const QF t[3] = {A, qf_neg(p1), p2};
   return qf_sum_to_qd<3>(t);
 }
