@@ -55,6 +55,9 @@ constexpr int kDowndateBits = 20;   // cancellation beyond which a norm is recom
 // Headroom (log2) of the QD fixed-point dot product over the bound ||a_k|| ||a_j||:
 // one bit for rounding, the rest keeps every product's shift non-negative.
 constexpr int kQfDotLg = 6;
+// QD: the pivot column in fixed point in shared memory ([2][N] QF, aliasing the
+// back substitution's buffer) up to this height
+constexpr int kQfCacheMaxN = 2560;
 
 PHD unsigned long long global_timer_ns() {
   unsigned long long t;
@@ -192,6 +195,7 @@ __global__ void __launch_bounds__(64 * WP) k_mgs(int N, int n, double *__restric
   __shared__ Q256 sh_q[2 * WP];                  // QD dot products: each warp's fixed-point sum
   __shared__ int sh_qb[2 * WP];                  // and whether it met a non-finite value
   constexpr bool kQD = std::is_same<P, QD>::value;
+  const bool qcache = kQD && N <= kQfCacheMaxN;
   extern __shared__ double s_y[];                // back substitution: [L][2][n]
   const int nc = n + 1;
   const long Ap = (long)nc * ldA, Wp = (long)nc * nc;
@@ -242,6 +246,20 @@ __global__ void __launch_bounds__(64 * WP) k_mgs(int N, int n, double *__restric
       if (tid == 0) atomicExch(&st->mgs_status, PH_NONFINITE);   // the same value in every block
       break;
     }
+    // QD: every row of the pivot column converted to fixed point once per pivot
+    // (both parts), for every column's dot product and update (a finite norm
+    // means finite entries)
+    QF *s_piv = reinterpret_cast<QF *>(s_y);
+    if constexpr (kQD) {
+      if (qcache) {
+        for (int i = tid; i < N; i += 64 * WP) {
+          bool bad = false;
+          s_piv[i] = qf_from(load_part_cg<P>(ak, Ap, 0, i), &bad);
+          s_piv[N + i] = qf_from(load_part_cg<P>(ak, Ap, 1, i), &bad);
+        }
+        __syncthreads();
+      }
+    }
     for (int j = k + 1 + (((b - (k + 1)) % G) + G) % G; j <= n; j += G) {
       double *aj = A + (long)j * ldA;
       // ||a_j||^2 before this update, read before the barriers of the reduction
@@ -261,7 +279,15 @@ __global__ void __launch_bounds__(64 * WP) k_mgs(int N, int n, double *__restric
         const bool zero = eo == 0;
         const int kb = (er + eo + 1) / 2 + 1;        // ||a_k|| ||a_j|| < 2^(kb - 1022)
         const int base = kb - 1022 + kQfDotLg + 1 - 255;
-        if (!zero && !bad) {
+        if (!zero && !bad && qcache) {
+          for (int i = r0; i < N; i += RS) {
+            const real ajr = load_part<P>(aj, Ap, 0, i), aji = load_part<P>(aj, Ap, 1, i);
+            if (part == 0) qf_dot2c(acc, s_piv[i], ajr, s_piv[N + i], aji, 1.0, base, &bad);
+            else qf_dot2c(acc, s_piv[i], aji, s_piv[N + i], ajr, -1.0, base, &bad);
+          }
+#pragma unroll
+          for (int m = 16; m > 0; m >>= 1) acc = fix_add<4>(acc, q_shfl_xor(acc, m));
+        } else if (!zero && !bad) {
 #pragma unroll
           for (int q = 0; q < kRowCache; ++q) {
             const int i = r0 + RS * q;
@@ -360,7 +386,27 @@ __global__ void __launch_bounds__(64 * WP) k_mgs(int N, int n, double *__restric
       const bool crit = j == k + 1;
       const bool fresh = N > 64 * kRowCache;
       const bool split = crit && !fresh && WP == 2;
-      if (!(split && w == 0)) {
+      bool updated = false;
+      if constexpr (kQD) {
+        if (qcache) {                              // the pivot rows from shared memory
+          if (!(split && w == 0)) {
+            for (int i = r0; i < N; i += RS) {
+              if (part == 0)
+                store_part<P>(aj, Ap, 0, i, qf_upd3(load_part<P>(aj, Ap, 0, i), qalr, s_piv[i], qali,
+                                                    s_piv[N + i], 1.0, abad));
+              else
+                store_part<P>(aj, Ap, 1, i, qf_upd3(load_part<P>(aj, Ap, 1, i), qalr, s_piv[N + i],
+                                                    qali, s_piv[i], -1.0, abad));
+            }
+            if (split && w == 1)                   // warp 0's rows of the real part
+              for (int i = lane; i < N; i += 64)
+                store_part<P>(aj, Ap, 0, i, qf_upd3(load_part<P>(aj, Ap, 0, i), qalr, s_piv[i], qali,
+                                                    s_piv[N + i], 1.0, abad));
+          }
+          updated = true;
+        }
+      }
+      if (!updated && !(split && w == 0)) {
         // a_j -= alpha a_k:  re: ajr - alr akr + ali aki;  im: aji - alr aki - ali akr
 #pragma unroll
         for (int q = 0; q < kRowCache; ++q) {
@@ -496,7 +542,9 @@ template <class P, int WP>
 cudaError_t launch_wp(int sm_count, cudaStream_t stream, int N, int n, double *A, long ldA,
                       double *W, double *nrm2, double *dx, int *ready, PathState *st,
                       const int *skip, double *resid, unsigned long long limit_ns, int withhold) {
-  const size_t smem = sizeof(double) * 2 * P::L * (size_t)n;
+  size_t smem = sizeof(double) * 2 * P::L * (size_t)n;
+  if (std::is_same<P, QD>::value && N <= kQfCacheMaxN && sizeof(QF) * 2 * (size_t)N > smem)
+    smem = sizeof(QF) * 2 * (size_t)N;            // the pivot column in fixed point
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_mgs<P, WP>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

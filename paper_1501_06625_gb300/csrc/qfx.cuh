@@ -203,4 +203,27 @@ __device__ __forceinline__ qd qf_upd2(const qd &a, const QF &ar, const qd &b, co
   return qf_sum_to_qd<3>(t);
 }
 
+// qf_dot2 with x1, x2 already in fixed point
+__device__ __forceinline__ void qf_dot2c(Q256 &acc, const QF &x1, const qd &y1, const QF &x2,
+                                        const qd &y2, double sg, int base, bool *bad) {
+  const QF p1 = qf_mul(x1, qf_from(y1, bad));
+  QF p2 = qf_mul(x2, qf_from(y2, bad));
+  if (sg < 0) p2 = qf_neg(p2);
+  if (p1.e != kQFZeroE) acc = fix_add<4>(acc, q_sar(p1.m, base - p1.e));
+  if (p2.e != kQFZeroE) acc = fix_add<4>(acc, q_sar(p2.m, base - p2.e));
+}
+
+// qf_upd2 with b, c already in fixed point
+__device__ __forceinline__ qd qf_upd3(const qd &a, const QF &ar, const QF &b, const QF &ai,
+                                      const QF &c, double sg, bool abad) {
+  bool bad = abad;
+  const QF A = qf_from(a, &bad);
+  const QF p1 = qf_mul(ar, b);
+  QF p2 = qf_mul(ai, c);
+  if (sg < 0) p2 = qf_neg(p2);
+  if (bad) return {{__longlong_as_double(0x7ff8000000000000ll), 0.0, 0.0, 0.0}};
+  const QF t[3] = {A, qf_neg(p1), p2};
+  return qf_sum_to_qd<3>(t);
+}
+
 }  // namespace ph
