@@ -73,10 +73,12 @@ inline JobLayout job_layout(int L, int n, long ldA, int emax, long nsf, long nsg
 }
 
 // dynamic shared memory of a block for jobs of up to n variables: the back
-// substitution's y [2L][n], the pivot norms [L][n+1], and the columns'
-// exponent bounds of the DD fixed-point MGS [n+1] (unsigned)
+// substitution's y [2L][n], the pivot norms [L][n+1], the columns' exponent
+// bounds of the fixed-point MGS [n+1] (unsigned), and in QD the pivot column
+// in fixed point [2][n] (QF)
 inline size_t job_smem_bytes(int L, int n) {
-  return sizeof(double) * (2L * L * n + (long)L * (n + 1) + (n + 2) / 2);
+  return sizeof(double) * (2L * L * n + (long)L * (n + 1) + (n + 2) / 2) +
+         (L == 4 ? sizeof(QF) * 2 * (size_t)n : 0);
 }
 
 // one part (0 = real, 1 = imaginary) of element i of a complex array laid out
@@ -173,6 +175,8 @@ __device__ int block_mgs(int N, int n, long ldA, double *A, double *W, double *d
   const long Ap = (long)nc * ldA, Wp = (long)nc * nc;
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
   unsigned *s_cexp = (unsigned *)(s_nrm + (long)P::L * nc);
+  QF *s_piv = (QF *)(s_nrm + (long)P::L * nc + (nc + 1) / 2);   // QD: [2][N]
+  const bool qcache = kQD && N <= n;               // the buffer holds n rows
   // headroom of a dot product's accumulator: 2N leading products and small terms
   const int lgN = 32 - __clz(2 * N + 1);
   if (tid == 0) s_bad = 0;
@@ -201,6 +205,16 @@ __device__ int block_mgs(int N, int n, long ldA, double *A, double *W, double *d
     }
     const real inv2 = P::recip(r2);
     const double *ak = A + (long)k * ldA;
+    if constexpr (kQD) {
+      if (qcache) {                                // the pivot column in fixed point, once
+        for (int i = tid; i < N; i += kBT) {
+          bool bad = false;
+          s_piv[i] = qf_from(rp_load<P>(ak, Ap, 0, i), &bad);
+          s_piv[N + i] = qf_from(rp_load<P>(ak, Ap, 1, i), &bad);
+        }
+        __syncthreads();
+      }
+    }
     for (int j = k + 1 + (((w - (k + 1)) % kNW) + kNW) % kNW; j <= n; j += kNW) {
       double *aj = A + (long)j * ldA;
       real dsr, dsi;                               // a_k^H a_j
@@ -238,10 +252,15 @@ __device__ int block_mgs(int N, int n, long ldA, double *A, double *W, double *d
           Q256 accr = q_zero(), acci = q_zero();
           bool bad = false;
           for (int i = lane; i < N; i += 32) {
-            const qd akr = rp_load<P>(ak, Ap, 0, i), aki = rp_load<P>(ak, Ap, 1, i);
             const qd ajr = rp_load<P>(aj, Ap, 0, i), aji = rp_load<P>(aj, Ap, 1, i);
-            qf_dot2(accr, akr, ajr, aki, aji, 1.0, base, &bad);
-            qf_dot2(acci, akr, aji, aki, ajr, -1.0, base, &bad);
+            if (qcache) {
+              qf_dot2c(accr, s_piv[i], ajr, s_piv[N + i], aji, 1.0, base, &bad);
+              qf_dot2c(acci, s_piv[i], aji, s_piv[N + i], ajr, -1.0, base, &bad);
+            } else {
+              const qd akr = rp_load<P>(ak, Ap, 0, i), aki = rp_load<P>(ak, Ap, 1, i);
+              qf_dot2(accr, akr, ajr, aki, aji, 1.0, base, &bad);
+              qf_dot2(acci, akr, aji, aki, ajr, -1.0, base, &bad);
+            }
           }
 #pragma unroll
           for (int m = 16; m > 0; m >>= 1) {
@@ -286,8 +305,13 @@ __device__ int block_mgs(int N, int n, long ldA, double *A, double *W, double *d
           aji = fx_upd(rp_load<P>(aj, Ap, 1, i), alr, aki, ali, akr, -1.0);
           emax = max(emax, max(dbl_ef(ajr.h), dbl_ef(aji.h)));
         } else if constexpr (kQD) {
-          ajr = qf_upd2(rp_load<P>(aj, Ap, 0, i), qalr, akr, qali, aki, 1.0, abad);
-          aji = qf_upd2(rp_load<P>(aj, Ap, 1, i), qalr, aki, qali, akr, -1.0, abad);
+          if (qcache) {
+            ajr = qf_upd3(rp_load<P>(aj, Ap, 0, i), qalr, s_piv[i], qali, s_piv[N + i], 1.0, abad);
+            aji = qf_upd3(rp_load<P>(aj, Ap, 1, i), qalr, s_piv[N + i], qali, s_piv[i], -1.0, abad);
+          } else {
+            ajr = qf_upd2(rp_load<P>(aj, Ap, 0, i), qalr, akr, qali, aki, 1.0, abad);
+            aji = qf_upd2(rp_load<P>(aj, Ap, 1, i), qalr, aki, qali, akr, -1.0, abad);
+          }
           emax = max(emax, max(dbl_ef(ajr.x[0]), dbl_ef(aji.x[0])));
         } else {
           ajr = PO::upd(rp_load<P>(aj, Ap, 0, i), alr, akr, ali, aki, 1.0);
