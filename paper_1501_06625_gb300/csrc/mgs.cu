@@ -559,15 +559,20 @@ cudaError_t launch_wp(int sm_count, cudaStream_t stream, int N, int n, double *A
                                      smem, stream);
 }
 
-// Two warps per part (128 threads).  (Four warps per part halve the chain of
-// instructions per warp on a pivot's critical path, but measured slower on
-// tall QD matrices -- 259 against 235 ms at 512 x 513 -- where each column's
-// reductions then combine four warps instead of two.)
+// Two warps per part (128 threads); four (256 threads) for QD columns taller
+// than 128 rows.  With FP64 sums four warps per part measured slower on tall
+// QD matrices (259 against 235 ms at 512 x 513: the FP64 pipe was already
+// full); with the fixed-point QD arithmetic the integer chains are
+// latency-bound and twice the warps hide more of it (134 -> 107 ms at
+// 512 x 513, 29.6 -> 26.3 ms at 256 x 257).
 template <class P>
 cudaError_t launch_p(int sm_count, cudaStream_t stream, int N, int n, double *A, long ldA,
                      double *W, double *nrm2, double *dx, int *ready, PathState *st,
                      const int *skip, double *resid, unsigned long long limit_ns = kWaitLimitNs,
                      int withhold = -1) {
+  if (std::is_same<P, QD>::value && N > 128)
+    return launch_wp<P, 4>(sm_count, stream, N, n, A, ldA, W, nrm2, dx, ready, st, skip, resid,
+                           limit_ns, withhold);
   return launch_wp<P, 2>(sm_count, stream, N, n, A, ldA, W, nrm2, dx, ready, st, skip, resid,
                          limit_ns, withhold);
 }
