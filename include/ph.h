@@ -459,6 +459,17 @@ ph_status ph_set_wait_limit(ph_ctx *ctx, double ms);
  * and norms (each input truncated below 2^-116 (DD) / 2^-244 (QD) of the
  * largest; the total correctly rounded limb by limb). */
 ph_status ph_debug_warp_sum(int device, int limbs, const double *in, double *out);
+
+/* Test support for the fixed-point updates of the MGS kernels: for each of
+ * count cases, in[case][6][limbs] (host array) holds a, ar, b, ai, c and the
+ * sign sg (its leading limb, +1 or -1), and out[case][limbs] (host array)
+ * receives a - ar b + sg ai c as the MGS kernels form it in fixed point:
+ * limbs 2 (double-double) the exact products of the leading limbs and the
+ * cross products summed as 128-bit integers and rounded to two limbs; limbs 4
+ * (quad-double) 256-bit fixed-point values, products of their top words,
+ * exact sums and the four-limb round-back.  count <= 65536.  PH_EINVAL on a
+ * bad argument, PH_ENOMEM / PH_ECUDA on a failed device allocation or copy. */
+ph_status ph_debug_update(int device, int limbs, int count, const double *in, double *out);
 ph_status ph_set_memory_limit(int64_t bytes, int64_t *in_use);
 ph_status ph_debug_withhold_pivot(ph_ctx *ctx, int k);
 

@@ -850,3 +850,52 @@ extern "C" ph_status ph_debug_warp_sum(int device, int limbs, const double *in, 
   if (e != cudaSuccess) { cudaGetLastError(); return PH_ECUDA; }
   return PH_OK;
 }
+
+namespace {
+// one case per thread: a - ar b + sg ai c in the MGS kernels' fixed-point forms
+template <int L>
+__global__ void k_debug_update(int count, const double *in, double *out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= count) return;
+  const double *v = in + (long)c * 6 * L;
+  if constexpr (L == 2) {
+    const dd a = {v[0], v[1]}, ar = {v[2], v[3]}, b = {v[4], v[5]}, ai = {v[6], v[7]};
+    const dd cc = {v[8], v[9]};
+    const dd r = fx_upd(a, ar, b, ai, cc, v[10] < 0 ? -1.0 : 1.0);
+    out[2L * c] = r.h;
+    out[2L * c + 1] = r.l;
+  } else {
+    qd x[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q)
+#pragma unroll
+      for (int l = 0; l < 4; ++l) x[q].x[l] = v[4 * q + l];
+    const qd r = qf_upd(x[0], x[1], x[2], x[3], x[4], v[20] < 0 ? -1.0 : 1.0);
+#pragma unroll
+    for (int l = 0; l < 4; ++l) out[4L * c + l] = r.x[l];
+  }
+}
+}  // namespace
+
+extern "C" ph_status ph_debug_update(int device, int limbs, int count, const double *in,
+                                     double *out) {
+  if ((limbs != 2 && limbs != 4) || count < 1 || count > 65536 || !in || !out) return PH_EINVAL;
+  if (cudaSetDevice(device) != cudaSuccess) { cudaGetLastError(); return PH_ECUDA; }
+  const size_t nin = (size_t)count * 6 * limbs, nout = (size_t)count * limbs;
+  double *d = nullptr;
+  if (cudaMalloc(&d, sizeof(double) * (nin + nout)) != cudaSuccess) {
+    cudaGetLastError();
+    return PH_ENOMEM;
+  }
+  cudaError_t e = cudaMemcpy(d, in, sizeof(double) * nin, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    const int grid = (count + 127) / 128;
+    if (limbs == 2) k_debug_update<2><<<grid, 128>>>(count, d, d + nin);
+    else k_debug_update<4><<<grid, 128>>>(count, d, d + nin);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(out, d + nin, sizeof(double) * nout, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) { cudaGetLastError(); return PH_ECUDA; }
+  return PH_OK;
+}

@@ -66,7 +66,7 @@ EXPORTS = ["ph_init", "ph_destroy", "ph_last_error", "ph_system_load", "ph_syste
            "ph_server_job_bytes", "ph_mgs_variant", "ph_sum_lanes", "ph_ctrl_linear_contraction",
            "ph_mgs_set_variant", "ph_set_wait_limit", "ph_set_memory_limit",
            "ph_debug_withhold_pivot", "ph_block_lanes", "ph_set_block_lanes",
-           "ph_debug_warp_sum", "ph_unit_rates"]
+           "ph_debug_warp_sum", "ph_unit_rates", "ph_debug_update"]
 
 
 class PhError(RuntimeError):
@@ -110,6 +110,7 @@ def lib():
             L.ph_profile_newton.argtypes = [vp, vp, vp, vp, C.c_int, vp, vp, C.c_int, dp]
             L.ph_set_wait_limit.argtypes = [vp, C.c_double]
             L.ph_debug_warp_sum.argtypes = [C.c_int, C.c_int, dp, dp]
+            L.ph_debug_update.argtypes = [C.c_int, C.c_int, C.c_int, vp, vp]
             L.ph_unit_rates.argtypes = [vp, dp]
             L.ph_block_lanes.argtypes = [vp, vp, C.POINTER(C.c_int), dp]
             L.ph_set_block_lanes.argtypes = [vp, vp, C.c_int]
@@ -377,6 +378,20 @@ def ph_unit_rates(ctx):
     r = (C.c_double * 3)()
     _check(ctx, lib().ph_unit_rates(ctx, r))
     return list(r)
+
+
+def ph_debug_update(device: int, cases):
+    """a - ar b + sg ai c in the MGS kernels' fixed-point forms for cases
+    [count][6][limbs] (a, ar, b, ai, c, sg); returns [count][limbs] (test
+    support)."""
+    v = np.ascontiguousarray(cases, dtype=np.float64)
+    count, six, limbs = v.shape
+    assert six == 6
+    out = np.zeros((count, limbs))
+    st = lib().ph_debug_update(device, limbs, count, _ptr(v), _ptr(out))
+    if st != PH_OK:
+        raise PhError(st, "ph_debug_update failed")
+    return out
 
 
 def ph_debug_warp_sum(device: int, values):
