@@ -959,6 +959,54 @@ def sparse512_leg(libph, synth, ctx, torch, dev, seed, steps):
                             "ms_grid_cluster_tiled": vms}}
 
 
+def sparse512_whole_path(libph, synth, ctx, torch, dev, seed, max_steps=4000):
+    """One whole path of the sparse n = 512 QD homotopy to t = 1.  The
+    all-ones start root's path need not end at a regular root, so the system
+    is planted (synth.sparse512_planted: the sparse recipe plus the constant
+    terms that make f(x*) = 0 exactly).  x* is tracked backwards (start system
+    f, target the total-degree system, gamma' = 1/gamma; untimed), its end
+    rounded to the nearest root of x_i^{d_i} = 1, and the forward path from
+    that start root -- a path of the n = 512 total-degree homotopy -- is timed
+    with CUDA events and checked against x* (success: within 1e-48).  Corrector
+    tolerance on the way 1e-8 with 5 Newton iterations, QD at t = 1."""
+    stream = torch.cuda.current_stream(dev)
+    L = 4
+    wl, xs = synth.sparse512_planted(seed, "qd")
+    f = ctx.load(wl.f, L)
+    G = ctx.load(synth.total_degree_start(wl.f), L)
+    base = dict(synth.default_params(L), max_steps=max_steps, tol_path=1e-8, max_newton=5)
+    t0 = time.perf_counter()
+    gb = _soa([1.0 / wl.gamma], L).reshape(L, 2)
+    xl = np.zeros((L, 2, 512))
+    stb, sdb, _ = libph.ph_track_path(ctx.h, G, f, gb, _soa(xs, L), base, xl)
+    back_s = time.perf_counter() - t0
+    out = {"workload": wl.name, "backward_s": back_s, "backward_status": libph.STATUS_NAMES[stb],
+           "backward_steps": sdb["steps"], "backward_t_final": sdb["t_final"],
+           "params": {"tol_path": 1e-8, "max_newton": 5, "max_dt": base["max_dt"]}}
+    if stb == libph.PH_OK:
+        x0 = torch.tensor(_soa(synth.nearest_start_root(wl.f, xl[0, 0] + 1j * xl[0, 1]), L),
+                          device=dev)
+        gam = torch.tensor(wl.gamma_soa(), device=dev)
+        xo = torch.empty_like(x0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st, sd, _ = libph.ph_track_path(ctx.h, f, None, gam, x0, base, xo)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        err = _err_vs(xo.cpu().numpy(), xs)
+        out.update({"status": libph.STATUS_NAMES[st], "ms": ms, "steps": sd["steps"],
+                    "accepted": sd["accepted"], "rejected": sd["rejected"],
+                    "newton_iters": sd["newton_iters"], "t_final": sd["t_final"],
+                    "err_vs_planted": err, "ok": bool(st == libph.PH_OK and err <= 1e-48),
+                    "paths_per_s": 1e3 / ms,
+                    "corrector_steps_per_s": sd["newton_iters"] / (ms * 1e-3)})
+    ctx.free(f)
+    ctx.free(G)
+    return out
+
+
 def hard_precision_leg(libph, synth, ctx, torch, dev, seed, steps, decades=8.0, max_dt=1e-6):
     """The planted n = 128 workload where it is hard: precision128's shape with the coefficient
     moduli spread over `decades` decades between the equations (each
@@ -1233,6 +1281,9 @@ def main():
                     help="planted dense64 QD paths tracked whole by the single-path form")
     ap.add_argument("--sparse-steps", type=int, default=16,
                     help="predictor-corrector steps of the sparse n = 512 QD path (0 skips)")
+    ap.add_argument("--sparse-whole-paths", type=int, default=0,
+                    help="1: one whole planted sparse n = 512 QD path to t = 1, backwards "
+                         "then forwards (several minutes each way; off by default)")
     ap.add_argument("--large-jobs", type=int, default=1,
                     help="1: the serving loop's large-job route leg (0 skips it)")
     ap.add_argument("--hard-steps", type=int, default=30,
@@ -1396,7 +1447,7 @@ def main():
         monodromy["degree"] = monodromy_degree_leg(
             synth, ctx, args.seed, [(16, 32)] + ([(64, 76)] if args.monodromy_degree_64 else []))
 
-    whole = sparse = hard = large = None
+    whole = sparse = hard = large = sparse_whole = None
     if rank == 0 and world == 1:
         if args.whole_paths > 0 or args.whole_paths_qd > 0:
             _t0 = time.perf_counter()
@@ -1407,6 +1458,10 @@ def main():
             _t0 = time.perf_counter()
             sparse = sparse512_leg(libph, synth, ctx, torch, dev, args.seed, args.sparse_steps)
             legs['sparse512'] = time.perf_counter() - _t0
+        if args.sparse_whole_paths > 0:
+            _t0 = time.perf_counter()
+            sparse_whole = sparse512_whole_path(libph, synth, ctx, torch, dev, args.seed)
+            legs['sparse512_whole_path'] = time.perf_counter() - _t0
         if args.large_jobs:
             _t0 = time.perf_counter()
             large = large_job_leg(libph, synth, ctx, args.seed)
@@ -1492,7 +1547,8 @@ def main():
             "path": s["path"], "qd": qd, "batched": batch, "serving": serve,
             "serving_mixed": serve_mixed, "precision": precision, "cyclic": cyclic,
             "cyclic_monodromy_path": monodromy, "whole_paths": whole,
-            "sparse512_segment": sparse, "precision_ill_conditioned": hard,
+            "sparse512_segment": sparse, "sparse512_whole_path": sparse_whole,
+            "precision_ill_conditioned": hard,
             "serving_large_jobs": large,
             "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},

@@ -240,6 +240,46 @@ def planted_system(rng: Rng, n: int, terms_per_poly: int, vars_per_term: int,
     return spec, xs
 
 
+def sparse_planted(rng: Rng, n: int, extra_terms: int = 3, vars_per_term: int = 2,
+                   exps: tuple[int, ...] = (1, 2)) -> tuple[SystemSpec, np.ndarray]:
+    """The sparse recipe of sparse_system (a linear term c x_i plus
+    `extra_terms` monomials over `vars_per_term` other variables) with a
+    planted root x*: coordinates drawn from {1, i, -1, -i}, and polynomial i
+    gets the constant term b_i = -sum_k c_ik (x*)^{a_ik}, summed exactly in
+    rationals and stored as two limbs, so that f(x*) = 0 exactly.  Returns
+    (system, x*)."""
+    from fractions import Fraction
+    units = (1 + 0j, 1j, -1 + 0j, -1j)
+    xs = np.array([rng.choice(units) for _ in range(n)])
+    polys, lo = [], []
+    for i in range(n):
+        drawn = [(rng.unit_complex(), [(i, 1)])]
+        for _ in range(extra_terms):
+            vs = rng.sample(n - 1, vars_per_term)
+            vs = [v if v < i else v + 1 for v in vs]
+            drawn.append((rng.unit_complex(), [(v, rng.choice(exps)) for v in vs]))
+        terms = []
+        bre, bim = Fraction(0), Fraction(0)
+        for c, mono in drawn:
+            w = c
+            for v, k in mono:
+                w = w * xs[v] ** k                 # exact: a swap or negation of parts
+            bre -= Fraction(w.real)
+            bim -= Fraction(w.imag)
+            terms.append((c, mono))
+            lo.append(0j)
+        hre, him = float(bre), float(bim)
+        lre, lim = float(bre - Fraction(hre)), float(bim - Fraction(him))
+        if Fraction(hre) + Fraction(lre) != bre or Fraction(him) + Fraction(lim) != bim:
+            raise ValueError("the constant term does not fit in two limbs")
+        terms.append((complex(hre, him), []))
+        lo.append(complex(lre, lim))
+        polys.append(terms)
+    spec = build_system(n, n, polys)
+    spec.coeff_lo = np.asarray(lo, dtype=np.complex128)
+    return spec, xs
+
+
 def cyclic_system(n: int) -> SystemSpec:
     """Cyclic n-roots (Section 4.2, Eq. (10)): f_i = sum_j prod_{k=j}^{j+i-1}
     x_{k mod n} for i = 1..n-1, and f_n = x_0 x_1 ... x_{n-1} - 1.  Built with
@@ -467,6 +507,19 @@ def sparse512(seed: int = 1, prec="qd") -> Workload:
     gamma = rng.unit_complex()
     return Workload(f"sparse512_{'dd' if L == 2 else 'qd'}", seed, L, f, gamma,
                     np.ones(512, dtype=np.complex128), default_params(L))
+
+
+def sparse512_planted(seed: int = 1, prec="qd") -> tuple[Workload, np.ndarray]:
+    """The sparse n = 512 recipe with a planted root x* (sparse_planted), so
+    that a whole total-degree path ends at a regular root: the start root of
+    x*'s path comes from tracking x* backwards.  Returns (workload, x*)."""
+    L = _limbs(prec)
+    rng = Rng(seed)
+    f, xs = sparse_planted(rng, 512)
+    gamma = rng.unit_complex()
+    wl = Workload(f"sparse512_planted_{'dd' if L == 2 else 'qd'}", seed, L, f, gamma,
+                  np.ones(512, dtype=np.complex128), default_params(L))
+    return wl, xs
 
 
 def precision128(seed: int = 1, prec="qd") -> tuple[Workload, np.ndarray]:

@@ -158,3 +158,32 @@ def test_planted_root_is_exact(orc):
     for L in (2, 4):
         h, _ = orc.eval_h(orc.System(spec, L), soa_from_complex(xs, L), t=1.0)
         assert not np.any(h)
+
+
+def test_sparse_planted_root_is_exact(orc):
+    """The sparse planted generator (the sparse n = 512 recipe with a planted
+    root, here at n = 40): f(x*) = 0 exactly in rationals and by the oracle,
+    and every polynomial keeps the recipe's linear term in its own variable."""
+    from fractions import Fraction
+    rng = synth.Rng(11)
+    spec, xs = synth.sparse_planted(rng, 40)
+    for i in range(spec.N):
+        sre, sim = Fraction(0), Fraction(0)
+        for k in range(spec.term_ptr[i], spec.term_ptr[i + 1]):
+            cre = Fraction(spec.coeff[k].real) + Fraction(spec.coeff_lo[k].real)
+            cim = Fraction(spec.coeff[k].imag) + Fraction(spec.coeff_lo[k].imag)
+            ure, uim = Fraction(1), Fraction(0)
+            for q in range(spec.var_ptr[k], spec.var_ptr[k + 1]):
+                z = xs[spec.var_idx[q]]
+                for _ in range(int(spec.var_exp[q])):
+                    ure, uim = ure * Fraction(z.real) - uim * Fraction(z.imag), \
+                        ure * Fraction(z.imag) + uim * Fraction(z.real)
+            sre += cre * ure - cim * uim
+            sim += cre * uim + cim * ure
+        assert sre == 0 and sim == 0
+        k0 = spec.term_ptr[i]                       # the linear term c x_i comes first
+        assert list(spec.var_idx[spec.var_ptr[k0]:spec.var_ptr[k0 + 1]]) == [i]
+        assert list(spec.var_exp[spec.var_ptr[k0]:spec.var_ptr[k0 + 1]]) == [1]
+    for L in (2, 4):
+        h, _ = orc.eval_h(orc.System(spec, L), soa_from_complex(xs, L), t=1.0)
+        assert not np.any(h)
