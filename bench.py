@@ -253,7 +253,7 @@ CONTROL = {"control": 0}       # 1: host-side step control (for profiling runs)
 # DRAM bytes (read + write) of one k_mgs<DD> launch on the dense64 DD system,
 # from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # current kernel: the 64 x 65 matrix and the projection coefficients, read once.
-MGS_DENSE64_DD_TRAFFIC = 278016
+MGS_DENSE64_DD_TRAFFIC = 279040
 
 
 def seg_params(wl):
