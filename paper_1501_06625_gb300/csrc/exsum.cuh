@@ -21,6 +21,11 @@
 // Zero inputs add nothing; a non-finite input makes every lane's result NaN;
 // results below the normal range of a double are flushed to zero.  Every lane
 // of the warp must call (full-mask shuffles) and every lane gets the total.
+//
+// The second half of the file holds the double-double forms of the
+// throughput-bound kernels: a dot-product term or an update split into exact
+// products and cross products (8 FP64 instructions) whose terms are summed as
+// 128-bit integers and rounded back to two limbs.
 #pragma once
 #include "mp.cuh"
 
