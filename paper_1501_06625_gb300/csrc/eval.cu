@@ -113,17 +113,17 @@ __global__ void __launch_bounds__(128) k_ad_split(int s0, int s1, int Mp,
     int a = vexp[(long)p * Mp + s];
     if (a >= 2) {
       cx<P> w = c_load<P>(ptab + (a - 2) * pl, n, vidx[(long)p * Mp + s]);
-      cf = has_cf ? c_mul<P>(cf, w) : w;
+      cf = has_cf ? c_mul_ad<P>(cf, w) : w;
       has_cf = true;
     }
   }
   const cx<P> c0 = (active && q == 0) ? c_load<P>(coeff, Mp, s) : one;
   cx<P> B = c0;
   bool b_one = !(active && q == 0);
-  if (has_cf) { B = b_one ? cf : c_mul<P>(B, cf); b_one = false; }
+  if (has_cf) { B = b_one ? cf : c_mul_ad<P>(B, cf); b_one = false; }
   for (int p = p0; p < p1; ++p) {
     cx<P> xj = c_load<P>(ptab, n, vidx[(long)p * Mp + s]);
-    B = b_one ? xj : c_mul<P>(B, xj);
+    B = b_one ? xj : c_mul_ad<P>(B, xj);
     b_one = false;
   }
   // inclusive prefix and suffix products over the T lanes of this monomial
@@ -131,9 +131,9 @@ __global__ void __launch_bounds__(128) k_ad_split(int s0, int s1, int Mp,
 #pragma unroll
   for (int d = 1; d < T; d <<= 1) {
     cx<P> y = shfl_up_c<P>(I, d, T);
-    if (q >= d) I = c_mul<P>(y, I);
+    if (q >= d) I = c_mul_ad<P>(y, I);
     cx<P> z = shfl_down_c<P>(S, d, T);
-    if (q + d < T) S = c_mul<P>(S, z);
+    if (q + d < T) S = c_mul_ad<P>(S, z);
   }
   cx<P> left = shfl_up_c<P>(I, 1, T);
   cx<P> right = shfl_down_c<P>(S, 1, T);
@@ -145,24 +145,24 @@ __global__ void __launch_bounds__(128) k_ad_split(int s0, int s1, int Mp,
   bool o_one = true;
   if (q > 0) { outer = left; o_one = false; }
   else { outer = c0; o_one = false; }
-  if (q < T - 1) { outer = o_one ? right : c_mul<P>(outer, right); o_one = false; }
-  if (has_cf) { outer = o_one ? cf : c_mul<P>(outer, cf); o_one = false; }
+  if (q < T - 1) { outer = o_one ? right : c_mul_ad<P>(outer, right); o_one = false; }
+  if (has_cf) { outer = o_one ? cf : c_mul_ad<P>(outer, cf); o_one = false; }
   if (o_one) outer = one;
   // local reverse sweep over the chunk (prefixes parked in the slots)
   cx<P> pre = outer;
   for (int p = p0; p < p1; ++p) {
     c_store<P>(slots, nslots, (long)p * Mp + s, pre);
-    if (p + 1 < p1) pre = c_mul<P>(pre, c_load<P>(ptab, n, vidx[(long)p * Mp + s]));
+    if (p + 1 < p1) pre = c_mul_ad<P>(pre, c_load<P>(ptab, n, vidx[(long)p * Mp + s]));
   }
   cx<P> suf = one;
   for (int p = p1 - 1; p >= p0; --p) {
     cx<P> d = c_load<P>(slots, nslots, (long)p * Mp + s);
-    if (p < p1 - 1) d = c_mul<P>(d, suf);
+    if (p < p1 - 1) d = c_mul_ad<P>(d, suf);
     d = c_mul_int<P>(d, vexp[(long)p * Mp + s]);
     c_store<P>(slots, nslots, (long)p * Mp + s, d);
     if (p > p0) {
       cx<P> xj = c_load<P>(ptab, n, vidx[(long)p * Mp + s]);
-      suf = (p == p1 - 1) ? xj : c_mul<P>(suf, xj);
+      suf = (p == p1 - 1) ? xj : c_mul_ad<P>(suf, xj);
     }
   }
 }

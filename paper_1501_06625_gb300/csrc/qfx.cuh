@@ -226,4 +226,18 @@ __device__ __forceinline__ qd qf_upd3(const qd &a, const QF &ar, const QF &b, co
   return qf_sum_to_qd<3>(t);
 }
 
+// The complex product a b of QD values in fixed point: the four real parts
+// converted once, four products of their top words, each part's two products
+// summed exactly and rounded to four limbs.  A non-finite part falls back to
+// the FP64 form (which propagates it).
+__device__ __forceinline__ cx<QD> qf_cmul(const cx<QD> &a, const cx<QD> &b) {
+  bool bad = false;
+  const QF ar = qf_from(a.re, &bad), ai = qf_from(a.im, &bad);
+  const QF br = qf_from(b.re, &bad), bi = qf_from(b.im, &bad);
+  if (bad) return cops<QD>::mul(a, b);
+  const QF re[2] = {qf_mul(ar, br), qf_neg(qf_mul(ai, bi))};
+  const QF im[2] = {qf_mul(ar, bi), qf_mul(ai, br)};
+  return {qf_sum_to_qd<2>(re), qf_sum_to_qd<2>(im)};
+}
+
 }  // namespace ph
