@@ -2,7 +2,9 @@
 sequential rate is measured before the server runs, every request of the
 closed loop, the Poisson stream and the sweep of offered loads (0.5, 1 and 2
 x the sequential capacity) is submitted and waited for, and the figures come
-out with the keys the JSON line carries."""
+out with the keys the JSON line carries.  The whole sparse-path leg: x* is
+tracked backwards, its end rounded to roots of x_i^{d_i} = 1, the forward path
+checked against x*, and a failed backward path ends the leg."""
 import os
 import sys
 import time
